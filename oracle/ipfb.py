@@ -1,0 +1,177 @@
+"""Oracle: circulant inverse PFB with optional Wiener filtering (FP64).
+
+Test infrastructure only (see oracle/__init__.py).
+
+Steps, in the paper's order (Sec. 3.1, Sec. 4.1, App. C):
+  1. recorded spectra -> N-point inverse real FFT per spectrum ("undoing F"),
+     giving the [J, N] polyphase array d; column n is d_n (Eq. pfbsubsampled);
+  2. per column, J-point DFT along the frame axis: F d_n;
+  3. divide by the conjugate sub-filter spectrum (F w_n)^* (Eq. decorrelation),
+     optionally Wiener-weighted by H_n (Eq. wiener weights);
+  4. inverse J-point DFT; x_hat[j*N + n] = x_hat_n[j].
+
+Readings:
+  * Sec. 3.1 extends d_n "to b frames" without saying how; here the recorded
+    spectra are J periodic spectra of J frames, so the circulant model is exact
+    and exactly J frames are reconstructed.
+  * Eq. wiener weights is written for the filter H_n applied before the
+    decorrelation; the combined per-mode gain is G = H_n / W_n^* =
+    W_n (1 + phi^2) / (|W_n|^2 + phi^2), identical to conj(W)/(|W|^2 + N/S)
+    under the opposite DFT sign for W.  phi^2 = 0 is the exact inverse
+    1 / W_n^*.  The (1 + phi^2) factor is optional (App. B); `normalize`
+    switches it.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .pfb import dequantize
+
+
+def eigenvalues(window: np.ndarray, nframes: int, ks=None) -> np.ndarray:
+    """Sec. 3.1: W_n(k) = (F w_n)_k = sum_r w[r, n] exp(-2 pi i r k / J), the
+    J-point DFT of the zero-padded sub-filter w_n (the eigenvalues of the circulant
+    W_n^circ).  Direct p-term sum; phases from the exactly reduced (r*k mod J)/J.
+    Returns complex [len(ks), N] (all k < J when ks is None)."""
+    p, N = window.shape
+    J = int(nframes)
+    k = np.arange(J, dtype=np.int64) if ks is None else np.asarray(ks, dtype=np.int64)
+    out = np.zeros((k.shape[0], N), dtype=np.complex128)
+    for r in range(p):
+        ph = np.exp(-2j * np.pi * ((r * k) % J).astype(np.float64) / J)
+        out += ph[:, None] * window[r][None, :]
+    return out
+
+
+def gain(W: np.ndarray, noise_level: float, normalize: bool = True) -> np.ndarray:
+    """Per-mode decorrelation gain G = H_n / W_n^* (Eq. decorrelation with
+    Eq. wiener weights): W (1 + phi^2) / (|W|^2 + phi^2); phi^2 = 0 gives 1/W^*."""
+    phi2 = float(noise_level)
+    if phi2 == 0.0:
+        return 1.0 / np.conj(W)
+    norm = (1.0 + phi2) if normalize else 1.0
+    return W * norm / (np.abs(W) ** 2 + phi2)
+
+
+def wiener_filter(W: np.ndarray, noise_level: float, normalize: bool = True) -> np.ndarray:
+    """Eq. wiener weights: H_n = |W_n|^2 / (|W_n|^2 + phi^2) * (1 + phi^2)."""
+    phi2 = float(noise_level)
+    norm = (1.0 + phi2) if normalize else 1.0
+    a2 = np.abs(W) ** 2
+    return a2 / (a2 + phi2) * norm
+
+
+def frames_from_spectra(spectra: np.ndarray, lblock: int) -> np.ndarray:
+    """Step 1: N-point inverse real DFT of every spectrum (normalised 1/N)."""
+    return np.fft.irfft(spectra, n=lblock, axis=1)
+
+
+def decorrelate(d: np.ndarray, window: np.ndarray, noise_level: float,
+                normalize: bool = True) -> np.ndarray:
+    """Steps 2-4 on the [J, N] polyphase array d: per column, F d_n times G, then
+    F^dagger (normalised 1/J).  Returns the [J, N] reconstruction."""
+    J, N = d.shape
+    D = np.fft.fft(d, axis=0)
+    G = gain(eigenvalues(window, J), noise_level, normalize)
+    return np.real(np.fft.ifft(G * D, axis=0))
+
+
+def ipfb_from_spectra(spectra: np.ndarray, window: np.ndarray, noise_level: float,
+                      normalize: bool = True) -> np.ndarray:
+    """Circulant (Wiener) inverse PFB of complex spectra [J, N/2+1]; returns x_hat [J*N]."""
+    p, N = window.shape
+    d = frames_from_spectra(spectra, N)
+    return decorrelate(d, window, noise_level, normalize).reshape(-1)
+
+
+def ipfb_wiener(codes: np.ndarray, scale: np.ndarray, window: np.ndarray,
+                noise_level: float, normalize: bool = True) -> np.ndarray:
+    """Inverse PFB of packed 4-bit codes: dequantize, then ipfb_from_spectra."""
+    return ipfb_from_spectra(dequantize(codes, scale), window, noise_level, normalize)
+
+
+def ipfb_column(codes: np.ndarray, scale: np.ndarray, window: np.ndarray, n: int,
+                noise_level: float, normalize: bool = True) -> np.ndarray:
+    """Column n of the reconstruction only (x_hat[j*N + n] for all j), for checking
+    sampled outputs of full-size runs.  Step 1 is evaluated at the single index n
+    as d[j, n] = (1/N) sum over the full Hermitian spectrum of Y[j, c] e^{+2 pi i c n/N}."""
+    p, N = window.shape
+    Y = dequantize(codes, scale)  # [J, C]
+    C = Y.shape[1]
+    c = np.arange(C, dtype=np.int64)
+    ph = np.exp(2j * np.pi * ((c * n) % N).astype(np.float64) / N)
+    wt = np.full(C, 2.0)
+    wt[0] = 1.0
+    wt[C - 1] = 1.0
+    # the Nyquist and DC terms enter once, interior channels twice (conjugate pair)
+    dn = np.real(Y @ (wt * ph)) / N
+    J = Y.shape[0]
+    Dn = np.fft.fft(dn)
+    Wn = eigenvalues(window[:, n:n + 1], J)[:, 0]
+    G = gain(Wn, noise_level, normalize)
+    return np.real(np.fft.ifft(G * Dn))
+
+
+# --------------------------------------------------------------------------- #
+# Dense brute-force references (pins; tiny sizes only)
+# --------------------------------------------------------------------------- #
+
+def dense_pfb_matrix(window: np.ndarray, nframes: int) -> np.ndarray:
+    """The periodic PFB as one real matrix P of shape [J*(N+2), J*N]: rows are the
+    real and imaginary parts of every rfft channel of every spectrum, built column
+    by column from Eq. pfboperator (y = F S W x) applied to unit vectors."""
+    p, N = window.shape
+    J = int(nframes)
+    T = J * N
+    C = N // 2 + 1
+    P = np.zeros((J * 2 * C, T))
+    Fm = np.exp(-2j * np.pi * np.outer(np.arange(C), np.arange(N)) / N)  # [C, N]
+    for t in range(T):
+        j_in, n = divmod(t, N)
+        col = np.zeros((J, C), dtype=np.complex128)
+        for r in range(p):
+            j_out = (j_in - r) % J  # frame j_in feeds spectrum j_out with tap r
+            col[j_out] += window[r, n] * Fm[:, n]
+        P[:, t] = np.concatenate([col.real, col.imag], axis=1).reshape(-1)
+    return P
+
+
+def dense_circulant(window_col: np.ndarray, nframes: int) -> np.ndarray:
+    """W_n^circ of Eq. circ_convolution: (C x)[j] = sum_r w_r x[(j + r) mod J]."""
+    J = int(nframes)
+    Cm = np.zeros((J, J))
+    for j in range(J):
+        for r, wr in enumerate(window_col):
+            Cm[j, (j + r) % J] += wr
+    return Cm
+
+
+def tikhonov_column(d_col: np.ndarray, window_col: np.ndarray, noise_level: float,
+                    normalize: bool = True) -> np.ndarray:
+    """App. C: Tikhonov-regularised least squares for one column,
+    (1 + phi^2)(C^T C + phi^2 I)^{-1} C^T d, by a dense solve."""
+    J = d_col.shape[0]
+    Cm = dense_circulant(window_col, J)
+    phi2 = float(noise_level)
+    A = Cm.T @ Cm + phi2 * np.eye(J)
+    x = np.linalg.solve(A, Cm.T @ d_col)
+    return x * ((1.0 + phi2) if normalize else 1.0)
+
+
+# --------------------------------------------------------------------------- #
+# Analytic error spectra (App. B)
+# --------------------------------------------------------------------------- #
+
+def analytic_delta_naive(window: np.ndarray, nframes: int, snr: float) -> np.ndarray:
+    """App. B: delta(f) = (1/SNR)(1/N) sum_n 1/|W_n(Nf)|^2 for unfiltered
+    decorrelation of white input, evaluated at the J sub-stream frequencies."""
+    W = eigenvalues(window, nframes)
+    return np.mean(1.0 / np.abs(W) ** 2, axis=1) / snr
+
+
+def analytic_delta_wiener(window: np.ndarray, nframes: int, noise_level: float) -> np.ndarray:
+    """App. B: delta(f) = 1 - (1/N) sum_n H_n(Nf) with the un-normalised Wiener
+    filter H_n = |W_n|^2/(|W_n|^2 + phi^2), phi^2 = 1/SNR."""
+    W = eigenvalues(window, nframes)
+    H = wiener_filter(W, noise_level, normalize=False)
+    return 1.0 - np.mean(H, axis=1)

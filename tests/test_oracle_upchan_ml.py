@@ -1,0 +1,121 @@
+"""Pins for the oracle's up-channelization and ML / conjugate-gradient solve."""
+import numpy as np
+import pytest
+
+from oracle import ipfb, ml, pfb, upchan
+from paper_2608_23441_b300 import synth
+
+
+def test_upchannelize_brute_dft_and_parseval():
+    L = 64
+    x = synth.gaussian_stream(5 * L + 17, 1)   # trailing partial block dropped
+    X = upchannelize = upchan.upchannelize(x, L)
+    assert X.shape == (5, L // 2 + 1)
+    for b in range(5):
+        seg = x[b * L:(b + 1) * L]
+        assert np.allclose(X[b], upchan.brute_rdft(seg), atol=1e-11)
+        # Parseval for a real block: sum x^2 = (|X0|^2 + 2 sum |Xc|^2 + |X_{L/2}|^2) / L
+        e = (abs(X[b, 0]) ** 2 + 2 * np.sum(abs(X[b, 1:-1]) ** 2) + abs(X[b, -1]) ** 2) / L
+        assert e == pytest.approx(np.sum(seg ** 2), rel=1e-12)
+    assert upchannelize is X
+
+
+def test_upchannelize_bin_centred_tone():
+    L, c0 = 256, 37
+    t = np.arange(3 * L)
+    x = np.cos(2 * np.pi * c0 * t / L)
+    X = upchan.upchannelize(x, L)
+    mag = np.abs(X)
+    assert np.allclose(mag[:, c0], L / 2, rtol=1e-12)
+    mag[:, c0] = 0
+    assert mag.max() < 1e-9
+
+
+def _problem(N=8, p=4, J=32, seed=0, frac=0.2, noise=1e-2):
+    w = pfb.sinc_hamming_window(N, p)
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((J, N))
+    d = pfb.polyphase_sum(x.reshape(-1), w) + np.sqrt(noise) * rng.standard_normal((J, N))
+    mask = (rng.uniform(size=(J, N)) < frac).astype(np.float64)
+    return w, x, d, mask
+
+
+def test_operator_fft_equals_stencil_and_explicit_CtC():
+    w, x, d, mask = _problem(N=16, J=40)
+    V = np.random.default_rng(5).standard_normal(d.shape)
+    A1 = ml.normal_operator_fft(w, V, 0.3, mask, 1.7)
+    A2 = ml.normal_operator_stencil(w, V, 0.3, mask, 1.7)
+    assert np.allclose(A1, A2, atol=1e-12)
+    A3 = ml.apply_CT(w, ml.apply_C(w, V)) / 0.3 + 1.7 * mask * V
+    assert np.allclose(A1, A3, atol=1e-12)
+    # C^T is the transpose of C: <C u, v> = <u, C^T v> per column
+    U = np.random.default_rng(6).standard_normal(d.shape)
+    assert np.allclose(np.sum(ml.apply_C(w, U) * V, 0), np.sum(U * ml.apply_CT(w, V), 0))
+    # and C is exactly the periodic polyphase sum
+    assert np.allclose(ml.apply_C(w, U), pfb.polyphase_sum(U.reshape(-1), w))
+
+
+@pytest.mark.parametrize("precond", ["none", "wiener"])
+def test_cg_matches_dense_normal_equations(precond):
+    # Eq. chi squared: the minimiser solves the dense normal equations column by column.
+    w, x, d, mask = _problem()
+    sig2 = 1e-2
+    X, it, rel = ml.ml_solve_d(d, w, sig2, mask, x, 1.0, precond, 1e-12, 2000)
+    assert np.all(rel <= 1e-12)
+    for n in range(d.shape[1]):
+        ref = ml.dense_ml_column(d[:, n], w[:, n], sig2, mask[:, n], x[:, n], 1.0)
+        assert np.allclose(X[:, n], ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+    tr = ml.true_relative_residual(d, w, sig2, mask, x, 1.0, X)
+    assert np.all(tr < 1e-10)
+
+
+def test_toy_model_single_saved_sample():
+    # Sec. 4.2.2: symmetric window, no quantization: path N/2 loses its Nyquist mode
+    # (null vector alternating +-1); one saved sample pins it and the solve is exact.
+    N, p, J = 16, 4, 64
+    w = pfb.symmetric_sinc_hann_window(N, p)
+    x = np.random.default_rng(3).standard_normal((J, N))
+    d = pfb.polyphase_sum(x.reshape(-1), w)
+    # without a prior the alternating mode is invisible to chi^2
+    alt = (-1.0) ** np.arange(J)
+    assert np.abs(ml.apply_C(w[:, N // 2:N // 2 + 1], alt[:, None])).max() < 1e-14
+    mask = np.zeros((J, N))
+    mask[11, N // 2] = 1.0
+    X, it, rel = ml.ml_solve_d(d, w, 1.0, mask, x, 1.0, "none", 1e-13, 5000)
+    assert np.linalg.norm(X - x) / np.linalg.norm(x) < 1e-8
+
+
+def test_wiener_pcg_exact_without_mask():
+    # With an empty mask the Wiener preconditioner is the exact inverse: one iteration.
+    w, x, d, _ = _problem(N=16, J=64)
+    mask = np.zeros_like(d)
+    X, it, rel = ml.ml_solve_d(d, w, 0.05, mask, x, 1.0, "wiener", 1e-10, 50)
+    assert np.all(it == 1)
+    # and the answer is the exact circulant inverse of d
+    assert np.allclose(X, ipfb.decorrelate(d, w, 0.0), atol=1e-8)
+
+
+def test_cg_residual_and_error_decrease():
+    # CG minimises the A-norm of the error monotonically (Shewchuk 1994).
+    w, x, d, mask = _problem(N=8, J=48, seed=4)
+    sig2 = 1e-2
+    Xs = [ml.ml_solve_d(d, w, sig2, mask, x, 1.0, "none", 0.0, k)[0] for k in range(0, 12)]
+    Xstar = ml.ml_solve_d(d, w, sig2, mask, x, 1.0, "none", 1e-13, 3000)[0]
+    A = lambda V: ml.normal_operator_fft(w, V, sig2, mask, 1.0)  # noqa: E731
+    enorm = [np.sum((X - Xstar) * A(X - Xstar), axis=0) for X in Xs]
+    for a, b in zip(enorm[:-1], enorm[1:]):
+        assert np.all(b <= a * (1 + 1e-9) + 1e-18)
+
+
+def test_paper_protocol_wiener_start_improves_chi2():
+    # Sec. 4.3: Wiener initial guess, then 25 CG iterations; chi^2 must not increase.
+    w, x, d, mask = _problem(N=16, J=64, seed=7)
+    sig2 = 1e-2
+    x0 = ml.wiener_initial_guess(d, w, 0.01)
+
+    def chi2(X):
+        r = d - ml.apply_C(w, X)
+        return np.sum(r * r) / sig2 + np.sum(mask * (X - x) ** 2)
+
+    X25 = ml.ml_solve_d(d, w, sig2, mask, x, 1.0, "none", 0.0, 25, x0=x0)[0]
+    assert chi2(X25) < chi2(x0)
