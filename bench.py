@@ -1,0 +1,421 @@
+"""Benchmark: Wiener inverse PFB + up-channelization on one B300 (or N replicas).
+
+Workload (the large single-stream configuration): lblock 4096, ntap 4, sinc x
+Hamming window, 65536 spectra (2^28 samples), Gaussian noise plus 16 random
+tones (seed 2), FP32 on the GPU, 4-bit quantized spectra with per-channel step
+RMS/2.5; Wiener inversion with phi^2 measured from the simulation, then
+up-channelization by 64 (real FFTs of 262144 samples over consecutive blocks).
+
+One step = one call of ipfb_wiener_upchannelize over the resident 4-bit codes
+(unpack + per-frame inverse FFT, per-column frame-axis FFT + Wiener gain +
+inverse FFT, block real FFT).  The forward PFB that simulates the codes runs
+before timing and is reported separately under "stages".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank inverts its own stream (replicas, no data-path
+collective; weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LBLOCK, NTAP, NFRAMES, UPFACTOR = 4096, 4, 65536, 64
+NSAMP = LBLOCK * NFRAMES
+METRIC = "iPFB GSa/s at lblock=4096 ntap=4"
+UNIT = "GSa/s"
+WORKLOAD = "wiener_ipfb+upchannelize lblock=4096 ntap=4 nframes=65536 upfactor=64 (2^28 samples)"
+
+KERNEL_FILES = {
+    "k2_unpack_irfft": ["ipfb_kernels.cuh", "common.cuh", "k2_unpack.cu"],
+    "k3_column_wiener": ["ipfb_kernels.cuh", "common.cuh", "k3_large.cu", "k3_cluster.cu", "k3_small.cu"],
+    "k4_upchan": ["upchan_kernels.cuh", "common.cuh", "k4_upchan.cu"],
+    "k1_pfb_power": ["pfb_kernels.cuh", "common.cuh", "k1_forward.cu"],
+    "k1_pfb_quant": ["pfb_kernels.cuh", "common.cuh", "k1_forward.cu"],
+}
+
+
+def kernel_source_hash(name: str) -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_FILES.get(name, []):
+        with open(os.path.join(ROOT, "paper_2608_23441_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def ncu_traffic(name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current source of that kernel (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(name)
+    if not d or d.get("source_hash") != kernel_source_hash(name):
+        return None
+    return float(d["dram_bytes_per_launch_full_size"])
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"ipfb_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(ws):
+    if ws <= 1:
+        return None
+    import torch.distributed as dist
+    backend = "nccl"
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist, torch):
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def max_over_ranks(dist, torch, v: float) -> float:
+    if dist is None:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- CPU baseline
+ORACLE_SAMPLE_FRAMES = 8192
+
+
+def oracle_sample_step(codes, scale, window, phi2):
+    """The FP64 oracle on one bounded sample of the workload: the same lblock,
+    window and up-channelization factor, 8192 spectra (2^25 samples)."""
+    from oracle import ipfb as oipfb
+    from oracle import upchan as oup
+    x = oipfb.ipfb_wiener(codes, scale, window, phi2)
+    return oup.upchannelize(x, UPFACTOR * LBLOCK)
+
+
+def oracle_sample_inputs():
+    from oracle import pfb as opfb
+    from paper_2608_23441_b300 import synth
+    x = synth.stream_config(LBLOCK, ORACLE_SAMPLE_FRAMES, 2, ntones=16)
+    w = opfb.sinc_hamming_window(LBLOCK, NTAP).astype(np.float32).astype(np.float64)
+    codes, scale, spec = opfb.pfb_forward(x, w)
+    phi2 = float(np.var(opfb.dequantize(codes, scale) - spec) / np.var(spec))
+    return codes, scale, w, phi2
+
+
+def cpu_baseline_measure(steps: int = 1):
+    inp = oracle_sample_inputs()
+    ts = []
+    for _ in range(max(1, steps)):
+        t0 = time.perf_counter()
+        oracle_sample_step(*inp)
+        ts.append(time.perf_counter() - t0)
+    sec = statistics.median(ts)
+    value = ORACLE_SAMPLE_FRAMES * LBLOCK / sec / 1e9
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{ORACLE_SAMPLE_FRAMES} spectra x lblock {LBLOCK} (2^25 samples) of the same workload, "
+                      f"FP64 numpy oracle, single-threaded pocketfft, median of {len(ts)}",
+            "seconds_per_sample": sec}
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    inp = oracle_sample_inputs()
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_sample_step(*inp)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_sample_step(*inp)
+        ts.append(time.perf_counter() - t0)
+    total = sum(ts)
+    value = args.steps * ORACLE_SAMPLE_FRAMES * LBLOCK / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD + f" (sample: {ORACLE_SAMPLE_FRAMES} spectra per step)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{ORACLE_SAMPLE_FRAMES} spectra x lblock {LBLOCK} per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- our arm
+def make_inputs(torch, ipfb, dev):
+    from paper_2608_23441_b300 import synth
+    x = synth.stream_config(LBLOCK, NFRAMES, 2, ntones=16).astype(np.float32)
+    xg = torch.from_numpy(x).to(dev)
+    del x
+    w = torch.from_numpy(ipfb.sinc_hamming_window(LBLOCK, NTAP)).to(dev)
+    codes, scale, spec = ipfb.pfb_forward(xg, w, return_spectra=True)
+    # phi^2 = quantization noise variance / spectrum variance, from the simulation
+    # (setup only, outside the timed path)
+    s = scale.double()
+    sub = slice(0, 4096)
+    q = codes[sub]
+    lo = (q & 0xF).to(torch.int16)
+    hi = (q >> 4).to(torch.int16)
+    lo = torch.where(lo >= 8, lo - 16, lo).double()
+    hi = torch.where(hi >= 8, hi - 16, hi).double()
+    sp = spec[sub, : LBLOCK // 2]
+    err = (lo * s[: LBLOCK // 2] - sp.real.double()) ** 2 + (hi * s[: LBLOCK // 2] - sp.imag.double()) ** 2
+    err[:, 0] = (lo[:, 0] * s[0] - sp[:, 0].real.double()) ** 2
+    pw = sp.real.double() ** 2 + sp.imag.double() ** 2
+    phi2 = float(err.sum() / pw.sum())
+    del spec
+    return xg, w, codes, scale, phi2
+
+
+def run_ours(args):
+    import torch
+    from paper_2608_23441_b300 import ipfb
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(ws)
+
+    xg, w, codes, scale, phi2 = make_inputs(torch, ipfb, dev)
+    g = ipfb.geom(LBLOCK, NTAP, NFRAMES)
+    wsp = torch.empty(ipfb.workspace_size(g, ipfb.OP_WIENER_UPCHAN), dtype=torch.uint8, device=dev)
+    L = UPFACTOR * LBLOCK
+    nb = NFRAMES // UPFACTOR
+    out = torch.empty((nb, L // 2 + 1), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ipfb.ipfb_wiener_upchannelize(codes, scale, w, phi2, UPFACTOR, out=out, workspace=wsp)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region (inputs resident; every buffer > L2, so no flush needed)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ipfb.stage_timing(True)
+    with ClockSampler(local) as clk:
+        barrier(dist, torch)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier(dist, torch)
+    ms = e0.elapsed_time(e1) / args.steps
+    stages = ipfb.stage_times()
+    ipfb.stage_timing(False)
+    ms_max = max_over_ranks(dist, torch, ms)
+    launches = sum(c for _, c in stages.values())
+
+    # ---- end to end through host buffers (pinned), copies inside the timed region
+    h_codes = torch.empty(codes.shape, dtype=codes.dtype, pin_memory=True)
+    h_codes.copy_(codes)
+    h_out = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+    d_codes = torch.empty_like(codes)
+    for _ in range(2):
+        d_codes.copy_(h_codes, non_blocking=True)
+        ipfb.ipfb_wiener_upchannelize(d_codes, scale, w, phi2, UPFACTOR, out=out, workspace=wsp)
+        h_out.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(dist, torch)
+    e0.record(stream)
+    for _ in range(args.steps):
+        d_codes.copy_(h_codes, non_blocking=True)
+        ipfb.ipfb_wiener_upchannelize(d_codes, scale, w, phi2, UPFACTOR, out=out, workspace=wsp)
+        h_out.copy_(out, non_blocking=True)
+    e1.record(stream)
+    barrier(dist, torch)
+    ms_e2e = max_over_ranks(dist, torch, e0.elapsed_time(e1) / args.steps)
+
+    # ---- forward PFB (the simulation step), reported as a stage
+    fcodes = torch.empty_like(codes)
+    ipfb.stage_timing(True)
+    for _ in range(3):
+        ipfb.pfb_forward(xg, w)
+    torch.cuda.synchronize()
+    ipfb.stage_timing(True)
+    e0.record(stream)
+    nf = max(3, args.steps // 2)
+    for _ in range(nf):
+        ipfb.pfb_forward(xg, w)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fwd = e0.elapsed_time(e1) / nf
+    fstages = ipfb.stage_times()
+    ipfb.stage_timing(False)
+    del fcodes
+
+    # ---- roofline of the dominant kernel
+    peak, peak_kind = measured_peaks()
+    T = NSAMP
+    alg_bytes = {
+        "k2_unpack_irfft": T * 0.5 + T * 4.0,
+        "k3_column_wiener": T * 8.0,
+        "k4_upchan": T * 4.0 + nb * (L // 2 + 1) * 8.0,
+    }
+    per_kernel = {}
+    for k, (tot, cnt) in stages.items():
+        avg = tot / max(1, cnt)
+        ab = alg_bytes.get(k)
+        per_kernel[k] = {"avg_ms": avg, "launches": cnt, "share": tot / sum(t for t, _ in stages.values()),
+                         "alg_bytes": ab, "achieved_gbs": (ab / (avg * 1e-3) / 1e9) if ab else None}
+    dom = max(stages.items(), key=lambda kv: kv[1][0])[0]
+    dk = per_kernel[dom]
+    traffic = ncu_traffic(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": dk["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                "frac": dk["achieved_gbs"] / peak, "traffic": traffic, "peak_source": peak_kind,
+                "alg_bytes_per_launch": dk["alg_bytes"], "avg_launch_ms": dk["avg_ms"]}
+
+    value = ws * NSAMP / (ms_max * 1e-3) / 1e9
+    e2e_value = ws * NSAMP / (ms_e2e * 1e-3) / 1e9
+    pipe_bytes = T * 0.5 + nb * (L // 2 + 1) * 8.0
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (Gaussian + 16 tones, seed 2, 4-bit quantized)",
+        "config": {"workload": WORKLOAD, "lblock": LBLOCK, "ntap": NTAP, "nframes": NFRAMES,
+                   "upfactor": UPFACTOR, "noise_level": phi2, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs and outputs larger than L2 (128 MiB codes, 1 GiB scratch, 1.07 GB spectra)"},
+        "roofline": roofline,
+        "pipeline_alg_fraction": {"bytes_per_step": pipe_bytes,
+                                  "frac": pipe_bytes / (ms * 1e-3) / 1e9 / peak},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(codes.numel()),
+                "d2h_bytes_per_step": int(out.numel() * 8), "ms_per_step": ms_e2e},
+        "gpu_launches": int(launches),
+        "kernels": per_kernel,
+        "stages": {"pfb_forward_ms": ms_fwd, "pfb_forward_gsas": NSAMP / (ms_fwd * 1e-3) / 1e9,
+                   "pfb_forward_kernels": {k: {"avg_ms": t / max(1, c), "launches": c}
+                                           for k, (t, c) in fstages.items()}},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline_measure(1)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_profile_case(lblock: int, nframes: int, reps: int):
+    """A smaller case of the same pipeline for ncu captures: random 4-bit codes,
+    `reps` calls of ipfb_wiener_upchannelize (upfactor 64)."""
+    import torch
+    from paper_2608_23441_b300 import ipfb, synth
+    dev = torch.device("cuda", 0)
+    codes = torch.from_numpy(synth.random_code_bytes(nframes, lblock // 2, 1)).to(dev)
+    scale = torch.from_numpy(synth.random_scale(lblock // 2 + 1, 2)).to(dev)
+    w = torch.from_numpy(ipfb.sinc_hamming_window(lblock, NTAP)).to(dev)
+    for _ in range(reps):
+        ipfb.ipfb_wiener_upchannelize(codes, scale, w, 0.014, UPFACTOR)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": {"lblock": lblock, "nframes": nframes, "reps": reps}}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", nargs=3, type=int, metavar=("LBLOCK", "NFRAMES", "REPS"),
+                    help="run a smaller case of the pipeline (for ncu captures) and exit")
+    args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(*args.profile_case)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

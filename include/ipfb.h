@@ -1,0 +1,168 @@
+/*
+ * libipfb — circulant inverse polyphase filter bank on one B300 (sm_103a).
+ *
+ * Method: "Inverting and Up-channelizing Critically-Sampled Polyphase Filter
+ * Banks" (arXiv 2608.23441).  Section / equation names below refer to it.
+ *
+ * Conventions shared by every entry point
+ *   N = lblock (real samples per frame), p = ntap, J = nframes (spectra);
+ *   T = J*N samples; C = N/2 + 1 real-FFT channels.
+ *   DFT sign: forward exp(-2 pi i n k / N) (Sec. 2.3, operator F).
+ *   Complex arrays are interleaved float pairs (re, im), i.e. float2.
+ *   Time-ordered streams: x[j*N + n] = sample n of frame j.
+ *   Window: float [p][N], w[r][n] = h[r*N + n] (Sec. 2.3 "reshape into [p, N]").
+ *   4-bit codes: folded layout, N/2 bytes per spectrum: byte c (0 < c < N/2) =
+ *     Re_c (low nibble) | Im_c (high nibble), two's complement in [-7, 7];
+ *     byte 0 = Re_0 (low) | Re_{N/2} (high).  DC and Nyquist have no
+ *     imaginary part in a real PFB, so nothing is lost.
+ *
+ * Ownership: every array pointer is owned by the caller.  Unless stated
+ *   otherwise pointers are DEVICE pointers on the current CUDA device.  The
+ *   library allocates no device memory: scratch comes from the caller (size
+ *   from ipfb_workspace_size), 256-byte aligned.
+ * Execution: every compute call is asynchronous on `stream` (a cudaStream_t
+ *   passed as void*; NULL = legacy default stream).  Host-side argument checks
+ *   run before anything is enqueued.
+ * Errors: 0 on success, a negative IPFB_ERR_* code otherwise; nothing is
+ *   enqueued when a check fails.  A launch failure returns IPFB_ERR_CUDA and
+ *   the CUDA error string is available from ipfb_last_cuda_error().
+ */
+#ifndef IPFB_H
+#define IPFB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IPFB_OK 0
+#define IPFB_ERR_INVALID (-1)       /* null pointer, bad size, bad flag          */
+#define IPFB_ERR_UNSUPPORTED (-2)   /* valid, but outside the built kernel range */
+#define IPFB_ERR_WORKSPACE (-3)     /* workspace smaller than required           */
+#define IPFB_ERR_NOT_CONVERGED (-4) /* iterative solve hit max_iter              */
+#define IPFB_ERR_TIMEOUT (-5)       /* a bounded device wait gave up             */
+#define IPFB_ERR_CUDA (-6)          /* a CUDA runtime call failed                */
+
+/* operation ids for ipfb_workspace_size */
+#define IPFB_OP_FORWARD 1
+#define IPFB_OP_WIENER 2
+#define IPFB_OP_WIENER_UPCHAN 3
+#define IPFB_OP_ML 4
+
+typedef struct {
+  int lblock;   /* N: power of two, 32 <= N <= 16384                              */
+  int ntap;     /* p: 1 <= p <= 16                                                 */
+  int nframes;  /* J: spectra (= input frames for a periodic PFB); power of two,
+                   16 <= J <= 65536 for the inverse                               */
+  int periodic; /* 1: spectrum j uses frames j..j+p-1 mod J (the circulant model) */
+} ipfb_geom;
+
+/* Human-readable text for a status code (static storage). */
+const char* ipfb_strerror(int status);
+/* Text of the last CUDA error seen by this library in this thread ("" if none). */
+const char* ipfb_last_cuda_error(void);
+/* Library ABI version (major*100 + minor). */
+int ipfb_version(void);
+
+/*
+ * Testing knob (no counterpart in the paper): the longest run of frames one CTA
+ * transforms along a column (8192 by default; 512 is also accepted).  Columns
+ * longer than the run are split over a thread-block cluster of up to 8 CTAs, so
+ * a small run exercises the cluster path on small inputs.  Process-wide.
+ */
+int ipfb_set_max_column_run(int frames);
+
+/*
+ * Stage timing (no counterpart in the paper).  ipfb_stage_timing(1) clears the
+ * record and starts bracketing every kernel launch of every compute call with two
+ * CUDA events on that call's stream; ipfb_stage_timing(0) clears and stops.
+ * ipfb_stage_times waits for the recorded events and writes, per kernel name, the
+ * summed milliseconds and the launch count: names_csv receives the names in
+ * order, comma separated (HOST buffer of names_cap bytes); ms / counts are HOST
+ * arrays of max_entries.  Returns the number of names (>= 0) or an error code.
+ */
+int ipfb_stage_timing(int enable);
+int ipfb_stage_times(char* names_csv, size_t names_cap, double* ms, int* counts, int max_entries);
+
+/* Bytes of device scratch needed by operation `op` for geometry g (0 if none). */
+int ipfb_workspace_size(const ipfb_geom* g, int op, size_t* bytes);
+
+/*
+ * Sinc x Hamming PFB window (Sec. 2.2, Eq. chan_dft read as sinc((m - M/2)/N);
+ * App. A: Hamming with the cos(2 pi m/(M-1)) normalisation), M = ntap*lblock:
+ *   w[m] = sinc((m - M/2)/N) * (0.54 - 0.46 cos(2 pi m / (M - 1))).
+ * Computed on the host in double, rounded to float.  window_host: HOST float [M].
+ */
+int ipfb_sinc_hamming_window(int lblock, int ntap, float* window_host);
+
+/*
+ * Forward critically-sampled PFB with 4-bit quantization (Eq. pfb; Sec. 4.3).
+ *   d[j, n] = sum_{r<p} w[r][n] x[((j + r) mod J) N + n]        (periodic)
+ *   Y[j, c] = sum_n d[j, n] exp(-2 pi i n c / N),   c <= N/2
+ *   scale_c = RMS_c / 2.5 with RMS_c over the real and imaginary parts of
+ *     channel c (DC, Nyquist: real parts only), accumulated in FP64, rounded
+ *     once to float; used as given when scale_in != NULL.
+ *   code = clamp(rint(v / scale_c), -7, 7) on Re and Im (float32 IEEE divide,
+ *     round half to even; scale 0 gives code 0).
+ * x: float [J*N]; window: float [p][N]; scale_in: float [C] or NULL;
+ * codes: uint8 [J][N/2] (folded); scale_out: float [C] (may equal scale_in);
+ * spectra_out: float2 [J][C] or NULL.  Only periodic = 1 is supported.
+ */
+int pfb_forward(const ipfb_geom* g, const float* x, const float* window, const float* scale_in,
+                uint8_t* codes, float* scale_out, float* spectra_out, void* ws, size_t ws_bytes,
+                void* stream);
+
+/*
+ * The quantize-and-pack step alone (Sec. 4.3 quantizer) on given spectra:
+ * spectra: float2 [nspec][lblock/2 + 1]; scale: float [lblock/2 + 1];
+ * codes: uint8 [nspec][lblock/2].  Same decision rule as pfb_forward.
+ */
+int pfb_quantize(int lblock, int nspec, const float* spectra, const float* scale, uint8_t* codes,
+                 void* stream);
+
+/*
+ * Circulant inverse PFB with Wiener filtering (Sec. 3.1 Eq. decorrelation,
+ * Sec. 4.1 Eq. wiener weights, App. C):
+ *   d = N-point inverse real FFT of (codes x scale) per spectrum  ("undo F")
+ *   per column n: D_n = FFT_J(d[:, n]); W_n(k) = sum_r w[r][n] e^{-2 pi i r k/J}
+ *   x_hat_n = IFFT_J( G D_n ),  G = W_n (1 + phi^2) / (|W_n|^2 + phi^2)
+ *   (= H_n / conj(W_n)); noise_level = phi^2 (= N/S); noise_level = 0 is the
+ *   exact inverse 1/conj(W_n) (modes with W_n == 0 exactly are dropped).
+ *   normalize = 0 drops the optional (1 + phi^2) factor.
+ * codes: uint8 [J][N/2]; scale: float [C]; window: float [p][N];
+ * x_out: float [J*N], time order.  Requires periodic = 1 (J spectra -> J frames).
+ * Workspace: ipfb_workspace_size(g, IPFB_OP_WIENER).
+ */
+int ipfb_wiener(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
+                double noise_level, int normalize, float* x_out, void* ws, size_t ws_bytes,
+                void* stream);
+
+/*
+ * Up-channelization (Sec. 4.3, re-channelization with frames `block` samples
+ * long; read here as a plain real DFT of consecutive blocks, no window):
+ *   X_b[c] = sum_{t<L} x[b L + t] exp(-2 pi i t c / L),  c <= L/2,
+ *   b < floor(nsamples / L); a trailing partial block is ignored.
+ * x: float [nsamples] time order; out: float2 [nsamples/L][L/2 + 1].
+ * L: power of two, 1024 <= L <= 262144.
+ */
+int upchannelize(const float* x, int64_t nsamples, int64_t block, float* out, void* ws,
+                 size_t ws_bytes, void* stream);
+
+/*
+ * ipfb_wiener followed by upchannelize with block = upfactor * lblock, without
+ * a round trip of the reconstructed stream through time order.  x_out (time
+ * order) is optional (NULL = not written).  out: float2 [J/upfactor][L/2 + 1].
+ * Workspace: ipfb_workspace_size(g, IPFB_OP_WIENER_UPCHAN).
+ */
+int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const float* scale,
+                             const float* window, double noise_level, int normalize,
+                             int upfactor, float* out, float* x_out, void* ws, size_t ws_bytes,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IPFB_H */

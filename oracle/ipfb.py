@@ -48,7 +48,11 @@ def gain(W: np.ndarray, noise_level: float, normalize: bool = True) -> np.ndarra
     Eq. wiener weights): W (1 + phi^2) / (|W|^2 + phi^2); phi^2 = 0 gives 1/W^*."""
     phi2 = float(noise_level)
     if phi2 == 0.0:
-        return 1.0 / np.conj(W)
+        # exact inverse; a mode with W == 0 exactly carries no information and is
+        # dropped (the truncated pseudo-inverse of Sec. 4.2.2)
+        Wc = np.conj(W)
+        safe = np.where(Wc == 0, 1.0, Wc)
+        return np.where(Wc == 0, 0.0, 1.0 / safe)
     norm = (1.0 + phi2) if normalize else 1.0
     return W * norm / (np.abs(W) ** 2 + phi2)
 
@@ -110,6 +114,33 @@ def ipfb_column(codes: np.ndarray, scale: np.ndarray, window: np.ndarray, n: int
     Wn = eigenvalues(window[:, n:n + 1], J)[:, 0]
     G = gain(Wn, noise_level, normalize)
     return np.real(np.fft.ifft(G * Dn))
+
+
+def ipfb_columns(codes: np.ndarray, scale: np.ndarray, window: np.ndarray, ns,
+                 noise_level: float, normalize: bool = True, chunk: int = 4096) -> np.ndarray:
+    """Columns ns of the reconstruction, [J, len(ns)], evaluating step 1 only at the
+    requested indices (in chunks of spectra, so full-size inputs stay cheap)."""
+    from .pfb import unpack_codes
+    p, N = window.shape
+    ns = np.asarray(ns, dtype=np.int64)
+    J, half = codes.shape
+    C = half + 1
+    c = np.arange(C, dtype=np.int64)
+    wt = np.full(C, 2.0)
+    wt[0] = 1.0
+    wt[C - 1] = 1.0
+    ph = np.exp(2j * np.pi * ((np.outer(c, ns)) % N).astype(np.float64) / N) * wt[:, None]  # [C, k]
+    s = np.asarray(scale, dtype=np.float32).astype(np.float64)
+    d = np.empty((J, ns.shape[0]))
+    for j0 in range(0, J, chunk):
+        q_re, q_im = unpack_codes(codes[j0:j0 + chunk])
+        Y = (q_re.astype(np.float64) + 1j * q_im.astype(np.float64)) * s[None, :]
+        d[j0:j0 + chunk] = np.real(Y @ ph) / N
+    out = np.empty_like(d)
+    for i, n in enumerate(ns):
+        Wn = eigenvalues(window[:, n:n + 1], J)[:, 0]
+        out[:, i] = np.real(np.fft.ifft(gain(Wn, noise_level, normalize) * np.fft.fft(d[:, i])))
+    return out
 
 
 # --------------------------------------------------------------------------- #

@@ -1,0 +1,345 @@
+// libipfb C ABI: argument checks, workspace sizing, kernel dispatch.
+// Declarations and the meaning of every argument: include/ipfb.h.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ipfb.h"
+#include "launch.h"
+
+using namespace ipfb;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+std::atomic<int> g_max_column_run{8192};
+
+// ---------------------------------------------------------------- stage timing
+// When enabled, every kernel launch of a compute call is bracketed by two CUDA
+// events recorded on the call's stream; ipfb_stage_times sums their elapsed times.
+struct StageRec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+std::mutex g_tmu;
+bool g_timing = false;
+std::vector<StageRec> g_recs;
+std::vector<cudaEvent_t> g_pool;
+
+cudaEvent_t pool_get() {
+  if (!g_pool.empty()) {
+    cudaEvent_t e = g_pool.back();
+    g_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+struct Stage {
+  const char* name;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  Stage(const char* n, cudaStream_t s) : name(n), st(s) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    if (g_timing) {
+      a = pool_get();
+      if (a) cudaEventRecord(a, st);
+    }
+  }
+  void done() {
+    if (!a) return;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    cudaEvent_t b = pool_get();
+    if (!b) return;
+    cudaEventRecord(b, st);
+    g_recs.push_back({name, a, b});
+    a = nullptr;
+  }
+};
+
+int cuda_fail(cudaError_t e, const char* where) {
+  if (e == cudaErrorNotSupported) return IPFB_ERR_UNSUPPORTED;
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", where, cudaGetErrorString(e));
+  return IPFB_ERR_CUDA;
+}
+
+#define CK(call, where)                                 \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+constexpr int kMaxTapsAbi = 16;
+
+int check_geom(const ipfb_geom* g, bool need_inverse) {
+  if (!g) return IPFB_ERR_INVALID;
+  if (g->lblock < 2 || g->ntap < 1 || g->nframes < 1) return IPFB_ERR_INVALID;
+  if (!is_pow2(g->lblock) || g->lblock < 64 || g->lblock > 16384) return IPFB_ERR_UNSUPPORTED;
+  if (g->ntap > kMaxTapsAbi) return IPFB_ERR_UNSUPPORTED;
+  if (g->periodic != 1) return IPFB_ERR_UNSUPPORTED;
+  if (need_inverse) {
+    if (!is_pow2(g->nframes) || g->nframes < 16 || g->nframes > 65536) return IPFB_ERR_UNSUPPORTED;
+  }
+  return IPFB_OK;
+}
+
+// column cluster split of J frames: C CTAs of S = J/C frames each (S <= max run)
+void column_split(int J, int* C, int* S) {
+  int c = 1;
+  const int lim = g_max_column_run.load();
+  while (J / c > lim && c < 8) c *= 2;
+  *C = c;
+  *S = J / c;
+}
+
+int run_inverse_core(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
+                     double noise_level, int normalize, float2* d2, int C, int S, cudaStream_t st) {
+  const int N = g->lblock, J = g->nframes, H = N / 2;
+  {
+    Stage t("k2_unpack_irfft", st);
+    CK(launch_k2(H, codes, scale, d2, C, S, st), "k2_unpack_irfft");
+    t.done();
+  }
+  GainParams gp;
+  gp.phi2 = (float)noise_level;
+  gp.gnorm = (noise_level > 0.0 && normalize) ? (float)(1.0 + noise_level) : 1.0f;
+  gp.invJ = 1.0f / (float)J;
+  gp.J = J;
+  gp.ntap = g->ntap;
+  Stage t("k3_column_wiener", st);
+  CK(launch_k3(C, S, d2, window, N, gp, st), "k3_column_wiener");
+  t.done();
+  return IPFB_OK;
+}
+
+int check_noise(double noise_level) {
+  if (!(noise_level >= 0.0) || !std::isfinite(noise_level)) return IPFB_ERR_INVALID;
+  return IPFB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ipfb_strerror(int status) {
+  switch (status) {
+    case IPFB_OK: return "ok";
+    case IPFB_ERR_INVALID: return "invalid argument";
+    case IPFB_ERR_UNSUPPORTED: return "unsupported size or option";
+    case IPFB_ERR_WORKSPACE: return "workspace too small";
+    case IPFB_ERR_NOT_CONVERGED: return "iterative solve did not converge";
+    case IPFB_ERR_TIMEOUT: return "bounded device wait timed out";
+    case IPFB_ERR_CUDA: return "CUDA runtime error";
+  }
+  return "unknown status";
+}
+
+const char* ipfb_last_cuda_error(void) { return g_cuda_err; }
+
+int ipfb_version(void) { return 100; }
+
+int ipfb_stage_timing(int enable) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  for (auto& r : g_recs) {
+    g_pool.push_back(r.a);
+    g_pool.push_back(r.b);
+  }
+  g_recs.clear();
+  g_timing = enable != 0;
+  return IPFB_OK;
+}
+
+int ipfb_stage_times(char* names, size_t names_cap, double* ms, int* counts, int max_entries) {
+  if (!names || !ms || !counts || max_entries < 1 || names_cap < 1) return IPFB_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_tmu);
+  std::vector<std::string> keys;
+  std::vector<double> tot;
+  std::vector<int> cnt;
+  for (auto& r : g_recs) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaEventSynchronize");
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return cuda_fail(cudaGetLastError(), "elapsed");
+    size_t i = 0;
+    for (; i < keys.size(); ++i)
+      if (keys[i] == r.name) break;
+    if (i == keys.size()) {
+      keys.push_back(r.name);
+      tot.push_back(0.0);
+      cnt.push_back(0);
+    }
+    tot[i] += t;
+    cnt[i] += 1;
+  }
+  std::string csv;
+  int n = 0;
+  for (size_t i = 0; i < keys.size() && n < max_entries; ++i, ++n) {
+    if (i) csv += ",";
+    csv += keys[i];
+    ms[i] = tot[i];
+    counts[i] = cnt[i];
+  }
+  if (csv.size() + 1 > names_cap) return IPFB_ERR_INVALID;
+  std::memcpy(names, csv.c_str(), csv.size() + 1);
+  return n;
+}
+
+int ipfb_set_max_column_run(int frames) {
+  if (frames != 512 && frames != 8192) return IPFB_ERR_INVALID;
+  g_max_column_run.store(frames);
+  return IPFB_OK;
+}
+
+int ipfb_workspace_size(const ipfb_geom* g, int op, size_t* bytes) {
+  if (!bytes) return IPFB_ERR_INVALID;
+  *bytes = 0;
+  int rc;
+  switch (op) {
+    case IPFB_OP_FORWARD:
+      rc = check_geom(g, false);
+      if (rc) return rc;
+      *bytes = 2 * (size_t)(g->lblock / 2 + 1) * sizeof(double);
+      return IPFB_OK;
+    case IPFB_OP_WIENER:
+    case IPFB_OP_WIENER_UPCHAN:
+    case IPFB_OP_ML:
+      rc = check_geom(g, true);
+      if (rc) return rc;
+      *bytes = (size_t)g->nframes * (size_t)g->lblock * sizeof(float);
+      return IPFB_OK;
+  }
+  return IPFB_ERR_INVALID;
+}
+
+int ipfb_sinc_hamming_window(int lblock, int ntap, float* window_host) {
+  if (!window_host || lblock < 1 || ntap < 1) return IPFB_ERR_INVALID;
+  const long long M = (long long)lblock * ntap;
+  const double pi = 3.14159265358979323846;
+  for (long long m = 0; m < M; ++m) {
+    const double t = ((double)m - (double)M / 2.0) / (double)lblock;
+    const double sinc = (t == 0.0) ? 1.0 : std::sin(pi * t) / (pi * t);
+    const double taper = (M > 1) ? 0.54 - 0.46 * std::cos(2.0 * pi * (double)m / (double)(M - 1)) : 1.0;
+    window_host[m] = (float)(sinc * taper);
+  }
+  return IPFB_OK;
+}
+
+int pfb_quantize(int lblock, int nspec, const float* spectra, const float* scale, uint8_t* codes,
+                 void* stream) {
+  if (!spectra || !scale || !codes || nspec < 0 || lblock < 4 || (lblock & 1)) return IPFB_ERR_INVALID;
+  if (nspec == 0) return IPFB_OK;
+  Stage t("k_quantize", as_stream(stream));
+  CK(launch_quantize(lblock / 2, nspec, reinterpret_cast<const float2*>(spectra), scale, codes,
+                     as_stream(stream)),
+     "k_quantize");
+  t.done();
+  return IPFB_OK;
+}
+
+int pfb_forward(const ipfb_geom* g, const float* x, const float* window, const float* scale_in, uint8_t* codes,
+                float* scale_out, float* spectra_out, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_geom(g, false);
+  if (rc) return rc;
+  if (!x || !window || !codes || !scale_out) return IPFB_ERR_INVALID;
+  const int H = g->lblock / 2, J = g->nframes;
+  cudaStream_t st = as_stream(stream);
+  if (!scale_in) {
+    size_t need = 0;
+    ipfb_workspace_size(g, IPFB_OP_FORWARD, &need);
+    if (!ws || ws_bytes < need) return IPFB_ERR_WORKSPACE;
+    double* sums = reinterpret_cast<double*>(ws);
+    CK(cudaMemsetAsync(sums, 0, need, st), "cudaMemsetAsync");
+    Stage t1("k1_pfb_power", st);
+    CK(launch_k1_power(H, x, window, g->ntap, J, sums, st), "k1_pfb_power");
+    t1.done();
+    Stage t2("k1_scale_from_sums", st);
+    CK(launch_k1_scale(H, J, sums, scale_out, st), "k1_scale_from_sums");
+    t2.done();
+  } else if (scale_out != scale_in) {
+    CK(cudaMemcpyAsync(scale_out, scale_in, (size_t)(H + 1) * sizeof(float), cudaMemcpyDeviceToDevice, st),
+       "cudaMemcpyAsync");
+  }
+  Stage t3("k1_pfb_quant", st);
+  CK(launch_k1_quant(H, x, window, g->ntap, J, scale_out, codes, reinterpret_cast<float2*>(spectra_out), st),
+     "k1_pfb_quant");
+  t3.done();
+  return IPFB_OK;
+}
+
+int ipfb_wiener(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
+                double noise_level, int normalize, float* x_out, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_geom(g, true);
+  if (rc) return rc;
+  if (!codes || !scale || !window || !x_out) return IPFB_ERR_INVALID;
+  if ((rc = check_noise(noise_level))) return rc;
+  size_t need = 0;
+  ipfb_workspace_size(g, IPFB_OP_WIENER, &need);
+  if (!ws || ws_bytes < need) return IPFB_ERR_WORKSPACE;
+  cudaStream_t st = as_stream(stream);
+  float2* d2 = reinterpret_cast<float2*>(ws);
+  int C, S;
+  column_split(g->nframes, &C, &S);
+  rc = run_inverse_core(g, codes, scale, window, noise_level, normalize, d2, C, S, st);
+  if (rc) return rc;
+  Stage t("k_pairs_to_time", st);
+  CK(launch_pairs_to_time(d2, x_out, g->lblock, C, S, st), "k_pairs_to_time");
+  t.done();
+  return IPFB_OK;
+}
+
+int upchannelize(const float* x, int64_t nsamples, int64_t block, float* out, void* ws, size_t ws_bytes,
+                 void* stream) {
+  (void)ws;
+  (void)ws_bytes;
+  if (!x || !out || nsamples < 0 || block < 2) return IPFB_ERR_INVALID;
+  if (!is_pow2(block) || block < 1024 || block > 262144) return IPFB_ERR_UNSUPPORTED;
+  const long long nb = nsamples / block;
+  if (nb == 0) return IPFB_OK;
+  UpchanSrc src{x, nullptr, 0, 0, 0};
+  Stage t("k4_upchan", as_stream(stream));
+  CK(launch_upchan(src, (int)block, nb, reinterpret_cast<float2*>(out), nullptr, as_stream(stream)), "k4_upchan");
+  t.done();
+  return IPFB_OK;
+}
+
+int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
+                             double noise_level, int normalize, int upfactor, float* out, float* x_out, void* ws,
+                             size_t ws_bytes, void* stream) {
+  int rc = check_geom(g, true);
+  if (rc) return rc;
+  if (!codes || !scale || !window || !out) return IPFB_ERR_INVALID;
+  if ((rc = check_noise(noise_level))) return rc;
+  if (upfactor < 1 || !is_pow2(upfactor)) return IPFB_ERR_UNSUPPORTED;
+  const long long L = (long long)upfactor * g->lblock;
+  if (L < 1024 || L > 262144) return IPFB_ERR_UNSUPPORTED;
+  size_t need = 0;
+  ipfb_workspace_size(g, IPFB_OP_WIENER_UPCHAN, &need);
+  if (!ws || ws_bytes < need) return IPFB_ERR_WORKSPACE;
+  cudaStream_t st = as_stream(stream);
+  float2* d2 = reinterpret_cast<float2*>(ws);
+  int C, S;
+  column_split(g->nframes, &C, &S);
+  if (upfactor % C) return IPFB_ERR_UNSUPPORTED;
+  rc = run_inverse_core(g, codes, scale, window, noise_level, normalize, d2, C, S, st);
+  if (rc) return rc;
+  const long long nb = (long long)g->nframes / upfactor;
+  if (nb == 0) return IPFB_OK;
+  UpchanSrc src{nullptr, d2, g->lblock, C, S};
+  Stage t("k4_upchan", st);
+  CK(launch_upchan(src, (int)L, nb, reinterpret_cast<float2*>(out), x_out, st), "k4_upchan");
+  t.done();
+  return IPFB_OK;
+}
+
+}  // extern "C"

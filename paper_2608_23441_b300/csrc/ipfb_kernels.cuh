@@ -1,0 +1,302 @@
+// Inverse-PFB kernels (Sec. 3.1, Sec. 4.1, App. C).
+//
+// Scratch layout "d2" (column-pair, residue-major), shared by the iPFB, the ML
+// solve and the up-channelizer:  columns 2p and 2p+1 of the [J, N] polyphase
+// array are packed as one complex sequence z_p[j] = d[j, 2p] + i d[j, 2p+1];
+// with J = C*S (C = CTAs per column cluster) frame j = C*m + r is stored at
+//     d2[(p*C + r)*S + m]          (float2)
+// so each of the C CTAs that transform column pair p reads and writes one
+// contiguous S-element run.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace ipfb {
+namespace cg = cooperative_groups;
+
+// ----------------------------------------------------------------------------
+// K2: 4-bit unpack x scale  ->  N-point inverse real FFT per spectrum ("undoing F")
+// ----------------------------------------------------------------------------
+// One CTA inverts F spectra j = C*m + r, m in [m0, m0+F), with TPF threads per
+// spectrum.  The real inverse FFT of length N = 2H runs as an H-point complex
+// inverse FFT of Z[k] = E[k] + i O[k] with
+//     E[k] = (Y[k] + conj Y[H-k]) / 2,  O[k] = (Y[k] - conj Y[H-k]) e^{+2 pi i k/N} / 2,
+// so that z[m] = x[2m] + i x[2m+1] -- exactly the column-pair value of pair m.
+// The 1/H normalisation is folded into the pre-scale.
+template <int H, int TPF, int F>
+__global__ void __launch_bounds__(TPF* F)
+k2_unpack_irfft(const uint8_t* __restrict__ codes, const float* __restrict__ scale,
+                float2* __restrict__ d2, int C, int S) {
+  extern __shared__ float2 smem[];
+  const int f = threadIdx.x / TPF;
+  const int tid = threadIdx.x % TPF;
+  float2* sm = smem + f * padded_len(H);
+  const int per_res = S / F;
+  const int r = blockIdx.x / per_res;
+  const int m0 = (blockIdx.x % per_res) * F;
+  const int j = C * (m0 + f) + r;
+  const uint8_t* row = codes + (size_t)j * H;
+  const float pre = 0.5f / (float)H;
+
+  // pre-processing: each thread forms Z[k] and Z[H-k] for k in [0, H/2]
+  for (int k = tid; k <= H / 2; k += TPF) {
+    const int km = H - k;  // == H for k == 0 (Nyquist lives in byte 0's high nibble)
+    const uint8_t bk = row[k];
+    const uint8_t bm = row[km == H ? 0 : km];
+    auto nib = [](uint8_t v, int hi) -> float {
+      int q = hi ? (v >> 4) : (v & 0xF);
+      return (float)((q ^ 8) - 8);
+    };
+    float2 yk, ym;
+    if (k == 0) {
+      yk = make_float2(nib(bk, 0) * scale[0], 0.0f);
+      ym = make_float2(nib(bk, 1) * scale[H], 0.0f);
+    } else {
+      yk = make_float2(nib(bk, 0) * scale[k], nib(bk, 1) * scale[k]);
+      ym = make_float2(nib(bm, 0) * scale[km], nib(bm, 1) * scale[km]);
+    }
+    // E, O at k:   E = (yk + conj ym)/2, O = (yk - conj ym) w/2, w = e^{+2 pi i k/N}
+    const float2 w = twiddle<true>(k, 2 * H);
+    const float2 e = cadd(yk, cconj(ym));
+    const float2 o = cmul(csub(yk, cconj(ym)), w);
+    const float2 zk = cscale(cadd(e, cmul_i(o)), pre);
+    // at H-k: E' = conj(E), O' = (ym - conj yk) w', w' = e^{+2 pi i (H-k)/N} = -conj(w)
+    const float2 e2 = cconj(e);
+    const float2 o2 = cmul(csub(ym, cconj(yk)), make_float2(-w.x, w.y));
+    const float2 zm = cscale(cadd(e2, cmul_i(o2)), pre);
+    sm[pidx(k)] = zk;
+    if (k != 0 && km != k) sm[pidx(km)] = zm;
+  }
+  __syncthreads();
+  auto lds = [sm](int i) { return sm[pidx(i)]; };
+  auto sts = [sm](int i, float2 v) { sm[pidx(i)] = v; };
+  block_fft<H, TPF, true>(sm, tid, lds, sts);
+  __syncthreads();
+  // transposed store: for each pair p, F consecutive m of residue r
+  for (int idx = threadIdx.x; idx < H * F; idx += TPF * F) {
+    const int p = idx / F, ff = idx % F;
+    d2[((size_t)p * C + r) * S + m0 + ff] = smem[ff * padded_len(H) + pidx(p)];
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Gain per frame-axis mode (Eq. decorrelation with Eq. wiener weights):
+//   W_n(k) = sum_t w[t, n] e^{-2 pi i t k / J}
+//   G = W gnorm / (|W|^2 + phi^2) / J      (phi^2 = 0, gnorm = 1: 1/conj(W) / J)
+// |W|^2 below kFp64Below is recomputed in FP64 (near-zero eigenvalues, App. A).
+// An exactly zero denominator gives G = 0 (the mode is dropped).
+// ----------------------------------------------------------------------------
+constexpr float kFp64Below = 1e-4f;
+constexpr int kMaxTaps = 16;
+
+__device__ __forceinline__ float2 gain_at(const float* taps, int k, float2 e1, const GainParams& gp) {
+  // Horner in e1 = e^{-2 pi i k/J}; the loop is unrolled to kMaxTaps so the taps stay
+  // in registers (ntap is uniform across the CTA, so the guard does not diverge)
+  float2 W = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int t = kMaxTaps - 1; t >= 0; --t) {
+    if (t < gp.ntap) {
+      W = cmul(W, e1);
+      W.x += taps[t];
+    }
+  }
+  float a2 = fmaf(W.x, W.x, W.y * W.y);
+  if (a2 < kFp64Below) {
+    double s, c;
+    sincospi(2.0 * (double)k / (double)gp.J, &s, &c);
+    double wx = 0.0, wy = 0.0;
+#pragma unroll
+    for (int t = kMaxTaps - 1; t >= 0; --t) {
+      if (t < gp.ntap) {
+        const double nx = wx * c + wy * s;  // (wx + i wy)(c - i s)
+        const double ny = wy * c - wx * s;
+        wx = nx + (double)taps[t];
+        wy = ny;
+      }
+    }
+    const double den = wx * wx + wy * wy + (double)gp.phi2;
+    if (den == 0.0) return make_float2(0.0f, 0.0f);
+    const double g = (double)gp.gnorm * (double)gp.invJ / den;
+    return make_float2((float)(wx * g), (float)(wy * g));
+  }
+  const float g = gp.gnorm * gp.invJ / (a2 + gp.phi2);
+  return make_float2(W.x * g, W.y * g);
+}
+
+// Column-pair split, per-column gain, recombination for modes k and -k:
+//   A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i)      (spectra of columns a, b)
+//   Z'_k = Ga A + i Gb B,   Z'_-k = conj(Ga A) + i conj(Gb B)
+__device__ __forceinline__ void split_gain(float2& zk, float2& zm, float2 ga, float2 gb) {
+  const float2 A = cscale(cadd(zk, cconj(zm)), 0.5f);
+  const float2 d = csub(zk, cconj(zm));
+  const float2 B = make_float2(0.5f * d.y, -0.5f * d.x);
+  const float2 ya = cmul(ga, A), yb = cmul(gb, B);
+  zk = cadd(ya, cmul_i(yb));
+  zm = cadd(cconj(ya), cmul_i(cconj(yb)));
+}
+
+// ----------------------------------------------------------------------------
+// K3: per column pair: FFT_J along frames -> gain -> inverse FFT_J, in place on d2.
+// A cluster of C CTAs handles one pair; CTA r owns z[C m + r], m < S.
+//   1. local S-point FFT:      U_r[kb] = sum_m z[Cm + r] e^{-2 pi i m kb / S}
+//   2. cross stage (DSMEM):    Z[kb + S ka] = sum_r e^{-2 pi i r ka / C} e^{-2 pi i r kb/J} U_r[kb]
+//   3. gains on modes k and -k; -k of (kb, ka) is (S-kb, C-1-ka) (kb != 0), so one
+//      thread owns both and nothing crosses CTAs between 2 and 4
+//   4. inverse cross stage, pushed back to the owners, then local inverse FFT.
+// ----------------------------------------------------------------------------
+template <int C, int S, int T>
+__global__ void __launch_bounds__(T)
+k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int N, GainParams gp) {
+  extern __shared__ float2 sm[];
+  const int tid = threadIdx.x;
+  const int p = blockIdx.x / C;
+  int r = 0;
+  if constexpr (C > 1) r = (int)cg::this_cluster().block_rank();
+  float2* base = d2 + ((size_t)p * C + r) * S;
+  const int J = C * S;
+
+  float ta[kMaxTaps], tb[kMaxTaps];
+#pragma unroll
+  for (int t = 0; t < kMaxTaps; ++t) {
+    ta[t] = (t < gp.ntap) ? __ldg(window + (size_t)t * N + 2 * p) : 0.0f;
+    tb[t] = (t < gp.ntap) ? __ldg(window + (size_t)t * N + 2 * p + 1) : 0.0f;
+  }
+
+  auto ldg = [base](int i) { return base[i]; };
+  auto lds = [](int i) { return sm[pidx(i)]; };
+  auto sts = [](int i, float2 v) { sm[pidx(i)] = v; };
+  auto stg = [base](int i, float2 v) { base[i] = v; };
+
+  // 1. forward local FFT: global -> smem
+  block_fft<S, T, false>(sm, tid, ldg, sts);
+  if constexpr (C > 1) {
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+
+  float2* peer[C];
+#pragma unroll
+  for (int q = 0; q < C; ++q) {
+    if constexpr (C > 1)
+      peer[q] = cg::this_cluster().map_shared_rank(sm, q);
+    else
+      peer[q] = sm;
+  }
+
+  // 2-4. tasks: t = 0 (kb = 0), t = S/2 (kb = S/2), else the pair (t, S - t)
+  for (int t = r * T + tid; t <= S / 2; t += C * T) {
+    const bool pairtask = (t != 0) && (2 * t != S);
+    const int kb0 = t, kb1 = S - t;
+    float2 z0[C], z1[C];
+    float2 w0[C], w1[C];
+    // gather + cross-stage twiddle + C-point DFT over r
+    if constexpr (C > 1) {
+      twiddle_powers<C>(twiddle<false>(kb0, J), w0);
+      if (pairtask) twiddle_powers<C>(twiddle<false>(kb1, J), w1);
+    }
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+      z0[q] = peer[q][pidx(kb0)];
+      if (pairtask) z1[q] = peer[q][pidx(kb1)];
+    }
+    if constexpr (C > 1) {
+#pragma unroll
+      for (int q = 1; q < C; ++q) {
+        z0[q] = cmul(z0[q], w0[q]);
+        if (pairtask) z1[q] = cmul(z1[q], w1[q]);
+      }
+      DFT<C, false>::run(z0);
+      if (pairtask) DFT<C, false>::run(z1);
+    }
+    // gains: z0[ka] is mode kb0 + S*ka
+    if (pairtask) {
+#pragma unroll
+      for (int ka = 0; ka < C; ++ka) {
+        const int k = kb0 + S * ka;
+        const float2 e1 = twiddle<false>(k, J);
+        const float2 ga = gain_at(ta, k, e1, gp), gb = gain_at(tb, k, e1, gp);
+        split_gain(z0[ka], z1[C - 1 - ka], ga, gb);
+      }
+    } else if (t == 0) {
+      // modes S*ka; -k is S*((C-ka) mod C)
+#pragma unroll
+      for (int ka = 0; ka <= C / 2; ++ka) {
+        const int km = (C - ka) % C;
+        const int k = S * ka;
+        const float2 e1 = twiddle<false>(k, J);
+        const float2 ga = gain_at(ta, k, e1, gp), gb = gain_at(tb, k, e1, gp);
+        float2 a = z0[ka], b = z0[km];
+        split_gain(a, b, ga, gb);
+        z0[ka] = a;
+        if (km != ka) z0[km] = b;
+      }
+    } else {
+      // kb = S/2: modes S/2 + S*ka; -k is S/2 + S*(C-1-ka)
+#pragma unroll
+      for (int ka = 0; ka < (C + 1) / 2; ++ka) {
+        const int km = C - 1 - ka;
+        const int k = kb0 + S * ka;
+        const float2 e1 = twiddle<false>(k, J);
+        const float2 ga = gain_at(ta, k, e1, gp), gb = gain_at(tb, k, e1, gp);
+        float2 a = z0[ka], b = z0[km];
+        split_gain(a, b, ga, gb);
+        z0[ka] = a;
+        if (km != ka) z0[km] = b;
+      }
+    }
+    // inverse C-point DFT over ka, conj twiddle, push back to owner q
+    if constexpr (C > 1) {
+      DFT<C, true>::run(z0);
+      if (pairtask) DFT<C, true>::run(z1);
+#pragma unroll
+      for (int q = 1; q < C; ++q) {
+        z0[q] = cmul(z0[q], cconj(w0[q]));
+        if (pairtask) z1[q] = cmul(z1[q], cconj(w1[q]));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+      peer[q][pidx(kb0)] = z0[q];
+      if (pairtask) peer[q][pidx(kb1)] = z1[q];
+    }
+  }
+  if constexpr (C > 1) {
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+  // 4. inverse local FFT: smem -> global (in place over this CTA's input run)
+  block_fft<S, T, true>(sm, tid, lds, stg);
+}
+
+// ----------------------------------------------------------------------------
+// d2 (column-pair, residue-major) -> time-ordered x[j*N + n]
+// Tile: TJ consecutive frames x 32 pairs.
+// ----------------------------------------------------------------------------
+template <int TJ>
+__global__ void __launch_bounds__(256)
+k_pairs_to_time(const float2* __restrict__ d2, float* __restrict__ x, int N, int C, int S) {
+  __shared__ float2 tile[TJ][33];
+  const int H = N / 2;
+  const int p0 = blockIdx.x * 32;
+  const int j0 = blockIdx.y * TJ;
+  // load: for pair p0+pp, frames j0..j0+TJ-1
+  for (int idx = threadIdx.x; idx < 32 * TJ; idx += 256) {
+    const int pp = idx / TJ, jj = idx % TJ;
+    const int j = j0 + jj;
+    const int p = p0 + pp;
+    if (p < H) tile[jj][pp] = d2[((size_t)p * C + (j % C)) * S + j / C];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 32 * TJ; idx += 256) {
+    const int jj = idx / 32, pp = idx % 32;
+    const int p = p0 + pp;
+    if (p < H) reinterpret_cast<float2*>(x + (size_t)(j0 + jj) * N)[p] = tile[jj][pp];
+  }
+}
+
+}  // namespace ipfb

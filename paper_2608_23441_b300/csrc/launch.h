@@ -1,0 +1,46 @@
+// Host-side launch functions, one translation unit per kernel family so that the
+// library compiles in parallel.  All return a cudaError_t (cudaErrorNotSupported
+// for shapes without an instantiation).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ipfb {
+
+struct GainParams {
+  float phi2;
+  float gnorm;
+  float invJ;
+  int J;
+  int ntap;
+};
+
+struct UpchanSrc {
+  const float* x;    // time order, or nullptr
+  const float2* d2;  // column-pair scratch, or nullptr
+  int N;             // lblock of d2 (P = N/2 pairs)
+  int C, S;          // residue split of d2 (J = C*S)
+};
+
+// threads per frame and frames per CTA for the N/2 = H point per-frame transforms
+constexpr int tpf_for(int H) { return H / 16 < 32 ? 32 : (H / 16 > 256 ? 256 : H / 16); }
+constexpr int fpc_for(int H) { return H >= 8192 ? 1 : (H >= 4096 ? 2 : 4); }
+// threads for the S-point column transform
+constexpr int t_for(int S) { return S / 16 < 32 ? 32 : (S / 16 > 256 ? 256 : S / 16); }
+
+cudaError_t launch_k1_power(int H, const float* x, const float* window, int ntap, int J, double* sums,
+                            cudaStream_t st);
+cudaError_t launch_k1_scale(int H, int J, const double* sums, float* scale, cudaStream_t st);
+cudaError_t launch_k1_quant(int H, const float* x, const float* window, int ntap, int J, const float* scale,
+                            uint8_t* codes, float2* spectra, cudaStream_t st);
+cudaError_t launch_quantize(int H, long long nspec, const float2* spec, const float* scale, uint8_t* codes,
+                            cudaStream_t st);
+cudaError_t launch_k2(int H, const uint8_t* codes, const float* scale, float2* d2, int C, int S,
+                      cudaStream_t st);
+cudaError_t launch_k3(int C, int S, float2* d2, const float* window, int N, GainParams gp, cudaStream_t st);
+cudaError_t launch_pairs_to_time(const float2* d2, float* x, int N, int C, int S, cudaStream_t st);
+cudaError_t launch_upchan(const UpchanSrc& src, int L, long long nblocks, float2* out, float* x_out,
+                          cudaStream_t st);
+
+}  // namespace ipfb

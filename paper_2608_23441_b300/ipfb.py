@@ -1,0 +1,262 @@
+"""Thin Python binding of libipfb (include/ipfb.h): argument marshalling only.
+
+Every compute step runs in the library's CUDA kernels; this module checks
+dtypes, shapes and devices of torch tensors, allocates outputs and workspaces
+with torch (device memory only) and passes raw pointers plus the current torch
+CUDA stream.  There is no CPU fallback: without the built library, or with
+tensors that are not on a CUDA device, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libipfb.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "ipfb.h")
+
+OK = 0
+ERR_INVALID, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA = -1, -2, -3, -4, -5, -6
+OP_FORWARD, OP_WIENER, OP_WIENER_UPCHAN, OP_ML = 1, 2, 3, 4
+
+
+class Geom(ctypes.Structure):
+    _fields_ = [("lblock", ctypes.c_int), ("ntap", ctypes.c_int),
+                ("nframes", ctypes.c_int), ("periodic", ctypes.c_int)]
+
+
+class IpfbError(RuntimeError):
+    def __init__(self, fn: str, rc: int):
+        self.rc = rc
+        msg = f"{fn}: {strerror(rc)} ({rc})"
+        if rc == ERR_CUDA:
+            msg += f": {last_cuda_error()}"
+        super().__init__(msg)
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SZ = ctypes.c_size_t
+_I64 = ctypes.c_int64
+
+_SIGS = {
+    "ipfb_strerror": (ctypes.c_char_p, [_I]),
+    "ipfb_last_cuda_error": (ctypes.c_char_p, []),
+    "ipfb_version": (_I, []),
+    "ipfb_set_max_column_run": (_I, [_I]),
+    "ipfb_stage_timing": (_I, [_I]),
+    "ipfb_stage_times": (_I, [ctypes.c_char_p, _SZ, ctypes.POINTER(_D), ctypes.POINTER(_I), _I]),
+    "ipfb_workspace_size": (_I, [ctypes.POINTER(Geom), _I, ctypes.POINTER(_SZ)]),
+    "ipfb_sinc_hamming_window": (_I, [_I, _I, _P]),
+    "pfb_forward": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "pfb_quantize": (_I, [_I, _I, _P, _P, _P, _P]),
+    "ipfb_wiener": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _D, _I, _P, _P, _SZ, _P]),
+    "upchannelize": (_I, [_P, _I64, _I64, _P, _P, _SZ, _P]),
+    "ipfb_wiener_upchannelize": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _D, _I, _I, _P, _P, _P, _SZ, _P]),
+}
+
+
+def lib():
+    """Load libipfb.so from the package directory (built by `build.py`)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run `python -m paper_2608_23441_b300.build`")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            if hasattr(handle, name):
+                f = getattr(handle, name)
+                f.restype = res
+                f.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of every function declared in include/ipfb.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(",
+                      text, flags=re.M)
+
+
+def strerror(rc: int) -> str:
+    return lib().ipfb_strerror(rc).decode()
+
+
+def last_cuda_error() -> str:
+    return lib().ipfb_last_cuda_error().decode()
+
+
+def _check(fn: str, rc: int):
+    if rc != OK:
+        raise IpfbError(fn, rc)
+
+
+def set_max_column_run(frames: int):
+    _check("ipfb_set_max_column_run", lib().ipfb_set_max_column_run(int(frames)))
+
+
+def stage_timing(enable: bool):
+    """Start (and clear) or stop per-kernel CUDA-event timing inside the library."""
+    _check("ipfb_stage_timing", lib().ipfb_stage_timing(int(bool(enable))))
+
+
+def stage_times() -> dict:
+    """{kernel name: (total ms, launches)} recorded since stage_timing(True)."""
+    cap = 4096
+    names = ctypes.create_string_buffer(cap)
+    ms = (_D * 64)()
+    cnt = (_I * 64)()
+    n = lib().ipfb_stage_times(names, cap, ms, cnt, 64)
+    if n < 0:
+        raise IpfbError("ipfb_stage_times", n)
+    keys = names.value.decode().split(",") if n else []
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(keys)}
+
+
+def geom(lblock: int, ntap: int, nframes: int, periodic: int = 1) -> Geom:
+    return Geom(int(lblock), int(ntap), int(nframes), int(periodic))
+
+
+def workspace_size(g: Geom, op: int) -> int:
+    n = _SZ(0)
+    _check("ipfb_workspace_size", lib().ipfb_workspace_size(ctypes.byref(g), op, ctypes.byref(n)))
+    return int(n.value)
+
+
+def sinc_hamming_window(lblock: int, ntap: int) -> np.ndarray:
+    """Host-side window of the library, float32 [ntap, lblock]."""
+    out = np.empty(int(lblock) * int(ntap), dtype=np.float32)
+    _check("ipfb_sinc_hamming_window",
+           lib().ipfb_sinc_hamming_window(int(lblock), int(ntap), out.ctypes.data_as(_P)))
+    return out.reshape(int(ntap), int(lblock))
+
+
+# --------------------------------------------------------------------------- torch side
+def _torch():
+    import torch
+    return torch
+
+
+def _dev(t, dtype, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _workspace(nbytes: int, device, ws=None):
+    torch = _torch()
+    if nbytes == 0:
+        return None, 0
+    if ws is not None:
+        return ws, ws.numel() * ws.element_size()
+    return torch.empty(nbytes, dtype=torch.uint8, device=device), nbytes
+
+
+def pfb_forward(x, window, scale=None, return_spectra: bool = False, workspace=None):
+    """Forward PFB + 4-bit quantization.  x float32 [J*N] (CUDA); window float32
+    [ntap, N].  Returns (codes uint8 [J, N/2], scale float32 [N/2+1], spectra
+    complex64 [J, N/2+1] or None)."""
+    torch = _torch()
+    window = _dev(window, torch.float32, "window")
+    p, N = window.shape
+    x = _dev(x, torch.float32, "x")
+    J = x.numel() // N
+    if J * N != x.numel():
+        raise ValueError("len(x) must be a multiple of lblock")
+    g = geom(N, p, J)
+    codes = torch.empty((J, N // 2), dtype=torch.uint8, device=x.device)
+    scale_out = torch.empty(N // 2 + 1, dtype=torch.float32, device=x.device)
+    spec = torch.empty((J, N // 2 + 1), dtype=torch.complex64, device=x.device) if return_spectra else None
+    if scale is not None:
+        scale = _dev(scale, torch.float32, "scale")
+    ws, wsb = _workspace(workspace_size(g, OP_FORWARD), x.device, workspace)
+    _check("pfb_forward", lib().pfb_forward(ctypes.byref(g), _ptr(x), _ptr(window), _ptr(scale), _ptr(codes),
+                                            _ptr(scale_out), _ptr(spec), _ptr(ws), wsb, _stream()))
+    return codes, scale_out, spec
+
+
+def pfb_quantize(spectra, scale):
+    """Quantize complex64 spectra [nspec, N/2+1] with float32 scale [N/2+1]."""
+    torch = _torch()
+    spectra = _dev(spectra, torch.complex64, "spectra")
+    scale = _dev(scale, torch.float32, "scale")
+    nspec, C = spectra.shape
+    N = 2 * (C - 1)
+    codes = torch.empty((nspec, N // 2), dtype=torch.uint8, device=spectra.device)
+    _check("pfb_quantize", lib().pfb_quantize(N, nspec, _ptr(spectra), _ptr(scale), _ptr(codes), _stream()))
+    return codes
+
+
+def ipfb_wiener(codes, scale, window, noise_level: float, normalize: bool = True, out=None, workspace=None):
+    """Circulant (Wiener) inverse PFB.  codes uint8 [J, N/2]; scale float32 [N/2+1];
+    window float32 [ntap, N].  Returns x float32 [J*N] (time order)."""
+    torch = _torch()
+    codes = _dev(codes, torch.uint8, "codes")
+    scale = _dev(scale, torch.float32, "scale")
+    window = _dev(window, torch.float32, "window")
+    p, N = window.shape
+    J = codes.shape[0]
+    g = geom(N, p, J)
+    x = out if out is not None else torch.empty(J * N, dtype=torch.float32, device=codes.device)
+    ws, wsb = _workspace(workspace_size(g, OP_WIENER), codes.device, workspace)
+    _check("ipfb_wiener", lib().ipfb_wiener(ctypes.byref(g), _ptr(codes), _ptr(scale), _ptr(window),
+                                            float(noise_level), int(bool(normalize)), _ptr(x), _ptr(ws), wsb,
+                                            _stream()))
+    return x
+
+
+def upchannelize(x, block: int, out=None):
+    """Block real DFT of a time-ordered float32 stream: complex64 [len(x)//L, L/2+1]."""
+    torch = _torch()
+    x = _dev(x, torch.float32, "x")
+    L = int(block)
+    nb = x.numel() // L
+    if out is None:
+        out = torch.empty((nb, L // 2 + 1), dtype=torch.complex64, device=x.device)
+    _check("upchannelize", lib().upchannelize(_ptr(x), x.numel(), L, _ptr(out), None, 0, _stream()))
+    return out
+
+
+def ipfb_wiener_upchannelize(codes, scale, window, noise_level: float, upfactor: int, normalize: bool = True,
+                             want_x: bool = False, out=None, x_out=None, workspace=None):
+    """Wiener iPFB followed by up-channelization with L = upfactor * lblock.
+    Returns (spectra complex64 [J/upfactor, L/2+1], x float32 [J*N] or None)."""
+    torch = _torch()
+    codes = _dev(codes, torch.uint8, "codes")
+    scale = _dev(scale, torch.float32, "scale")
+    window = _dev(window, torch.float32, "window")
+    p, N = window.shape
+    J = codes.shape[0]
+    g = geom(N, p, J)
+    L = int(upfactor) * N
+    if out is None:
+        out = torch.empty((J // int(upfactor), L // 2 + 1), dtype=torch.complex64, device=codes.device)
+    if want_x and x_out is None:
+        x_out = torch.empty(J * N, dtype=torch.float32, device=codes.device)
+    ws, wsb = _workspace(workspace_size(g, OP_WIENER_UPCHAN), codes.device, workspace)
+    _check("ipfb_wiener_upchannelize",
+           lib().ipfb_wiener_upchannelize(ctypes.byref(g), _ptr(codes), _ptr(scale), _ptr(window),
+                                          float(noise_level), int(bool(normalize)), int(upfactor), _ptr(out),
+                                          _ptr(x_out), _ptr(ws), wsb, _stream()))
+    return out, x_out

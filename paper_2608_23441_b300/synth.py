@@ -36,15 +36,31 @@ def tone_params(lblock: int, ntones: int, seed: int, channel: float | None = Non
 
 
 def add_tones(x: np.ndarray, lblock: int, chans, phases, amplitude: float = 0.1,
-              chunk: int = 1 << 22) -> np.ndarray:
-    """x[t] += amplitude * sin(2*pi*(chan/lblock)*t + phase) for every tone (in place,
-    chunked so that 2^28-sample streams stay within a few hundred MB of temporaries)."""
+              block: int = 4096) -> np.ndarray:
+    """x[t] += amplitude * sum over tones of sin(2 pi (chan/lblock) t + phase), in place.
+    Evaluated block-wise as sin(a_k + b_u) = sin a_k cos b_u + cos a_k sin b_u with
+    t = k*block + u: one [blocks, 2*ntones] x [2*ntones, block] matrix product adds
+    every tone to a 2^28-sample stream in about a second."""
     T = x.shape[0]
-    for t0 in range(0, T, chunk):
-        t = np.arange(t0, min(T, t0 + chunk), dtype=np.float64)
-        for c, ph in zip(chans, phases):
-            # reduce the phase exactly: (c/lblock)*t mod 1 computed in two parts
-            x[t0:t0 + t.shape[0]] += amplitude * np.sin(2.0 * math.pi * np.mod(c * t / lblock, 1.0) + ph)
+    nfull = T // block
+    u = np.arange(block, dtype=np.float64)
+    k = np.arange(nfull, dtype=np.float64)
+    A = np.empty((nfull, 2 * len(chans)))
+    B = np.empty((2 * len(chans), block))
+    for i, (c, ph) in enumerate(zip(chans, phases)):
+        f = float(c) / float(lblock)
+        bu = 2.0 * math.pi * np.mod(f * u, 1.0)
+        ak = 2.0 * math.pi * np.mod(f * block * k, 1.0) + ph
+        A[:, 2 * i], A[:, 2 * i + 1] = np.sin(ak), np.cos(ak)
+        B[2 * i], B[2 * i + 1] = np.cos(bu), np.sin(bu)
+        if T > nfull * block:
+            t = np.arange(nfull * block, T, dtype=np.float64)
+            x[nfull * block:] += amplitude * np.sin(2.0 * math.pi * np.mod(f * t, 1.0) + ph)
+    if nfull:
+        step = 8192
+        xv = x[: nfull * block].reshape(nfull, block)
+        for r0 in range(0, nfull, step):
+            xv[r0:r0 + step] += amplitude * (A[r0:r0 + step] @ B)
     return x
 
 
@@ -104,3 +120,19 @@ def batched_geometries(nstreams: int, seed: int, lblocks=(1024, 2048, 4096),
 def prior_fraction_draw(seed: int, lo: float = 0.02, hi: float = 0.20) -> float:
     """Prior fraction U[lo, hi] for one training instance."""
     return float(np.random.default_rng(seed + 49979687).uniform(lo, hi))
+
+
+def random_code_bytes(nspec: int, half: int, seed: int) -> np.ndarray:
+    """Random 4-bit code bytes [nspec, half]: both nibbles uniform over the 15
+    two's-complement levels -7..7 (nibble value 8, i.e. -8, never appears)."""
+    rng = np.random.default_rng(seed + 86028121)
+    lv = np.array([0, 1, 2, 3, 4, 5, 6, 7, 9, 10, 11, 12, 13, 14, 15], dtype=np.uint8)
+    lo = lv[rng.integers(0, 15, size=(nspec, half))]
+    hi = lv[rng.integers(0, 15, size=(nspec, half))]
+    return (lo | (hi << 4)).astype(np.uint8)
+
+
+def random_scale(nchan: int, seed: int) -> np.ndarray:
+    """Positive per-channel quantizer steps, float32, log-uniform over [0.5, 2]."""
+    rng = np.random.default_rng(seed + 122949823)
+    return np.exp(rng.uniform(np.log(0.5), np.log(2.0), size=nchan)).astype(np.float32)

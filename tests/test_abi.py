@@ -1,0 +1,87 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every symbol that
+include/ipfb.h declares, and rejects bad arguments on the host (no GPU needed:
+every call here fails validation before anything is enqueued)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import pfb as opfb
+from paper_2608_23441_b300 import ipfb
+
+
+def test_library_exports_every_header_symbol():
+    names = ipfb.header_functions()
+    assert len(names) >= 10
+    handle = ipfb.lib()
+    missing = [n for n in names if not hasattr(handle, n)]
+    assert not missing, missing
+    assert ipfb.lib().ipfb_version() >= 100
+
+
+def test_strerror_codes():
+    for rc in (0, -1, -2, -3, -4, -5, -6):
+        assert ipfb.strerror(rc)
+    assert ipfb.strerror(12345) == "unknown status"
+
+
+def test_workspace_sizes():
+    g = ipfb.geom(4096, 4, 65536)
+    assert ipfb.workspace_size(g, ipfb.OP_WIENER) == 65536 * 4096 * 4
+    assert ipfb.workspace_size(g, ipfb.OP_WIENER_UPCHAN) == 65536 * 4096 * 4
+    assert ipfb.workspace_size(g, ipfb.OP_FORWARD) == 2 * 2049 * 8
+    with pytest.raises(ipfb.IpfbError) as e:
+        ipfb.workspace_size(ipfb.geom(4096, 4, 65537), ipfb.OP_WIENER)
+    assert e.value.rc == ipfb.ERR_UNSUPPORTED
+    with pytest.raises(ipfb.IpfbError) as e:
+        ipfb.workspace_size(ipfb.geom(4096, 4, 1024), 99)
+    assert e.value.rc == ipfb.ERR_INVALID
+    with pytest.raises(ipfb.IpfbError) as e:
+        ipfb.workspace_size(ipfb.geom(4096, 4, 1024, periodic=0), ipfb.OP_WIENER)
+    assert e.value.rc == ipfb.ERR_UNSUPPORTED
+
+
+def test_library_window_matches_oracle_window():
+    for N, p in ((64, 4), (256, 4), (4096, 4), (128, 3)):
+        w = ipfb.sinc_hamming_window(N, p)
+        ref = opfb.sinc_hamming_window(N, p)
+        assert w.dtype == np.float32 and w.shape == (p, N)
+        assert np.array_equal(w, ref.astype(np.float32))
+
+
+def test_host_validation_rejects_before_launch():
+    L = ipfb.lib()
+    g = ipfb.geom(256, 4, 64)
+    G = ctypes.byref(g)
+    # null pointers
+    assert L.ipfb_wiener(G, None, None, None, 0.01, 1, None, None, 0, None) == ipfb.ERR_INVALID
+    assert L.pfb_forward(G, None, None, None, None, None, None, None, 0, None) == ipfb.ERR_INVALID
+    assert L.upchannelize(None, 0, 1024, None, None, 0, None) == ipfb.ERR_INVALID
+    # bogus (never dereferenced) pointers with bad sizes or flags
+    fake = ctypes.c_void_p(0x1000)
+    assert L.ipfb_wiener(G, fake, fake, fake, -1.0, 1, fake, fake, 1 << 30, None) == ipfb.ERR_INVALID
+    assert L.ipfb_wiener(G, fake, fake, fake, float("nan"), 1, fake, fake, 1 << 30, None) == ipfb.ERR_INVALID
+    assert L.ipfb_wiener(G, fake, fake, fake, 0.01, 1, fake, fake, 16, None) == ipfb.ERR_WORKSPACE
+    assert L.upchannelize(fake, 4096, 1000, fake, None, 0, None) == ipfb.ERR_UNSUPPORTED
+    g_bad = ipfb.geom(100, 4, 64)
+    assert L.ipfb_wiener(ctypes.byref(g_bad), fake, fake, fake, 0.01, 1, fake, fake, 1 << 30, None) \
+        == ipfb.ERR_UNSUPPORTED
+    g_taps = ipfb.geom(256, 17, 64)
+    assert L.ipfb_wiener(ctypes.byref(g_taps), fake, fake, fake, 0.01, 1, fake, fake, 1 << 30, None) \
+        == ipfb.ERR_UNSUPPORTED
+    # forward without a scale needs its FP64 reduction workspace
+    assert L.pfb_forward(G, fake, fake, None, fake, fake, None, None, 0, None) == ipfb.ERR_WORKSPACE
+    g_up = ipfb.geom(256, 4, 64)
+    assert L.ipfb_wiener_upchannelize(ctypes.byref(g_up), fake, fake, fake, 0.01, 1, 3, fake, None, fake,
+                                      1 << 30, None) == ipfb.ERR_UNSUPPORTED
+    assert ipfb.lib().ipfb_set_max_column_run(1000) == ipfb.ERR_INVALID
+
+
+def test_binding_refuses_cpu_tensors():
+    torch = pytest.importorskip("torch")
+    x = torch.zeros(1024, dtype=torch.float32)
+    w = torch.zeros(4, 256, dtype=torch.float32)
+    with pytest.raises(TypeError):
+        ipfb.pfb_forward(x, w)
+    with pytest.raises(TypeError):
+        ipfb.upchannelize(x, 1024)
