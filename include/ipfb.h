@@ -161,6 +161,39 @@ int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const flo
                              int upfactor, float* out, float* x_out, void* ws, size_t ws_bytes,
                              void* stream);
 
+/*
+ * Maximum-likelihood inverse PFB with a time-domain prior (Sec. 4.2,
+ * Eq. chi squared), by conjugate gradient on the per-column normal equations
+ *   (C_n^T C_n / sigma^2 + lam M_n) x_n = C_n^T d_n / sigma^2 + lam M_n p_n
+ * with d = N-point inverse real FFT of (codes x scale) ("undo F"), the circulant
+ * sub-filter correlation (C x)[j] = sum_r w[r][n] x[(j + r) mod J], sigma^2 =
+ * noise_var, lam = prior_weight, M_n = the prior mask of column n, p = prior values.
+ * C^T C is applied as its exact circular (2p-1)-tap stencil; inner products are
+ * reduced in FP64, vectors are FP32.  Each column stops on its own when
+ * ||b - A x|| / ||b|| <= tol (recursively updated residual), or after max_iter.
+ * precond: 0 none; 1 Wiener, z = F^dagger[F r / (|W_n|^2/sigma^2 + lam mean(M_n))];
+ * 2 learned (net != NULL; see ipfb_precond_*).
+ * prior_mask: uint8 [J*N] time order (nonzero = saved sample); prior_values:
+ * float [J*N]; x_inout: float [J*N], the initial guess when use_x0 != 0 (else
+ * zero is used), the solution on return.  iters: int [N] iterations per column;
+ * resid: float [2][N], recursive then true relative residual per column (the
+ * true one recomputed from the final x).  Non-convergence is reported through
+ * these arrays (the call itself returns 0).  Requires 128 <= J <= 8192.
+ * Workspace: ipfb_workspace_size(g, IPFB_OP_ML).
+ */
+typedef struct {
+  double noise_var;    /* sigma^2 (> 0) in units of d                        */
+  double prior_weight; /* lam >= 0 (1 in the paper)                           */
+  double tol;          /* relative residual target per column (e.g. 1e-6)     */
+  int max_iter;        /* iteration cap per column                            */
+  int precond;         /* 0 none, 1 Wiener, 2 learned                         */
+} ipfb_ml_params;
+
+int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
+                  const ipfb_ml_params* prm, const uint8_t* prior_mask, const float* prior_values,
+                  const void* net, float* x_inout, int use_x0, int* iters, float* resid, void* ws,
+                  size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -213,10 +213,15 @@ int ipfb_workspace_size(const ipfb_geom* g, int op, size_t* bytes) {
       return IPFB_OK;
     case IPFB_OP_WIENER:
     case IPFB_OP_WIENER_UPCHAN:
-    case IPFB_OP_ML:
       rc = check_geom(g, true);
       if (rc) return rc;
       *bytes = (size_t)g->nframes * (size_t)g->lblock * sizeof(float);
+      return IPFB_OK;
+    case IPFB_OP_ML:
+      rc = check_geom(g, true);
+      if (rc) return rc;
+      if (g->nframes < 128 || g->nframes > 8192) return IPFB_ERR_UNSUPPORTED;
+      *bytes = 2 * (size_t)g->nframes * (size_t)g->lblock * sizeof(float);
       return IPFB_OK;
   }
   return IPFB_ERR_INVALID;
@@ -338,6 +343,56 @@ int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const flo
   UpchanSrc src{nullptr, d2, g->lblock, C, S};
   Stage t("k4_upchan", st);
   CK(launch_upchan(src, (int)L, nb, reinterpret_cast<float2*>(out), x_out, st), "k4_upchan");
+  t.done();
+  return IPFB_OK;
+}
+
+int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
+                  const ipfb_ml_params* prm, const uint8_t* prior_mask, const float* prior_values, const void* net,
+                  float* x_inout, int use_x0, int* iters, float* resid, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_geom(g, true);
+  if (rc) return rc;
+  if (!codes || !scale || !window || !prm || !prior_mask || !prior_values || !x_inout || !iters || !resid)
+    return IPFB_ERR_INVALID;
+  if (!(prm->noise_var > 0.0) || !std::isfinite(prm->noise_var) || !(prm->prior_weight >= 0.0) ||
+      !std::isfinite(prm->prior_weight) || !(prm->tol >= 0.0) || prm->max_iter < 0)
+    return IPFB_ERR_INVALID;
+  if (prm->precond < 0 || prm->precond > 2) return IPFB_ERR_INVALID;
+  if (prm->precond == 2) return IPFB_ERR_UNSUPPORTED;
+  (void)net;
+  size_t need = 0;
+  if ((rc = ipfb_workspace_size(g, IPFB_OP_ML, &need))) return rc;
+  if (!ws || ws_bytes < need) return IPFB_ERR_WORKSPACE;
+  const int N = g->lblock, J = g->nframes;
+  if (J / 16 < g->ntap - 1 && g->ntap > 4) return IPFB_ERR_UNSUPPORTED;
+  cudaStream_t st = as_stream(stream);
+  float2* d2 = reinterpret_cast<float2*>(ws);
+  float2* x2 = d2 + (size_t)J * (N / 2);
+  {
+    Stage t("k2_unpack_irfft", st);
+    CK(launch_k2(N / 2, codes, scale, d2, 1, J, st), "k2_unpack_irfft");
+    t.done();
+  }
+  if (use_x0) {
+    Stage t("k_time_to_pairs", st);
+    CK(launch_time_to_pairs(x_inout, x2, N, J, st), "k_time_to_pairs");
+    t.done();
+  }
+  MLParams mp;
+  mp.inv_s2 = (float)(1.0 / prm->noise_var);
+  mp.lam = (float)prm->prior_weight;
+  mp.tol = (float)prm->tol;
+  mp.max_iter = prm->max_iter;
+  mp.ntap = g->ntap;
+  mp.precond = prm->precond;
+  mp.use_x0 = use_x0 ? 1 : 0;
+  {
+    Stage t("k5_ml_cg", st);
+    CK(launch_k5(J, d2, x2, prior_mask, prior_values, window, N, mp, iters, resid, st), "k5_ml_cg");
+    t.done();
+  }
+  Stage t("k_pairs_to_time", st);
+  CK(launch_pairs_to_time(x2, x_inout, N, 1, J, st), "k_pairs_to_time");
   t.done();
   return IPFB_OK;
 }

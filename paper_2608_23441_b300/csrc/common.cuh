@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace ipfb {
 
 // ----------------------------------------------------------------------------
@@ -26,12 +28,34 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2
 __device__ __forceinline__ float2 cmul_i(float2 a) { return make_float2(-a.y, a.x); }
 
 // exp(s * 2 pi i * num / den) with s = -1 (forward) or +1 (inverse), 0 <= num < den.
-// sincospif keeps the argument an exact multiple of pi for power-of-two den.
+// For a power-of-two den the argument 2 num / den is formed exactly (a multiply by
+// an exact reciprocal), so sincospif sees an exact multiple of pi.
 template <bool INV>
 __device__ __forceinline__ float2 twiddle(int num, int den) {
   float s, c;
-  sincospif(__fdiv_rn(2.0f * (float)num, (float)den), &s, &c);
+  const float x = ((den & (den - 1)) == 0) ? (float)num * (2.0f / (float)den) : __fdiv_rn(2.0f * (float)num, (float)den);
+  sincospif(x, &s, &c);
   return make_float2(c, INV ? s : -s);
+}
+
+// exp(-+2 pi i t / L) for 0 <= t < L from two small tables built once per CTA:
+//   hi[t >> LO] = exp(-+2 pi i (t >> LO) 2^LO / L),  lo[t & (2^LO - 1)] = exp(-+2 pi i (t & ..) / L)
+// one complex multiply and two shared-memory reads per twiddle.
+template <int LO>
+struct Twid2 {
+  const float2* hi;
+  const float2* lo;
+  __device__ __forceinline__ float2 operator()(int t) const {
+    return cmul(hi[t >> LO], lo[t & ((1 << LO) - 1)]);
+  }
+};
+
+// Fill the two tables for length L (power of two, > 2^LO) with T threads.
+template <int LO, bool INV>
+__device__ __forceinline__ void twid2_fill(float2* hi, float2* lo, int L, int tid, int T) {
+  const int nhi = L >> LO;
+  for (int i = tid; i < nhi; i += T) hi[i] = twiddle<INV>(i << LO, L);
+  for (int i = tid; i < (1 << LO); i += T) lo[i] = twiddle<INV>(i, L);
 }
 
 // ----------------------------------------------------------------------------
@@ -94,48 +118,81 @@ __device__ __forceinline__ float2 rot_const(float2 a) {
   }
 }
 
-// ----------------------------------------------------------------------------
-// R-point DFT in registers, natural order in and out, radix-2 decimation in time
-// ----------------------------------------------------------------------------
-template <int K, int H, bool INV>
-struct Combine {
-  __device__ __forceinline__ static void run(float2* v, const float2* e, const float2* o) {
-    float2 t = rot_const<K, 2 * H, INV>(o[K]);
-    v[K] = cadd(e[K], t);
-    v[K + H] = csub(e[K], t);
-    Combine<K + 1, H, INV>::run(v, e, o);
+// a * W_C^q for a runtime q in [0, C) (C a small power of two): the unrolled
+// callers pass loop indices, which the compiler turns into constants.
+template <int C, bool INV>
+__device__ __forceinline__ float2 rotq(float2 a, int q) {
+  float2 out = a;
+#pragma unroll
+  for (int k = 1; k < C; ++k) {
+    if (q == k) {
+      switch (k) {
+        case 1: out = rot_const<1, C, INV>(a); break;
+        case 2: out = rot_const<2 % C, C, INV>(a); break;
+        case 3: out = rot_const<3 % C, C, INV>(a); break;
+        case 4: out = rot_const<4 % C, C, INV>(a); break;
+        case 5: out = rot_const<5 % C, C, INV>(a); break;
+        case 6: out = rot_const<6 % C, C, INV>(a); break;
+        case 7: out = rot_const<7 % C, C, INV>(a); break;
+        default: break;
+      }
+    }
   }
-};
-template <int H, bool INV>
-struct Combine<H, H, INV> {
-  __device__ __forceinline__ static void run(float2*, const float2*, const float2*) {}
-};
+  return out;
+}
+
+// ----------------------------------------------------------------------------
+// R-point DFT in registers, natural order in and out: in-place radix-2
+// decimation-in-frequency stages (block 2H: a + b, (a - b) W_{2H}^i), then the
+// bit-reversal permutation as compile-time register swaps.  Peak register use is
+// the R values plus one butterfly's temporaries.
+// ----------------------------------------------------------------------------
+template <int R, bool INV, int H, int P, int I>
+__device__ __forceinline__ void dif_bf(float2* v) {
+  const float2 a = v[P], b = v[P + H];
+  v[P] = cadd(a, b);
+  v[P + H] = rot_const<I * (R / (2 * H)), R, INV>(csub(a, b));
+}
+template <int R, bool INV, int H, int... Is>
+__device__ __forceinline__ void dif_stage(float2* v, std::integer_sequence<int, Is...>) {
+  (dif_bf<R, INV, H, (Is / H) * 2 * H + Is % H, Is % H>(v), ...);
+}
+__host__ __device__ constexpr int bitrev(int k, int R) {
+  int r = 0;
+  for (int m = R >> 1; m >= 1; m >>= 1, k >>= 1) r = (r << 1) | (k & 1);
+  return r;
+}
+template <int R, int K>
+__device__ __forceinline__ void bitrev_swap(float2* v) {
+  constexpr int B = bitrev(K, R);
+  if constexpr (K < B) {
+    const float2 t = v[K];
+    v[K] = v[B];
+    v[B] = t;
+  }
+}
+template <int R, int... Ks>
+__device__ __forceinline__ void bitrev_all(float2* v, std::integer_sequence<int, Ks...>) {
+  (bitrev_swap<R, Ks>(v), ...);
+}
+template <int R, bool INV, int H>
+__device__ __forceinline__ void dif_stages(float2* v) {
+  if constexpr (H >= 1) {
+    dif_stage<R, INV, H>(v, std::make_integer_sequence<int, R / 2>{});
+    dif_stages<R, INV, H / 2>(v);
+  }
+}
 
 template <int R, bool INV>
 struct DFT {
   __device__ __forceinline__ static void run(float2* v) {
-    float2 e[R / 2], o[R / 2];
-#pragma unroll
-    for (int i = 0; i < R / 2; ++i) {
-      e[i] = v[2 * i];
-      o[i] = v[2 * i + 1];
-    }
-    DFT<R / 2, INV>::run(e);
-    DFT<R / 2, INV>::run(o);
-    Combine<0, R / 2, INV>::run(v, e, o);
+    dif_stages<R, INV, R / 2>(v);
+    bitrev_all<R>(v, std::make_integer_sequence<int, R>{});
   }
 };
 template <bool INV>
 struct DFT<1, INV> {
   __device__ __forceinline__ static void run(float2*) {}
-};
-template <bool INV>
-struct DFT<2, INV> {
-  __device__ __forceinline__ static void run(float2* v) {
-    float2 a = v[0], b = v[1];
-    v[0] = cadd(a, b);
-    v[1] = csub(a, b);
-  }
 };
 
 // w^r for r = 0..R-1 by a balanced product tree (rounding depth ~log2 R)
@@ -145,6 +202,32 @@ __device__ __forceinline__ void twiddle_powers(float2 w, float2* wr) {
   if (R > 1) wr[1] = w;
 #pragma unroll
   for (int r = 2; r < R; ++r) wr[r] = cmul(wr[r / 2], wr[r - r / 2]);
+}
+
+// v[r] *= w^r for r = 1..R-1 without holding all R powers: w^(a + 4b) =
+// w^a (a < 4, kept) times w^(4b) (advanced by one multiply per b).  The longest
+// product chain is R/4 + 2 multiplies.
+template <int R>
+__device__ __forceinline__ void apply_twiddles(float2* v, float2 w) {
+  if constexpr (R >= 2) v[1] = cmul(v[1], w);
+  if constexpr (R >= 4) {
+    const float2 w2 = cmul(w, w);
+    const float2 w3 = cmul(w2, w);
+    v[2] = cmul(v[2], w2);
+    v[3] = cmul(v[3], w3);
+    if constexpr (R > 4) {
+      const float2 w4 = cmul(w2, w2);
+      float2 wb = w4;
+#pragma unroll
+      for (int b = 1; b < R / 4; ++b) {
+        v[4 * b] = cmul(v[4 * b], wb);
+        v[4 * b + 1] = cmul(v[4 * b + 1], cmul(wb, w));
+        v[4 * b + 2] = cmul(v[4 * b + 2], cmul(wb, w2));
+        v[4 * b + 3] = cmul(v[4 * b + 3], cmul(wb, w3));
+        if (b + 1 < R / 4) wb = cmul(wb, w4);
+      }
+    }
+  }
 }
 
 // padded shared-memory index: one spare float2 after every 16, so that radix-16
@@ -170,13 +253,7 @@ __device__ __forceinline__ void stockham_pass(int S, int Ns, int tid, LD ld, ST 
     if (b < nb) {
 #pragma unroll
       for (int r = 0; r < R; ++r) v[i][r] = ld(b + r * nb);
-      if (Ns > 1) {
-        const int k = b % Ns;
-        float2 wr[R];
-        twiddle_powers<R>(twiddle<INV>(k, Ns * R), wr);
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], wr[r]);
-      }
+      if (Ns > 1) apply_twiddles<R>(v[i], twiddle<INV>(b % Ns, Ns * R));
       DFT<R, INV>::run(v[i]);
     }
   }
@@ -194,19 +271,24 @@ __device__ __forceinline__ void stockham_pass(int S, int Ns, int tid, LD ld, ST 
 }
 
 // Radix choice for the pass that starts at sub-size Ns of an S-point transform:
-// the remaining factor if it is <= 32, otherwise 16.
-__host__ __device__ constexpr int next_radix(int S, int Ns) {
-  return (S / Ns) <= 32 ? (S / Ns) : 16;
+// the remaining factor if it is <= MAXR (32 by default), otherwise 16 (or MAXR if smaller).
+// A radix-32 pass is placed first (Ns == 1, where it needs no twiddles) when the
+// size is 32 x 16^k, so that no pass holds 32 twiddles in registers.
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
+__host__ __device__ constexpr int next_radix(int S, int Ns, int MAXR = 32) {
+  return (S / Ns) <= (MAXR < 16 ? MAXR : 16) ? (S / Ns)
+         : (Ns == 1 && MAXR >= 32 && ilog2c(S) % 4 == 1) ? 32
+         : (MAXR < 16 ? MAXR : 16);
 }
 
 // Full S-point FFT by T threads.  The first pass reads ld_first, the last writes
 // st_last, every intermediate pass works in place on the padded smem array sm.
 // Callers must __syncthreads() before (if ld_first reads smem written by others)
 // and after (if st_last writes smem read by others).
-template <int S, int T, bool INV, int Ns, class LDF, class STL>
+template <int S, int T, bool INV, int Ns, class LDF, class STL, int MAXR = 32>
 struct FFTPasses {
   __device__ __forceinline__ static void run(float2* sm, int tid, LDF ldf, STL stl) {
-    constexpr int R = next_radix(S, Ns);
+    constexpr int R = next_radix(S, Ns, MAXR);
     constexpr int BPT = (S / R + T - 1) / T;
     constexpr bool first = (Ns == 1);
     constexpr bool last = (Ns * R == S);
@@ -219,20 +301,20 @@ struct FFTPasses {
     } else if constexpr (first) {
       stockham_pass<R, BPT, T, INV, true>(S, Ns, tid, ldf, sts);
       __syncthreads();
-      FFTPasses<S, T, INV, Ns * R, LDF, STL>::run(sm, tid, ldf, stl);
+      FFTPasses<S, T, INV, Ns * R, LDF, STL, MAXR>::run(sm, tid, ldf, stl);
     } else if constexpr (last) {
       stockham_pass<R, BPT, T, INV, true>(S, Ns, tid, lds, stl);
     } else {
       stockham_pass<R, BPT, T, INV, true>(S, Ns, tid, lds, sts);
       __syncthreads();
-      FFTPasses<S, T, INV, Ns * R, LDF, STL>::run(sm, tid, ldf, stl);
+      FFTPasses<S, T, INV, Ns * R, LDF, STL, MAXR>::run(sm, tid, ldf, stl);
     }
   }
 };
 
-template <int S, int T, bool INV, class LDF, class STL>
+template <int S, int T, bool INV, class LDF, class STL, int MAXR = 32>
 __device__ __forceinline__ void block_fft(float2* sm, int tid, LDF ldf, STL stl) {
-  FFTPasses<S, T, INV, 1, LDF, STL>::run(sm, tid, ldf, stl);
+  FFTPasses<S, T, INV, 1, LDF, STL, MAXR>::run(sm, tid, ldf, stl);
 }
 
 }  // namespace ipfb

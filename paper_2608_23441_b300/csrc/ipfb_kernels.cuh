@@ -26,6 +26,10 @@ namespace cg = cooperative_groups;
 //     E[k] = (Y[k] + conj Y[H-k]) / 2,  O[k] = (Y[k] - conj Y[H-k]) e^{+2 pi i k/N} / 2,
 // so that z[m] = x[2m] + i x[2m+1] -- exactly the column-pair value of pair m.
 // The 1/H normalisation is folded into the pre-scale.
+// frame stride in smem (float2): padded length rounded to 4 (mod 16), so that the
+// F interleaved frames of the transposed store fall in distinct banks
+__host__ __device__ constexpr int k2_frame_stride(int H) { return ((padded_len(H) + 15) / 16) * 16 + 4; }
+
 template <int H, int TPF, int F>
 __global__ void __launch_bounds__(TPF* F)
 k2_unpack_irfft(const uint8_t* __restrict__ codes, const float* __restrict__ scale,
@@ -33,7 +37,7 @@ k2_unpack_irfft(const uint8_t* __restrict__ codes, const float* __restrict__ sca
   extern __shared__ float2 smem[];
   const int f = threadIdx.x / TPF;
   const int tid = threadIdx.x % TPF;
-  float2* sm = smem + f * padded_len(H);
+  float2* sm = smem + f * k2_frame_stride(H);
   const int per_res = S / F;
   const int r = blockIdx.x / per_res;
   const int m0 = (blockIdx.x % per_res) * F;
@@ -78,7 +82,7 @@ k2_unpack_irfft(const uint8_t* __restrict__ codes, const float* __restrict__ sca
   // transposed store: for each pair p, F consecutive m of residue r
   for (int idx = threadIdx.x; idx < H * F; idx += TPF * F) {
     const int p = idx / F, ff = idx % F;
-    d2[((size_t)p * C + r) * S + m0 + ff] = smem[ff * padded_len(H) + pidx(p)];
+    d2[((size_t)p * C + r) * S + m0 + ff] = smem[ff * k2_frame_stride(H) + pidx(p)];
   }
 }
 
@@ -92,13 +96,15 @@ k2_unpack_irfft(const uint8_t* __restrict__ codes, const float* __restrict__ sca
 constexpr float kFp64Below = 1e-4f;
 constexpr int kMaxTaps = 16;
 
+template <int NT>
 __device__ __forceinline__ float2 gain_at(const float* taps, int k, float2 e1, const GainParams& gp) {
-  // Horner in e1 = e^{-2 pi i k/J}; the loop is unrolled to kMaxTaps so the taps stay
-  // in registers (ntap is uniform across the CTA, so the guard does not diverge)
+  // Horner in e1 = e^{-2 pi i k/J}.  NT > 0: exactly NT taps (compile time);
+  // NT == 0: gp.ntap <= kMaxTaps taps, loop unrolled with a uniform guard.
+  constexpr int NMAX = NT > 0 ? NT : kMaxTaps;
   float2 W = make_float2(0.0f, 0.0f);
 #pragma unroll
-  for (int t = kMaxTaps - 1; t >= 0; --t) {
-    if (t < gp.ntap) {
+  for (int t = NMAX - 1; t >= 0; --t) {
+    if (NT > 0 || t < gp.ntap) {
       W = cmul(W, e1);
       W.x += taps[t];
     }
@@ -109,8 +115,8 @@ __device__ __forceinline__ float2 gain_at(const float* taps, int k, float2 e1, c
     sincospi(2.0 * (double)k / (double)gp.J, &s, &c);
     double wx = 0.0, wy = 0.0;
 #pragma unroll
-    for (int t = kMaxTaps - 1; t >= 0; --t) {
-      if (t < gp.ntap) {
+    for (int t = NMAX - 1; t >= 0; --t) {
+      if (NT > 0 || t < gp.ntap) {
         const double nx = wx * c + wy * s;  // (wx + i wy)(c - i s)
         const double ny = wy * c - wx * s;
         wx = nx + (double)taps[t];
@@ -147,8 +153,8 @@ __device__ __forceinline__ void split_gain(float2& zk, float2& zm, float2 ga, fl
 //      thread owns both and nothing crosses CTAs between 2 and 4
 //   4. inverse cross stage, pushed back to the owners, then local inverse FFT.
 // ----------------------------------------------------------------------------
-template <int C, int S, int T>
-__global__ void __launch_bounds__(T)
+template <int C, int S, int T, int NT>
+__global__ void __launch_bounds__(T, (S >= 4096 ? 2 : 1))
 k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int N, GainParams gp) {
   extern __shared__ float2 sm[];
   const int tid = threadIdx.x;
@@ -158,9 +164,10 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
   float2* base = d2 + ((size_t)p * C + r) * S;
   const int J = C * S;
 
-  float ta[kMaxTaps], tb[kMaxTaps];
+  constexpr int NMAX = NT > 0 ? NT : kMaxTaps;
+  float ta[NMAX], tb[NMAX];
 #pragma unroll
-  for (int t = 0; t < kMaxTaps; ++t) {
+  for (int t = 0; t < NMAX; ++t) {
     ta[t] = (t < gp.ntap) ? __ldg(window + (size_t)t * N + 2 * p) : 0.0f;
     tb[t] = (t < gp.ntap) ? __ldg(window + (size_t)t * N + 2 * p + 1) : 0.0f;
   }
@@ -178,36 +185,33 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
     __syncthreads();
   }
 
-  float2* peer[C];
-#pragma unroll
-  for (int q = 0; q < C; ++q) {
+  // peer q's shared array (mapped on use, to keep the addresses out of registers)
+  auto peer = [](int q) -> float2* {
     if constexpr (C > 1)
-      peer[q] = cg::this_cluster().map_shared_rank(sm, q);
+      return cg::this_cluster().map_shared_rank(sm, q);
     else
-      peer[q] = sm;
-  }
+      return sm;
+  };
 
   // 2-4. tasks: t = 0 (kb = 0), t = S/2 (kb = S/2), else the pair (t, S - t)
   for (int t = r * T + tid; t <= S / 2; t += C * T) {
     const bool pairtask = (t != 0) && (2 * t != S);
     const int kb0 = t, kb1 = S - t;
     float2 z0[C], z1[C];
-    float2 w0[C], w1[C];
-    // gather + cross-stage twiddle + C-point DFT over r
-    if constexpr (C > 1) {
-      twiddle_powers<C>(twiddle<false>(kb0, J), w0);
-      if (pairtask) twiddle_powers<C>(twiddle<false>(kb1, J), w1);
-    }
+    float2 w0[C];
+    // gather + cross-stage twiddle + C-point DFT over r.  The twiddle of kb1 = S - kb0
+    // is e^{-2 pi i q (S - kb0)/J} = e^{-2 pi i q / C} conj(w0[q]).
+    if constexpr (C > 1) twiddle_powers<C>(twiddle<false>(kb0, J), w0);
 #pragma unroll
     for (int q = 0; q < C; ++q) {
-      z0[q] = peer[q][pidx(kb0)];
-      if (pairtask) z1[q] = peer[q][pidx(kb1)];
+      z0[q] = peer(q)[pidx(kb0)];
+      if (pairtask) z1[q] = peer(q)[pidx(kb1)];
     }
     if constexpr (C > 1) {
 #pragma unroll
       for (int q = 1; q < C; ++q) {
         z0[q] = cmul(z0[q], w0[q]);
-        if (pairtask) z1[q] = cmul(z1[q], w1[q]);
+        if (pairtask) z1[q] = rotq<C, false>(cmul(z1[q], cconj(w0[q])), q);
       }
       DFT<C, false>::run(z0);
       if (pairtask) DFT<C, false>::run(z1);
@@ -218,7 +222,7 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
       for (int ka = 0; ka < C; ++ka) {
         const int k = kb0 + S * ka;
         const float2 e1 = twiddle<false>(k, J);
-        const float2 ga = gain_at(ta, k, e1, gp), gb = gain_at(tb, k, e1, gp);
+        const float2 ga = gain_at<NT>(ta, k, e1, gp), gb = gain_at<NT>(tb, k, e1, gp);
         split_gain(z0[ka], z1[C - 1 - ka], ga, gb);
       }
     } else if (t == 0) {
@@ -228,7 +232,7 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
         const int km = (C - ka) % C;
         const int k = S * ka;
         const float2 e1 = twiddle<false>(k, J);
-        const float2 ga = gain_at(ta, k, e1, gp), gb = gain_at(tb, k, e1, gp);
+        const float2 ga = gain_at<NT>(ta, k, e1, gp), gb = gain_at<NT>(tb, k, e1, gp);
         float2 a = z0[ka], b = z0[km];
         split_gain(a, b, ga, gb);
         z0[ka] = a;
@@ -241,7 +245,7 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
         const int km = C - 1 - ka;
         const int k = kb0 + S * ka;
         const float2 e1 = twiddle<false>(k, J);
-        const float2 ga = gain_at(ta, k, e1, gp), gb = gain_at(tb, k, e1, gp);
+        const float2 ga = gain_at<NT>(ta, k, e1, gp), gb = gain_at<NT>(tb, k, e1, gp);
         float2 a = z0[ka], b = z0[km];
         split_gain(a, b, ga, gb);
         z0[ka] = a;
@@ -255,13 +259,13 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
 #pragma unroll
       for (int q = 1; q < C; ++q) {
         z0[q] = cmul(z0[q], cconj(w0[q]));
-        if (pairtask) z1[q] = cmul(z1[q], cconj(w1[q]));
+        if (pairtask) z1[q] = rotq<C, true>(cmul(z1[q], w0[q]), q);
       }
     }
 #pragma unroll
     for (int q = 0; q < C; ++q) {
-      peer[q][pidx(kb0)] = z0[q];
-      if (pairtask) peer[q][pidx(kb1)] = z1[q];
+      peer(q)[pidx(kb0)] = z0[q];
+      if (pairtask) peer(q)[pidx(kb1)] = z1[q];
     }
   }
   if constexpr (C > 1) {

@@ -8,7 +8,7 @@ template <int CU, int U, int PP>
 cudaError_t k4(const UpchanSrc& src, long long nblocks, float2* out, float* x_out, cudaStream_t st) {
   constexpr int T = 256;
   auto kern = k4_upchan<CU, U, PP, T>;
-  const size_t smem = (size_t)padded_len(U * PP) * sizeof(float2);
+  const size_t smem = (size_t)(padded_len(U * PP) + 1024) * sizeof(float2);
   cudaError_t e;
   if (smem > 48 * 1024) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

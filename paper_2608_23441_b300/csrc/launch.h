@@ -40,6 +40,19 @@ cudaError_t launch_k2(int H, const uint8_t* codes, const float* scale, float2* d
                       cudaStream_t st);
 cudaError_t launch_k3(int C, int S, float2* d2, const float* window, int N, GainParams gp, cudaStream_t st);
 cudaError_t launch_pairs_to_time(const float2* d2, float* x, int N, int C, int S, cudaStream_t st);
+struct MLParams {
+  float inv_s2;  // 1 / sigma^2
+  float lam;     // prior weight (Q^-1 on saved samples)
+  float tol;     // relative residual target per column
+  int max_iter;
+  int ntap;
+  int precond;   // 0 none, 1 Wiener
+  int use_x0;    // 1: x2 holds the initial guess
+};
+
+cudaError_t launch_k5(int J, const float2* d2, float2* x2, const uint8_t* mask, const float* prior,
+                      const float* window, int N, const MLParams& mp, int* iters, float* resid, cudaStream_t st);
+cudaError_t launch_time_to_pairs(const float* x, float2* x2, int N, int J, cudaStream_t st);
 cudaError_t launch_upchan(const UpchanSrc& src, int L, long long nblocks, float2* out, float* x_out,
                           cudaStream_t st);
 

@@ -1,0 +1,372 @@
+// Maximum-likelihood inverse PFB with a time-domain prior (Sec. 4.2, Eq. chi squared)
+// by conjugate gradient, one CTA per column pair.
+//
+// Per column n the normal equations of Eq. chi squared in the circulant model are
+//     (C_n^T C_n / sigma^2 + lam M_n) x_n = C_n^T d_n / sigma^2 + lam M_n p_n,
+// (C x)[j] = sum_r w[r,n] x[(j + r) mod J].  C^T C is the circular stencil with taps
+// a_s = sum_r w_r w_{r+s} (|s| < ntap), applied exactly in FP32 from registers.
+// Both columns of a pair run their own CG (own alpha, beta, stopping test) in
+// lockstep; vectors are FP32, every inner product is reduced across the CTA in
+// FP64.  Optional Wiener preconditioner
+//     z = F^dagger[ F r / (|W_n|^2/sigma^2 + lam mbar_n) ]
+// through the same pair-packed J-point FFTs as the Wiener inverse.
+#pragma once
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace ipfb {
+
+constexpr int kMlMaxTaps = 16;
+
+// FP64 sum of K values over the CTA (warp shuffles, then every thread adds the
+// per-warp partials).  buf alternates between two slots so that one barrier per
+// call is enough.
+template <int K, int T>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* red /* [2][T/32][K] */, int& buf) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  }
+  constexpr int W = T / 32;
+  double* slot = red + buf * W * K;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) slot[warp * K + k] = v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+#pragma unroll 8
+    for (int w = 0; w < W; ++w) s += slot[w * K + k];
+    v[k] = s;
+  }
+  buf ^= 1;
+}
+
+// Wiener preconditioner on the pair held as r = (r_a, r_b) in smem (complex r_a + i r_b)
+template <int J, int T, int NT>
+__device__ __forceinline__ void wiener_precond_pair(float2* sm, const float* ta, const float* tb, int ntap,
+                                                   float inv_s2, float lam_ma, float lam_mb) {
+  constexpr int NMAX = NT > 0 ? NT : kMlMaxTaps;
+  auto lds = [sm](int i) { return sm[pidx(i)]; };
+  auto sts = [sm](int i, float2 v) { sm[pidx(i)] = v; };
+  const int tid = threadIdx.x;
+  block_fft<J, T, false, decltype(lds), decltype(sts), 8>(sm, tid, lds, sts);
+  __syncthreads();
+  for (int k = tid; k <= J / 2; k += T) {
+    const int km = (J - k) % J;
+    const float2 e1 = twiddle<false>(k, J);
+    float2 Wa = make_float2(0.0f, 0.0f), Wb = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int t = NMAX - 1; t >= 0; --t) {
+      if (NT > 0 || t < ntap) {
+        Wa = cmul(Wa, e1);
+        Wa.x += ta[t];
+        Wb = cmul(Wb, e1);
+        Wb.x += tb[t];
+      }
+    }
+    const float Pa = fmaf(Wa.x * Wa.x + Wa.y * Wa.y, inv_s2, lam_ma);
+    const float Pb = fmaf(Wb.x * Wb.x + Wb.y * Wb.y, inv_s2, lam_mb);
+    const float ga = Pa > 0.0f ? 1.0f / (Pa * (float)J) : 0.0f;
+    const float gb = Pb > 0.0f ? 1.0f / (Pb * (float)J) : 0.0f;
+    float2 zk = sm[pidx(k)], zm = sm[pidx(km)];
+    // split, scale by the real gains, recombine (modes k and -k)
+    const float2 A = cscale(cadd(zk, cconj(zm)), 0.5f);
+    const float2 dd = csub(zk, cconj(zm));
+    const float2 B = make_float2(0.5f * dd.y, -0.5f * dd.x);
+    const float2 ya = cscale(A, ga), yb = cscale(B, gb);
+    zk = cadd(ya, cmul_i(yb));
+    zm = cadd(cconj(ya), cmul_i(cconj(yb)));
+    sm[pidx(k)] = zk;
+    if (km != k) sm[pidx(km)] = zm;
+  }
+  __syncthreads();
+  block_fft<J, T, true, decltype(lds), decltype(sts), 8>(sm, tid, lds, sts);
+  __syncthreads();
+}
+
+// One CTA per column pair p (columns 2p, 2p+1).  Thread t owns frames
+// [t*EPT, (t+1)*EPT) of both columns.  The search direction p and the solution x
+// live in padded shared memory (the stencil reads its halo straight from there);
+// the residual r and A p stay in registers.
+//   d2: [P][J] pair-packed d;  x2: [P][J] pair-packed initial guess in, solution out
+//   mask / prior: time order [J][N] (bytes / floats)
+//   iters: [N]; resid: [2][N] (recursive relative residual, true relative residual)
+template <int J, int T, int RMAX>
+__device__ __forceinline__ void load_window(const float2* sm, int j0, float2 (&v)[J / T + 2 * RMAX]) {
+  constexpr int EPT = J / T;
+#pragma unroll
+  for (int i = 0; i < EPT + 2 * RMAX; ++i) v[i] = sm[pidx((j0 + i - RMAX + J) & (J - 1))];
+}
+
+// A v on a window v[-RMAX .. EPT+RMAX): inv_s2 * sum_s a_s v[e+s] + lam m v
+template <int EPT, int RMAX>
+__device__ __forceinline__ float2 apply_A_at(const float2* v, const float2 (&a)[RMAX + 1], uint32_t mbits,
+                                             float lam, int e) {
+  const float2 c = v[e + RMAX];
+  float2 acc = make_float2(a[0].x * c.x, a[0].y * c.y);
+#pragma unroll
+  for (int s = 1; s <= RMAX; ++s) {
+    const float2 lo = v[e + RMAX - s], hi = v[e + RMAX + s];
+    acc.x = fmaf(a[s].x, lo.x + hi.x, acc.x);
+    acc.y = fmaf(a[s].y, lo.y + hi.y, acc.y);
+  }
+  const float ma = ((mbits >> e) & 1u) ? lam : 0.0f;
+  const float mb = ((mbits >> (e + 16)) & 1u) ? lam : 0.0f;
+  return make_float2(fmaf(ma, c.x, acc.x), fmaf(mb, c.y, acc.y));
+}
+
+// b = C^T d / sigma^2 + lam m prior for this thread's frames, (C^T d)[i] = sum_r w_r d[i - r]
+template <int J, int T, int RMAX>
+__device__ __forceinline__ void build_rhs(const float2* __restrict__ d2p, const uint8_t* __restrict__ mask,
+                                          const float* __restrict__ prior, int N, int p, int j0, const float* ta,
+                                          const float* tb, float inv_s2, float lam, uint32_t& mbits,
+                                          float2 (&b)[J / T]) {
+  constexpr int EPT = J / T;
+  float2 d[EPT + RMAX];
+#pragma unroll
+  for (int i = 0; i < EPT + RMAX; ++i) d[i] = d2p[(j0 + i - RMAX + J) & (J - 1)];
+  mbits = 0;
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const size_t t_idx = (size_t)(j0 + e) * N + 2 * p;
+    const uint16_t mm = *reinterpret_cast<const uint16_t*>(mask + t_idx);
+    if (mm & 0xFFu) mbits |= 1u << e;
+    if (mm >> 8) mbits |= 1u << (e + 16);
+    float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int r = 0; r <= RMAX; ++r) {
+      acc.x = fmaf(ta[r], d[e + RMAX - r].x, acc.x);
+      acc.y = fmaf(tb[r], d[e + RMAX - r].y, acc.y);
+    }
+    const float2 pr = *reinterpret_cast<const float2*>(prior + t_idx);
+    const float ma = ((mbits >> e) & 1u) ? lam : 0.0f;
+    const float mb = ((mbits >> (e + 16)) & 1u) ? lam : 0.0f;
+    b[e] = make_float2(fmaf(ma, pr.x, acc.x * inv_s2), fmaf(mb, pr.y, acc.y * inv_s2));
+  }
+}
+
+template <int J, int T, int RMAX, int PRE, int NT>
+__global__ void __launch_bounds__(T, 1)
+k5_ml_cg(const float2* __restrict__ d2, float2* __restrict__ x2, const uint8_t* __restrict__ mask,
+         const float* __restrict__ prior, const float* __restrict__ window, int N, MLParams mp,
+         int* __restrict__ iters, float* __restrict__ resid) {
+  constexpr int EPT = J / T;
+  constexpr int WIN = EPT + 2 * RMAX;
+  static_assert(EPT >= 1 && EPT <= 16, "1..16 frames per thread");
+  extern __shared__ float2 smem[];
+  float2* sm_x = smem;                                  // [padded J] solution
+  float2* sm_p = sm_x + padded_len(J);                  // [padded J] search direction
+  double* red = reinterpret_cast<double*>(sm_p + padded_len(J));  // [2][T/32][4]
+  float2* sm_f = reinterpret_cast<float2*>(red + 2 * (T / 32) * 4);  // [padded J] FFT work (PRE == 1)
+
+  const int tid = threadIdx.x;
+  const int p = blockIdx.x;
+  const int j0 = tid * EPT;
+  const float2* d2p = d2 + (size_t)p * J;
+  int buf = 0;
+
+  constexpr int NMAX = NT > 0 ? NT : kMlMaxTaps;
+  float ta[NMAX], tb[NMAX];
+#pragma unroll
+  for (int t = 0; t < NMAX; ++t) {
+    ta[t] = (t < mp.ntap) ? __ldg(window + (size_t)t * N + 2 * p) : 0.0f;
+    tb[t] = (t < mp.ntap) ? __ldg(window + (size_t)t * N + 2 * p + 1) : 0.0f;
+  }
+  float2 a[RMAX + 1];
+#pragma unroll
+  for (int s = 0; s <= RMAX; ++s) {
+    float sa = 0.0f, sb = 0.0f;
+#pragma unroll
+    for (int r = 0; r + s < NMAX; ++r) {
+      sa = fmaf(ta[r], ta[r + s], sa);
+      sb = fmaf(tb[r], tb[r + s], sb);
+    }
+    a[s] = make_float2(sa * mp.inv_s2, sb * mp.inv_s2);
+  }
+
+  uint32_t mbits;
+  float2 r[EPT];
+  build_rhs<J, T, RMAX>(d2p, mask, prior, N, p, j0, ta, tb, mp.inv_s2, mp.lam, mbits, r);
+  double bn[4];
+  {
+    float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      s0 = fmaf(r[e].x, r[e].x, s0);
+      s1 = fmaf(r[e].y, r[e].y, s1);
+    }
+    bn[0] = s0;
+    bn[1] = s1;
+    bn[2] = __popc(mbits & 0xFFFFu);
+    bn[3] = __popc(mbits >> 16);
+  }
+  block_sum<4, T>(bn, red, buf);
+  const double bnorm_a = bn[0] > 0.0 ? sqrt(bn[0]) : 1.0;
+  const double bnorm_b = bn[1] > 0.0 ? sqrt(bn[1]) : 1.0;
+  const float lam_ma = mp.lam * (float)(bn[2] / (double)J);
+  const float lam_mb = mp.lam * (float)(bn[3] / (double)J);
+
+  // x0 (and r0 = b - A x0)
+#pragma unroll
+  for (int e = 0; e < EPT; ++e)
+    sm_x[pidx(j0 + e)] = mp.use_x0 ? x2[(size_t)p * J + j0 + e] : make_float2(0.0f, 0.0f);
+  if (mp.use_x0) {
+    __syncthreads();
+    float2 v[WIN];
+    load_window<J, T, RMAX>(sm_x, j0, v);
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) r[e] = csub(r[e], apply_A_at<EPT, RMAX>(v, a, mbits, mp.lam, e));
+  }
+
+  float2 z[EPT];
+  auto precondition = [&]() {
+    if constexpr (PRE == 1) {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) sm_f[pidx(j0 + e)] = r[e];
+      __syncthreads();
+      wiener_precond_pair<J, T, NT>(sm_f, ta, tb, mp.ntap, mp.inv_s2, lam_ma, lam_mb);
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) z[e] = sm_f[pidx(j0 + e)];
+    } else {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) z[e] = r[e];
+    }
+  };
+  precondition();
+  double rz[4];
+  {
+    float s0 = 0.0f, s1 = 0.0f, q0 = 0.0f, q1 = 0.0f;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      sm_p[pidx(j0 + e)] = z[e];
+      s0 = fmaf(r[e].x, z[e].x, s0);
+      s1 = fmaf(r[e].y, z[e].y, s1);
+      q0 = fmaf(r[e].x, r[e].x, q0);
+      q1 = fmaf(r[e].y, r[e].y, q1);
+    }
+    rz[0] = s0; rz[1] = s1; rz[2] = q0; rz[3] = q1;
+  }
+  block_sum<4, T>(rz, red, buf);  // its barrier also publishes sm_p
+  double rel_a = sqrt(rz[2]) / bnorm_a, rel_b = sqrt(rz[3]) / bnorm_b;
+  bool act_a = rel_a > mp.tol, act_b = rel_b > mp.tol;
+  int it_a = 0, it_b = 0;
+  double rzo_a = rz[0], rzo_b = rz[1];
+
+  for (int it = 0; it < mp.max_iter && (act_a || act_b); ++it) {
+    float2 pw[WIN];
+    load_window<J, T, RMAX>(sm_p, j0, pw);
+    double pap[2];
+    {
+      float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const float2 ape = apply_A_at<EPT, RMAX>(pw, a, mbits, mp.lam, e);
+        s0 = fmaf(pw[e + RMAX].x, ape.x, s0);
+        s1 = fmaf(pw[e + RMAX].y, ape.y, s1);
+      }
+      pap[0] = s0;
+      pap[1] = s1;
+    }
+    block_sum<2, T>(pap, red, buf);
+    const float al_a = (act_a && pap[0] != 0.0) ? (float)(rzo_a / pap[0]) : 0.0f;
+    const float al_b = (act_b && pap[1] != 0.0) ? (float)(rzo_b / pap[1]) : 0.0f;
+    // A p is recomputed here (7 FMA per element) rather than held across the reduction
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const float2 ape = apply_A_at<EPT, RMAX>(pw, a, mbits, mp.lam, e);
+      float2 xe = sm_x[pidx(j0 + e)];
+      xe.x = fmaf(al_a, pw[e + RMAX].x, xe.x);
+      xe.y = fmaf(al_b, pw[e + RMAX].y, xe.y);
+      sm_x[pidx(j0 + e)] = xe;
+      r[e].x = fmaf(-al_a, ape.x, r[e].x);
+      r[e].y = fmaf(-al_b, ape.y, r[e].y);
+    }
+    it_a += act_a;
+    it_b += act_b;
+    precondition();
+    {
+      float s0 = 0.0f, s1 = 0.0f, q0 = 0.0f, q1 = 0.0f;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        s0 = fmaf(r[e].x, z[e].x, s0);
+        s1 = fmaf(r[e].y, z[e].y, s1);
+        q0 = fmaf(r[e].x, r[e].x, q0);
+        q1 = fmaf(r[e].y, r[e].y, q1);
+      }
+      rz[0] = s0; rz[1] = s1; rz[2] = q0; rz[3] = q1;
+    }
+    block_sum<4, T>(rz, red, buf);  // all reads of sm_p for this iteration are done
+    if (act_a) rel_a = sqrt(rz[2]) / bnorm_a;
+    if (act_b) rel_b = sqrt(rz[3]) / bnorm_b;
+    const bool na = act_a && rel_a > mp.tol, nb = act_b && rel_b > mp.tol;
+    const float be_a = (na && rzo_a != 0.0) ? (float)(rz[0] / rzo_a) : 0.0f;
+    const float be_b = (nb && rzo_b != 0.0) ? (float)(rz[1] / rzo_b) : 0.0f;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      float2 pe = sm_p[pidx(j0 + e)];
+      if (na) pe.x = fmaf(be_a, pe.x, z[e].x);
+      if (nb) pe.y = fmaf(be_b, pe.y, z[e].y);
+      sm_p[pidx(j0 + e)] = pe;
+    }
+    if (na) rzo_a = rz[0];
+    if (nb) rzo_b = rz[1];
+    act_a = na;
+    act_b = nb;
+    __syncthreads();  // publish sm_p before the next stencil
+  }
+
+  // true residual b - A x (FP32 operator, FP64 norms); write the solution
+  __syncthreads();
+  float2 b[EPT];
+  uint32_t mb2;
+  build_rhs<J, T, RMAX>(d2p, mask, prior, N, p, j0, ta, tb, mp.inv_s2, mp.lam, mb2, b);
+  float2 xw[WIN];
+  load_window<J, T, RMAX>(sm_x, j0, xw);
+  double tr[2];
+  {
+    float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      const float2 q = csub(b[e], apply_A_at<EPT, RMAX>(xw, a, mbits, mp.lam, e));
+      s0 = fmaf(q.x, q.x, s0);
+      s1 = fmaf(q.y, q.y, s1);
+      x2[(size_t)p * J + j0 + e] = xw[e + RMAX];
+    }
+    tr[0] = s0;
+    tr[1] = s1;
+  }
+  block_sum<2, T>(tr, red, buf);
+  if (tid == 0) {
+    iters[2 * p] = it_a;
+    iters[2 * p + 1] = it_b;
+    resid[2 * p] = (float)rel_a;
+    resid[2 * p + 1] = (float)rel_b;
+    resid[N + 2 * p] = (float)(sqrt(tr[0]) / bnorm_a);
+    resid[N + 2 * p + 1] = (float)(sqrt(tr[1]) / bnorm_b);
+  }
+}
+
+// time order [J][N] -> pair-packed [P][J] (initial guess)
+__global__ void k_time_to_pairs(const float* __restrict__ x, float2* __restrict__ x2, int N, int J) {
+  __shared__ float2 tile[32][33];
+  const int H = N / 2;
+  const int p0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+    const int jj = i / 32, pp = i % 32;
+    if (p0 + pp < H && j0 + jj < J)
+      tile[jj][pp] = reinterpret_cast<const float2*>(x + (size_t)(j0 + jj) * N)[p0 + pp];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+    const int pp = i / 32, jj = i % 32;
+    if (p0 + pp < H && j0 + jj < J) x2[(size_t)(p0 + pp) * J + j0 + jj] = tile[jj][pp];
+  }
+}
+
+}  // namespace ipfb

@@ -36,12 +36,7 @@ __device__ __forceinline__ void batched_pass(int Ns, int tid, LD ld, ST st) {
       const int c = CFAST ? w % NC : w / nb, b = CFAST ? w / NC : w % nb;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[it][r] = ld(c, b + r * nb);
-      if (Ns > 1) {
-        float2 wr[R];
-        twiddle_powers<R>(twiddle<INV>(b % Ns, Ns * R), wr);
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[it][r] = cmul(v[it][r], wr[r]);
-      }
+      if (Ns > 1) apply_twiddles<R>(v[it], twiddle<INV>(b % Ns, Ns * R));
       DFT<R, INV>::run(v[it]);
     }
   }
@@ -85,10 +80,16 @@ k4_upchan(UpchanSrc src, float2* __restrict__ out, float* __restrict__ x_out) {
   if constexpr (CU > 1) s = (int)cg::this_cluster().block_rank();
   const long long b = blockIdx.x / CU;
   const int p0 = s * PP;
+  // twiddle tables exp(-2 pi i t / L), L = 2Q, after the data array
+  float2* tw_hi = sm + padded_len(U * PP);
+  float2* tw_lo = tw_hi + 512;
+  twid2_fill<9, false>(tw_hi, tw_lo, 2 * Q, tid, T);
+  const Twid2<9> tw{tw_hi, tw_lo};
 
   // ---- load [U][PP] (element (j, p') at pidx(j*PP + p'))
   if (src.x) {
     const float2* x2 = reinterpret_cast<const float2*>(src.x) + b * (long long)Q;
+#pragma unroll 8
     for (int idx = tid; idx < U * PP; idx += T) {
       const int j = idx / PP, pp = idx % PP;
       sm[pidx(idx)] = x2[(long long)j * P + p0 + pp];
@@ -98,6 +99,7 @@ k4_upchan(UpchanSrc src, float2* __restrict__ out, float* __restrict__ x_out) {
     const int C = src.C;
     const int mpr = U / C;  // frames per residue in this block
     const long long mbase = b * (long long)mpr;
+#pragma unroll 8
     for (int idx = tid; idx < U * PP; idx += T) {
       const int mm = idx % mpr;
       const int r = (idx / mpr) % C;
@@ -120,10 +122,9 @@ k4_upchan(UpchanSrc src, float2* __restrict__ out, float* __restrict__ x_out) {
   {
     auto ld = [](int c, int i) { return sm[pidx(i * PP + c)]; };
     auto st = [](int c, int i, float2 v) { sm[pidx(i * PP + c)] = v; };
-    auto stl = [p0](int c, int i, float2 v) {
-      // i = k1, c = p'; global pair p = p0 + c
-      const float2 w = twiddle<false>((p0 + c) * i, Q);
-      sm[pidx(i * PP + c)] = cmul(v, w);
+    auto stl = [p0, tw](int c, int i, float2 v) {
+      // i = k1, c = p'; global pair p = p0 + c; exp(-2 pi i p k1 / Q) = tw(2 p k1)
+      sm[pidx(i * PP + c)] = cmul(v, tw(2 * (p0 + c) * i));
     };
     BatchedFFT<PP, U, T, false, true, 1, decltype(ld), decltype(st), decltype(stl)>::run(tid, ld, st, stl);
   }
@@ -140,7 +141,7 @@ k4_upchan(UpchanSrc src, float2* __restrict__ out, float* __restrict__ x_out) {
       for (int q = 0; q < CU; ++q) v[q] = peer[q][pidx(w)];
       DFT<CU, false>::run(v);
       float2 wr[CU];
-      twiddle_powers<CU>(twiddle<false>(pp, P), wr);
+      twiddle_powers<CU>(tw(2 * U * pp), wr);  // exp(-2 pi i p' / P)
 #pragma unroll
       for (int q = 0; q < CU; ++q) peer[q][pidx(w)] = cmul(v[q], wr[q]);
     }
@@ -188,7 +189,7 @@ k4_upchan(UpchanSrc src, float2* __restrict__ out, float* __restrict__ x_out) {
     const float2 E = cscale(cadd(zk, cconj(zm)), 0.5f);
     const float2 dd = csub(zk, cconj(zm));
     const float2 O = make_float2(0.5f * dd.y, -0.5f * dd.x);
-    const float2 wk = twiddle<false>(k, 2 * Q);
+    const float2 wk = tw(k);
     ob[k] = cadd(E, cmul(wk, O));
     if (k == 0) ob[Q] = make_float2(zk.x - zk.y, 0.0f);
   }

@@ -28,6 +28,14 @@ class Geom(ctypes.Structure):
                 ("nframes", ctypes.c_int), ("periodic", ctypes.c_int)]
 
 
+class MLParams(ctypes.Structure):
+    _fields_ = [("noise_var", ctypes.c_double), ("prior_weight", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("precond", ctypes.c_int)]
+
+
+PRECOND = {"none": 0, "wiener": 1, "learned": 2}
+
+
 class IpfbError(RuntimeError):
     def __init__(self, fn: str, rc: int):
         self.rc = rc
@@ -58,6 +66,8 @@ _SIGS = {
     "ipfb_wiener": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _D, _I, _P, _P, _SZ, _P]),
     "upchannelize": (_I, [_P, _I64, _I64, _P, _P, _SZ, _P]),
     "ipfb_wiener_upchannelize": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _D, _I, _I, _P, _P, _P, _SZ, _P]),
+    "ipfb_ml_solve": (_I, [ctypes.POINTER(Geom), _P, _P, _P, ctypes.POINTER(MLParams), _P, _P, _P, _P, _I, _P, _P,
+                           _P, _SZ, _P]),
 }
 
 
@@ -260,3 +270,34 @@ def ipfb_wiener_upchannelize(codes, scale, window, noise_level: float, upfactor:
                                           float(noise_level), int(bool(normalize)), int(upfactor), _ptr(out),
                                           _ptr(x_out), _ptr(ws), wsb, _stream()))
     return out, x_out
+
+
+def ml_solve(codes, scale, window, noise_var: float, mask, prior, prior_weight: float = 1.0,
+             precond: str = "none", tol: float = 1e-6, max_iter: int = 1000, x0=None, net=None,
+             workspace=None):
+    """ML inverse PFB with a time-domain prior by conjugate gradient.
+    codes uint8 [J, N/2]; scale float32 [N/2+1]; window float32 [ntap, N];
+    mask uint8 [J*N] (nonzero = saved); prior float32 [J*N]; x0 float32 [J*N] or None.
+    Returns (x float32 [J*N], iters int32 [N], resid float32 [2, N])."""
+    torch = _torch()
+    codes = _dev(codes, torch.uint8, "codes")
+    scale = _dev(scale, torch.float32, "scale")
+    window = _dev(window, torch.float32, "window")
+    mask = _dev(mask, torch.uint8, "mask")
+    prior = _dev(prior, torch.float32, "prior")
+    p, N = window.shape
+    J = codes.shape[0]
+    g = geom(N, p, J)
+    if x0 is not None:
+        x = _dev(x0, torch.float32, "x0").clone()
+    else:
+        x = torch.empty(J * N, dtype=torch.float32, device=codes.device)
+    iters = torch.empty(N, dtype=torch.int32, device=codes.device)
+    resid = torch.empty((2, N), dtype=torch.float32, device=codes.device)
+    prm = MLParams(float(noise_var), float(prior_weight), float(tol), int(max_iter), PRECOND[precond])
+    ws, wsb = _workspace(workspace_size(g, OP_ML), codes.device, workspace)
+    _check("ipfb_ml_solve", lib().ipfb_ml_solve(ctypes.byref(g), _ptr(codes), _ptr(scale), _ptr(window),
+                                                ctypes.byref(prm), _ptr(mask), _ptr(prior), _ptr(net), _ptr(x),
+                                                int(x0 is not None), _ptr(iters), _ptr(resid), _ptr(ws), wsb,
+                                                _stream()))
+    return x, iters, resid
