@@ -53,9 +53,10 @@ struct Twid2 {
 // Fill the two tables for length L (power of two, > 2^LO) with T threads.
 template <int LO, bool INV>
 __device__ __forceinline__ void twid2_fill(float2* hi, float2* lo, int L, int tid, int T) {
-  const int nhi = L >> LO;
-  for (int i = tid; i < nhi; i += T) hi[i] = twiddle<INV>(i << LO, L);
-  for (int i = tid; i < (1 << LO); i += T) lo[i] = twiddle<INV>(i, L);
+  const int nhi = (L >> LO) > 0 ? (L >> LO) : 1;
+  const int nlo = (1 << LO) < L ? (1 << LO) : L;
+  for (int i = tid; i < nhi; i += T) hi[i] = twiddle<INV>((i << LO) % L, L);
+  for (int i = tid; i < nlo; i += T) lo[i] = twiddle<INV>(i, L);
 }
 
 // ----------------------------------------------------------------------------
@@ -236,36 +237,102 @@ __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4); }
 
 // ----------------------------------------------------------------------------
-// One Stockham decimation-in-time radix-R pass of an S-point FFT (S = Ns*R*...)
-// executed by T threads (BPT butterflies per thread, b = tid + i*T).
-//   input element i  : ld(i)      output element i : st(i, v)
+// Addressing policies for the Stockham passes.  A pass loads element b + r*nb of
+// its input and stores element j + r*Ns of its output (r < R); the policies turn
+// that into a per-butterfly base plus a compile-time offset per r wherever the
+// layout allows it.
+//   SPad : the padded shared array (element i at pidx(i)); constant offsets when
+//          nb % 16 == 0 (loads) and Ns % 16 == 0 or Ns == 1 with R % 16 == 0 (stores).
+//   GMem : a plain array (global memory), element i at p[i].
+//   FnLd / FnSt : arbitrary element functions (computed loads, scattered stores).
+// ----------------------------------------------------------------------------
+struct SPad {
+  float2* p;
+  template <int R, int NB>
+  __device__ __forceinline__ int lbase(int b) const {
+    if constexpr (NB % 16 == 0) return pidx(b);
+    else return b;
+  }
+  template <int R, int NB>
+  __device__ __forceinline__ float2 ld(int base, int r) const {
+    if constexpr (NB % 16 == 0) return p[base + r * (NB + NB / 16)];
+    else return p[pidx(base + r * NB)];
+  }
+  template <int R, int NS>
+  __device__ __forceinline__ int sbase(int j) const {
+    if constexpr ((NS == 1 && R % 16 == 0) || NS % 16 == 0) return pidx(j);
+    else return j;
+  }
+  template <int R, int NS>
+  __device__ __forceinline__ void st(int base, int r, float2 v) const {
+    if constexpr (NS == 1 && R % 16 == 0) p[base + r + r / 16] = v;
+    else if constexpr (NS % 16 == 0) p[base + r * (NS + NS / 16)] = v;
+    else p[pidx(base + r * NS)] = v;
+  }
+};
+struct GMem {
+  float2* p;
+  template <int R, int NB>
+  __device__ __forceinline__ int lbase(int b) const { return b; }
+  template <int R, int NB>
+  __device__ __forceinline__ float2 ld(int base, int r) const { return p[base + r * NB]; }
+  template <int R, int NS>
+  __device__ __forceinline__ int sbase(int j) const { return j; }
+  template <int R, int NS>
+  __device__ __forceinline__ void st(int base, int r, float2 v) const { p[base + r * NS] = v; }
+};
+template <class F>
+struct FnLd {
+  F f;
+  template <int R, int NB>
+  __device__ __forceinline__ int lbase(int b) const { return b; }
+  template <int R, int NB>
+  __device__ __forceinline__ float2 ld(int base, int r) const { return f(base + r * NB); }
+};
+template <class F>
+struct FnSt {
+  F f;
+  template <int R, int NS>
+  __device__ __forceinline__ int sbase(int j) const { return j; }
+  template <int R, int NS>
+  __device__ __forceinline__ void st(int base, int r, float2 v) const { f(base + r * NS, v); }
+};
+template <class F>
+__device__ __forceinline__ FnLd<F> fn_ld(F f) { return FnLd<F>{f}; }
+template <class F>
+__device__ __forceinline__ FnSt<F> fn_st(F f) { return FnSt<F>{f}; }
+
+// ----------------------------------------------------------------------------
+// One Stockham decimation-in-time radix-R pass of an S-point FFT (sub-size Ns ->
+// Ns*R) executed by T threads (BPT butterflies per thread, b = tid + i*T).
 // Butterfly b reads elements b + r*S/R, applies exp(-+2 pi i r k / (Ns R)) with
 // k = b mod Ns, does an R-point DFT and writes (b/Ns)*Ns*R + k + r*Ns.
-// If INPLACE, a block barrier separates all loads from all stores.
+// A block barrier separates all loads from all stores (in-place safe).
 // ----------------------------------------------------------------------------
-template <int R, int BPT, int T, bool INV, bool INPLACE, class LD, class ST>
-__device__ __forceinline__ void stockham_pass(int S, int Ns, int tid, LD ld, ST st) {
-  const int nb = S / R;
+template <int R, int BPT, int T, bool INV, int S, int Ns, class LD, class ST>
+__device__ __forceinline__ void stockham_pass(int tid, const LD& ld, const ST& st) {
+  constexpr int nb = S / R;
   float2 v[BPT][R];
 #pragma unroll
   for (int i = 0; i < BPT; ++i) {
     const int b = tid + i * T;
-    if (b < nb) {
+    if (nb % T == 0 || b < nb) {
+      const int lb = ld.template lbase<R, nb>(b);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = ld(b + r * nb);
-      if (Ns > 1) apply_twiddles<R>(v[i], twiddle<INV>(b % Ns, Ns * R));
+      for (int r = 0; r < R; ++r) v[i][r] = ld.template ld<R, nb>(lb, r);
+      if constexpr (Ns > 1) apply_twiddles<R>(v[i], twiddle<INV>(b % Ns, Ns * R));
       DFT<R, INV>::run(v[i]);
     }
   }
-  if (INPLACE) __syncthreads();
+  __syncthreads();
 #pragma unroll
   for (int i = 0; i < BPT; ++i) {
     const int b = tid + i * T;
-    if (b < nb) {
-      const int k = b % Ns;
-      const int j = (b / Ns) * Ns * R + k;
+    if (nb % T == 0 || b < nb) {
+      const int j = (b / Ns) * Ns * R + b % Ns;
+      const int sb = st.template sbase<R, Ns>(j);
 #pragma unroll
-      for (int r = 0; r < R; ++r) st(j + r * Ns, v[i][r]);
+      for (int r = 0; r < R; ++r) st.template st<R, Ns>(sb, r, v[i][r]);
     }
   }
 }
@@ -281,40 +348,44 @@ __host__ __device__ constexpr int next_radix(int S, int Ns, int MAXR = 32) {
          : (MAXR < 16 ? MAXR : 16);
 }
 
-// Full S-point FFT by T threads.  The first pass reads ld_first, the last writes
-// st_last, every intermediate pass works in place on the padded smem array sm.
-// Callers must __syncthreads() before (if ld_first reads smem written by others)
-// and after (if st_last writes smem read by others).
-template <int S, int T, bool INV, int Ns, class LDF, class STL, int MAXR = 32>
-struct FFTPasses {
-  __device__ __forceinline__ static void run(float2* sm, int tid, LDF ldf, STL stl) {
-    constexpr int R = next_radix(S, Ns, MAXR);
-    constexpr int BPT = (S / R + T - 1) / T;
-    constexpr bool first = (Ns == 1);
-    constexpr bool last = (Ns * R == S);
-    auto lds = [sm](int i) { return sm[pidx(i)]; };
-    auto sts = [sm](int i, float2 v) { sm[pidx(i)] = v; };
-    // every pass separates its loads from its stores by a barrier, so the first
-    // pass may read, and the last pass may write, the same smem array
-    if constexpr (first && last) {
-      stockham_pass<R, BPT, T, INV, true>(S, Ns, tid, ldf, stl);
-    } else if constexpr (first) {
-      stockham_pass<R, BPT, T, INV, true>(S, Ns, tid, ldf, sts);
-      __syncthreads();
-      FFTPasses<S, T, INV, Ns * R, LDF, STL, MAXR>::run(sm, tid, ldf, stl);
-    } else if constexpr (last) {
-      stockham_pass<R, BPT, T, INV, true>(S, Ns, tid, lds, stl);
-    } else {
-      stockham_pass<R, BPT, T, INV, true>(S, Ns, tid, lds, sts);
-      __syncthreads();
-      FFTPasses<S, T, INV, Ns * R, LDF, STL, MAXR>::run(sm, tid, ldf, stl);
-    }
+// radix of the last pass of the plan chosen by next_radix for an S-point transform
+__host__ __device__ constexpr int last_radix(int S, int MAXR = 32) {
+  int Ns = 1;
+  while (true) {
+    const int R = next_radix(S, Ns, MAXR);
+    if (Ns * R == S) return R;
+    Ns *= R;
   }
-};
+}
 
-template <int S, int T, bool INV, class LDF, class STL, int MAXR = 32>
-__device__ __forceinline__ void block_fft(float2* sm, int tid, LDF ldf, STL stl) {
-  FFTPasses<S, T, INV, 1, LDF, STL, MAXR>::run(sm, tid, ldf, stl);
+// Full S-point FFT by T threads.  The first pass reads `first` (a policy), the
+// last writes `last`, every intermediate pass works in place on the padded smem
+// array sm.  Passes are separated by block barriers.
+template <int S, int T, bool INV, int Ns, int MAXR, class LDF, class STL>
+__device__ __forceinline__ void fft_passes(float2* sm, int tid, const LDF& first, const STL& last) {
+  constexpr int R = next_radix(S, Ns, MAXR);
+  constexpr int BPT = (S / R + T - 1) / T;
+  constexpr bool is_first = (Ns == 1);
+  constexpr bool is_last = (Ns * R == S);
+  const SPad pad{sm};
+  if constexpr (is_first && is_last) {
+    stockham_pass<R, BPT, T, INV, S, Ns>(tid, first, last);
+  } else if constexpr (is_first) {
+    stockham_pass<R, BPT, T, INV, S, Ns>(tid, first, pad);
+    __syncthreads();
+    fft_passes<S, T, INV, Ns * R, MAXR>(sm, tid, first, last);
+  } else if constexpr (is_last) {
+    stockham_pass<R, BPT, T, INV, S, Ns>(tid, pad, last);
+  } else {
+    stockham_pass<R, BPT, T, INV, S, Ns>(tid, pad, pad);
+    __syncthreads();
+    fft_passes<S, T, INV, Ns * R, MAXR>(sm, tid, first, last);
+  }
+}
+
+template <int S, int T, bool INV, int MAXR = 32, class LDF, class STL>
+__device__ __forceinline__ void block_fft(float2* sm, int tid, const LDF& first, const STL& last) {
+  fft_passes<S, T, INV, 1, MAXR>(sm, tid, first, last);
 }
 
 }  // namespace ipfb

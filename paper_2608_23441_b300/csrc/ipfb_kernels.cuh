@@ -44,6 +44,12 @@ k2_unpack_irfft(const uint8_t* __restrict__ codes, const float* __restrict__ sca
   const int j = C * (m0 + f) + r;
   const uint8_t* row = codes + (size_t)j * H;
   const float pre = 0.5f / (float)H;
+  // exp(+2 pi i k / N), N = 2H, from two tables of 64 entries shared by the CTA
+  float2* tw_hi = smem + F * k2_frame_stride(H);
+  float2* tw_lo = tw_hi + 128;
+  twid2_fill<7, true>(tw_hi, tw_lo, 2 * H, threadIdx.x, TPF * F);
+  __syncthreads();
+  const Twid2<7> tw{tw_hi, tw_lo};
 
   // pre-processing: each thread forms Z[k] and Z[H-k] for k in [0, H/2]
   for (int k = tid; k <= H / 2; k += TPF) {
@@ -63,7 +69,7 @@ k2_unpack_irfft(const uint8_t* __restrict__ codes, const float* __restrict__ sca
       ym = make_float2(nib(bm, 0) * scale[km], nib(bm, 1) * scale[km]);
     }
     // E, O at k:   E = (yk + conj ym)/2, O = (yk - conj ym) w/2, w = e^{+2 pi i k/N}
-    const float2 w = twiddle<true>(k, 2 * H);
+    const float2 w = tw(k);
     const float2 e = cadd(yk, cconj(ym));
     const float2 o = cmul(csub(yk, cconj(ym)), w);
     const float2 zk = cscale(cadd(e, cmul_i(o)), pre);
@@ -75,9 +81,7 @@ k2_unpack_irfft(const uint8_t* __restrict__ codes, const float* __restrict__ sca
     if (k != 0 && km != k) sm[pidx(km)] = zm;
   }
   __syncthreads();
-  auto lds = [sm](int i) { return sm[pidx(i)]; };
-  auto sts = [sm](int i, float2 v) { sm[pidx(i)] = v; };
-  block_fft<H, TPF, true>(sm, tid, lds, sts);
+  block_fft<H, TPF, true>(sm, tid, SPad{sm}, SPad{sm});
   __syncthreads();
   // transposed store: for each pair p, F consecutive m of residue r
   for (int idx = threadIdx.x; idx < H * F; idx += TPF * F) {
@@ -128,7 +132,7 @@ __device__ __forceinline__ float2 gain_at(const float* taps, int k, float2 e1, c
     const double g = (double)gp.gnorm * (double)gp.invJ / den;
     return make_float2((float)(wx * g), (float)(wy * g));
   }
-  const float g = gp.gnorm * gp.invJ / (a2 + gp.phi2);
+  const float g = __fdividef(gp.gnorm * gp.invJ, a2 + gp.phi2);
   return make_float2(W.x * g, W.y * g);
 }
 
@@ -172,13 +176,8 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
     tb[t] = (t < gp.ntap) ? __ldg(window + (size_t)t * N + 2 * p + 1) : 0.0f;
   }
 
-  auto ldg = [base](int i) { return base[i]; };
-  auto lds = [](int i) { return sm[pidx(i)]; };
-  auto sts = [](int i, float2 v) { sm[pidx(i)] = v; };
-  auto stg = [base](int i, float2 v) { base[i] = v; };
-
   // 1. forward local FFT: global -> smem
-  block_fft<S, T, false>(sm, tid, ldg, sts);
+  block_fft<S, T, false>(sm, tid, GMem{base}, SPad{sm});
   if constexpr (C > 1) {
     cg::this_cluster().sync();
   } else {
@@ -216,12 +215,17 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
       DFT<C, false>::run(z0);
       if (pairtask) DFT<C, false>::run(z1);
     }
-    // gains: z0[ka] is mode kb0 + S*ka
+    // gains: z0[ka] is mode k = kb0 + S*ka, e^{-2 pi i k/J} = e0 e^{-2 pi i ka/C}
+    float2 e0;
+    if constexpr (C > 1)
+      e0 = w0[1];
+    else
+      e0 = twiddle<false>(kb0, J);
     if (pairtask) {
 #pragma unroll
       for (int ka = 0; ka < C; ++ka) {
         const int k = kb0 + S * ka;
-        const float2 e1 = twiddle<false>(k, J);
+        const float2 e1 = rotq<C, false>(e0, ka);
         const float2 ga = gain_at<NT>(ta, k, e1, gp), gb = gain_at<NT>(tb, k, e1, gp);
         split_gain(z0[ka], z1[C - 1 - ka], ga, gb);
       }
@@ -231,7 +235,7 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
       for (int ka = 0; ka <= C / 2; ++ka) {
         const int km = (C - ka) % C;
         const int k = S * ka;
-        const float2 e1 = twiddle<false>(k, J);
+        const float2 e1 = rotq<C, false>(make_float2(1.0f, 0.0f), ka);
         const float2 ga = gain_at<NT>(ta, k, e1, gp), gb = gain_at<NT>(tb, k, e1, gp);
         float2 a = z0[ka], b = z0[km];
         split_gain(a, b, ga, gb);
@@ -244,7 +248,7 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
       for (int ka = 0; ka < (C + 1) / 2; ++ka) {
         const int km = C - 1 - ka;
         const int k = kb0 + S * ka;
-        const float2 e1 = twiddle<false>(k, J);
+        const float2 e1 = rotq<C, false>(e0, ka);
         const float2 ga = gain_at<NT>(ta, k, e1, gp), gb = gain_at<NT>(tb, k, e1, gp);
         float2 a = z0[ka], b = z0[km];
         split_gain(a, b, ga, gb);
@@ -274,7 +278,7 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
     __syncthreads();
   }
   // 4. inverse local FFT: smem -> global (in place over this CTA's input run)
-  block_fft<S, T, true>(sm, tid, lds, stg);
+  block_fft<S, T, true>(sm, tid, SPad{sm}, GMem{base});
 }
 
 // ----------------------------------------------------------------------------

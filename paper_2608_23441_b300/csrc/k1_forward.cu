@@ -12,7 +12,7 @@ cudaError_t smem_attr(K kern, size_t bytes) {
 template <int H>
 size_t k1_smem() {
   constexpr int F = fpc_for(H);
-  const size_t a = (size_t)F * padded_len(H) * sizeof(float2);
+  const size_t a = ((size_t)F * padded_len(H) + 256) * sizeof(float2);
   const size_t b = (size_t)F * 4 * (H / 2 + 1) * sizeof(float);
   return a > b ? a : b;
 }

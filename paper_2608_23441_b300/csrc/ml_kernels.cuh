@@ -52,10 +52,8 @@ template <int J, int T, int NT>
 __device__ __forceinline__ void wiener_precond_pair(float2* sm, const float* ta, const float* tb, int ntap,
                                                    float inv_s2, float lam_ma, float lam_mb) {
   constexpr int NMAX = NT > 0 ? NT : kMlMaxTaps;
-  auto lds = [sm](int i) { return sm[pidx(i)]; };
-  auto sts = [sm](int i, float2 v) { sm[pidx(i)] = v; };
   const int tid = threadIdx.x;
-  block_fft<J, T, false, decltype(lds), decltype(sts), 8>(sm, tid, lds, sts);
+  block_fft<J, T, false, 8>(sm, tid, SPad{sm}, SPad{sm});
   __syncthreads();
   for (int k = tid; k <= J / 2; k += T) {
     const int km = (J - k) % J;
@@ -86,7 +84,7 @@ __device__ __forceinline__ void wiener_precond_pair(float2* sm, const float* ta,
     if (km != k) sm[pidx(km)] = zm;
   }
   __syncthreads();
-  block_fft<J, T, true, decltype(lds), decltype(sts), 8>(sm, tid, lds, sts);
+  block_fft<J, T, true, 8>(sm, tid, SPad{sm}, SPad{sm});
   __syncthreads();
 }
 

@@ -25,22 +25,22 @@ __device__ __forceinline__ void frame_rfft_core(const float2* __restrict__ x2, c
     }
     return acc;
   };
-  auto sts = [sm](int i, float2 v) { sm[pidx(i)] = v; };
-  block_fft<H, TPF, false>(sm, tid, ldp, sts);
+  block_fft<H, TPF, false>(sm, tid, fn_ld(ldp), SPad{sm});
 }
 
 // Post-processing of the half-length FFT into the real-input spectrum:
 //   E = (Z[k] + conj Z[H-k])/2, O = (Z[k] - conj Z[H-k])/(2i),
 //   Y[k] = E + e^{-2 pi i k/N} O,   Y[H-k] = conj(E) - e^{+2 pi i k/N} conj(O)... (see below)
 // Computes Y[k] and Y[H-k] for k in [0, H/2]; k = 0 also gives Y[H] (Nyquist).
-__device__ __forceinline__ void rfft_post(const float2* sm, int H, int k, float2& yk, float2& ym) {
+__device__ __forceinline__ void rfft_post(const float2* sm, int H, int k, const Twid2<7>& tw, float2& yk,
+                                          float2& ym) {
   const int km = H - k;
   const float2 zk = sm[pidx(k)];
   const float2 zm = sm[pidx(km == H ? 0 : km)];
   const float2 E = cscale(cadd(zk, cconj(zm)), 0.5f);
   const float2 dd = csub(zk, cconj(zm));
   const float2 O = make_float2(0.5f * dd.y, -0.5f * dd.x);  // dd / (2i)
-  const float2 w = twiddle<false>(k, 2 * H);                  // e^{-2 pi i k / N}
+  const float2 w = tw(k);                                     // e^{-2 pi i k / N}
   yk = cadd(E, cmul(w, O));
   // at H-k: E' = conj(E), O' = conj(O), twiddle e^{-2 pi i (H-k)/N} = -conj(w)
   ym = csub(cconj(E), cmul(cconj(w), cconj(O)));
@@ -58,6 +58,9 @@ k1_pfb_power(const float* __restrict__ x, const float* __restrict__ window, int 
   float2* sm = smem + f * padded_len(H);
   const float2* x2 = reinterpret_cast<const float2*>(x);
   const float2* w2 = reinterpret_cast<const float2*>(window);
+  float2* tw_hi = smem + F * padded_len(H);
+  twid2_fill<7, false>(tw_hi, tw_hi + 128, 2 * H, threadIdx.x, TPF * F);
+  const Twid2<7> tw{tw_hi, tw_hi + 128};
   float re_k[KPT], im_k[KPT], re_m[KPT], im_m[KPT];
 #pragma unroll
   for (int i = 0; i < KPT; ++i) re_k[i] = im_k[i] = re_m[i] = im_m[i] = 0.0f;
@@ -72,7 +75,7 @@ k1_pfb_power(const float* __restrict__ x, const float* __restrict__ window, int 
         const int k = tid + i * TPF;
         if (k <= H / 2) {
           float2 yk, ym;
-          rfft_post(sm, H, k, yk, ym);
+          rfft_post(sm, H, k, tw, yk, ym);
           re_k[i] = fmaf(yk.x, yk.x, re_k[i]);
           im_k[i] = fmaf(yk.y, yk.y, im_k[i]);
           re_m[i] = fmaf(ym.x, ym.x, re_m[i]);
@@ -141,6 +144,9 @@ k1_pfb_quant(const float* __restrict__ x, const float* __restrict__ window, int 
   float2* sm = smem + f * padded_len(H);
   const float2* x2 = reinterpret_cast<const float2*>(x);
   const float2* w2 = reinterpret_cast<const float2*>(window);
+  float2* tw_hi = smem + F * padded_len(H);
+  twid2_fill<7, false>(tw_hi, tw_hi + 128, 2 * H, threadIdx.x, TPF * F);
+  const Twid2<7> tw{tw_hi, tw_hi + 128};
   for (int jb = blockIdx.x * F; jb < J; jb += gridDim.x * F) {
     const int j = jb + f;
     const bool live = j < J;
@@ -151,7 +157,7 @@ k1_pfb_quant(const float* __restrict__ x, const float* __restrict__ window, int 
       float2* srow = spectra ? spectra + (size_t)j * (H + 1) : nullptr;
       for (int k = tid; k <= H / 2; k += TPF) {
         float2 yk, ym;
-        rfft_post(sm, H, k, yk, ym);
+        rfft_post(sm, H, k, tw, yk, ym);
         const int km = H - k;
         if (k == 0) {
           row[0] = pack2(quant4(yk.x, scale[0]), quant4(ym.x, scale[H]));

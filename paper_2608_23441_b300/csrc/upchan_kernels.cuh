@@ -24,8 +24,12 @@ namespace cg = cooperative_groups;
 // Batched Stockham radix-R pass over NC sequences of length S.  Work item w covers
 // sequence c = w % NC, butterfly b = w / NC when CFAST (sequences interleaved in
 // memory), else b = w % nb, c = w / nb (sequences contiguous).  ld(c, i) / st(c, i, v).
-template <int R, int NC, int S, int T, bool INV, bool CFAST, class LD, class ST>
-__device__ __forceinline__ void batched_pass(int Ns, int tid, LD ld, ST st) {
+struct NoPost {
+  __device__ __forceinline__ void operator()(int, int, int, float2*) const {}
+};
+
+template <int R, int NC, int S, int T, bool INV, bool CFAST, class LD, class ST, class POST = NoPost>
+__device__ __forceinline__ void batched_pass(int Ns, int tid, LD ld, ST st, POST post = POST{}) {
   constexpr int nb = S / R;
   constexpr int IPT = (NC * nb + T - 1) / T;
   float2 v[IPT][R];
@@ -48,23 +52,40 @@ __device__ __forceinline__ void batched_pass(int Ns, int tid, LD ld, ST st) {
       const int c = CFAST ? w % NC : w / nb, b = CFAST ? w / NC : w % nb;
       const int k = b % Ns;
       const int j = (b / Ns) * Ns * R + k;
+      post(c, j, Ns, v[it]);
 #pragma unroll
       for (int r = 0; r < R; ++r) st(c, j + r * Ns, v[it][r]);
     }
   }
 }
 
-template <int NC, int S, int T, bool INV, bool CFAST, int Ns, class LDI, class STI, class STL>
+template <int NC, int S, int T, bool INV, bool CFAST, int Ns, class LDI, class STI, class STL, class POST = NoPost>
 struct BatchedFFT {
-  __device__ __forceinline__ static void run(int tid, LDI ldi, STI sti, STL stl) {
+  __device__ __forceinline__ static void run(int tid, LDI ldi, STI sti, STL stl, POST post = POST{}) {
     constexpr int R = next_radix(S, Ns);
     if constexpr (Ns * R == S) {
-      batched_pass<R, NC, S, T, INV, CFAST>(Ns, tid, ldi, stl);
+      batched_pass<R, NC, S, T, INV, CFAST>(Ns, tid, ldi, stl, post);
     } else {
       batched_pass<R, NC, S, T, INV, CFAST>(Ns, tid, ldi, sti);
       __syncthreads();
-      BatchedFFT<NC, S, T, INV, CFAST, Ns * R, LDI, STI, STL>::run(tid, ldi, sti, stl);
+      BatchedFFT<NC, S, T, INV, CFAST, Ns * R, LDI, STI, STL, POST>::run(tid, ldi, sti, stl, post);
     }
+  }
+};
+
+// Step-(2) twiddle of the up-channelizer applied to the R outputs k1 = j + r*Ns of
+// one butterfly of pair p = p0 + c: exp(-2 pi i p k1 / Q) = base * step^r with
+// base = exp(-2 pi i p j / Q), step = exp(-2 pi i p Ns / Q) (tables over L = 2Q).
+template <int R>
+struct UpchanTwiddle {
+  Twid2<9> tw;
+  int p0;
+  __device__ __forceinline__ void operator()(int c, int j, int Ns, float2* v) const {
+    const int p = p0 + c;
+    const float2 base = tw(2 * p * j);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = cmul(v[r], base);
+    apply_twiddles<R>(v, tw(2 * p * Ns));
   }
 };
 
@@ -122,11 +143,10 @@ k4_upchan(UpchanSrc src, float2* __restrict__ out, float* __restrict__ x_out) {
   {
     auto ld = [](int c, int i) { return sm[pidx(i * PP + c)]; };
     auto st = [](int c, int i, float2 v) { sm[pidx(i * PP + c)] = v; };
-    auto stl = [p0, tw](int c, int i, float2 v) {
-      // i = k1, c = p'; global pair p = p0 + c; exp(-2 pi i p k1 / Q) = tw(2 p k1)
-      sm[pidx(i * PP + c)] = cmul(v, tw(2 * (p0 + c) * i));
-    };
-    BatchedFFT<PP, U, T, false, true, 1, decltype(ld), decltype(st), decltype(stl)>::run(tid, ld, st, stl);
+    constexpr int RL = last_radix(U);
+    const UpchanTwiddle<RL> post{tw, p0};
+    BatchedFFT<PP, U, T, false, true, 1, decltype(ld), decltype(st), decltype(st), UpchanTwiddle<RL>>::run(
+        tid, ld, st, st, post);
   }
   if constexpr (CU > 1) {
     cg::this_cluster().sync();
