@@ -115,6 +115,25 @@ int pfb_forward(const ipfb_geom* g, const float* x, const float* window, const f
                 void* stream);
 
 /*
+ * pfb_forward without a workspace (the paper has no counterpart: this is a
+ * calling convention, not part of the method).  Same computation and outputs as
+ * pfb_forward with scale_in = NULL.  For callers that cannot give the library a
+ * scratch buffer: streaming ingest code that reserves all device memory at
+ * start-up and must not allocate afterwards (cudaMalloc can synchronize the
+ * device and stall the stream), or host frameworks that only pass in the buffers
+ * they own.  The FP64 power sums live in a fixed array inside the library sized
+ * for lblock <= 16384 (131 KB held on every GPU that loads the library, until the
+ * process exits); larger lblock returns IPFB_ERR_UNSUPPORTED before anything is
+ * enqueued.  No device memory is allocated.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, once per device); make that
+ * first call before any stream capture.  All calls share the array: each clears
+ * it on its own stream, and calls that overlap on the GPU (other streams or host
+ * threads on the same device) race on it -- serialize them.
+ */
+int pfb_forward_noalloc(const ipfb_geom* g, const float* x, const float* window, uint8_t* codes,
+                        float* scale_out, float* spectra_out, void* stream);
+
+/*
  * The quantize-and-pack step alone (Sec. 4.3 quantizer) on given spectra:
  * spectra: float2 [nspec][lblock/2 + 1]; scale: float [lblock/2 + 1];
  * codes: uint8 [nspec][lblock/2].  Same decision rule as pfb_forward.
