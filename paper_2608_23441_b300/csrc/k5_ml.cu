@@ -9,7 +9,7 @@ cudaError_t k5(const float2* d2, float2* x2, const uint8_t* mask, const float* p
                const MLParams& mp, int* iters, float* resid, cudaStream_t st) {
   constexpr int T = (J / 16 < 32) ? 32 : (J / 16 > 512 ? 512 : J / 16);
   auto kern = k5_ml_cg<J, T, RMAX, PRE, NT>;
-  size_t smem = 2 * (size_t)padded_len(J) * sizeof(float2) + 2 * (size_t)(T / 32) * 4 * sizeof(double);
+  size_t smem = 2 * (size_t)padded_len(J) * sizeof(float2) + 24 * sizeof(double) + (size_t)(T / 32) * 4 * sizeof(float);
   if (PRE == 1) smem += (size_t)padded_len(J) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

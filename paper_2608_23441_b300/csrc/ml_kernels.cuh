@@ -19,33 +19,46 @@ namespace ipfb {
 
 constexpr int kMlMaxTaps = 16;
 
-// FP64 sum of K values over the CTA (warp shuffles, then every thread adds the
-// per-warp partials).  buf alternates between two slots so that one barrier per
-// call is enough.
-template <int K, int T>
-__device__ __forceinline__ void block_sum(double (&v)[K], double* red /* [2][T/32][K] */, int& buf) {
+// Sum of K values over the CTA: FP32 within each warp (shuffles), then one warp
+// adds the per-warp partials in FP64 and (optionally) derives the CG scalars; the
+// results are broadcast through shared memory.  FP64 work is O(warps) per call,
+// since FP64 throughput on this part is a small fraction of FP32.
+//   part : [T/32][K] floats,  res : [K + 8] doubles (sums, then scalars)
+template <int K, int T, class SCALARS>
+__device__ __forceinline__ void block_sum_bcast(float (&v)[K], float* part, double* res, SCALARS scalars) {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
   }
   constexpr int W = T / 32;
-  double* slot = red + buf * W * K;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) slot[warp * K + k] = v[k];
+    for (int k = 0; k < K; ++k) part[warp * K + k] = v[k];
   }
   __syncthreads();
+  if (warp == 0) {
+    double acc[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double s = 0.0;
-#pragma unroll 8
-    for (int w = 0; w < W; ++w) s += slot[w * K + k];
-    v[k] = s;
+    for (int k = 0; k < K; ++k) {
+      acc[k] = lane < W ? (double)part[lane * K + k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) res[k] = acc[k];
+      scalars(acc, res + K);
+    }
   }
-  buf ^= 1;
+  __syncthreads();
 }
+
+struct NoScalars {
+  template <class A>
+  __device__ __forceinline__ void operator()(const A&, double*) const {}
+};
 
 // Wiener preconditioner on the pair held as r = (r_a, r_b) in smem (complex r_a + i r_b)
 template <int J, int T, int NT>
@@ -160,14 +173,14 @@ k5_ml_cg(const float2* __restrict__ d2, float2* __restrict__ x2, const uint8_t* 
   extern __shared__ float2 smem[];
   float2* sm_x = smem;                                  // [padded J] solution
   float2* sm_p = sm_x + padded_len(J);                  // [padded J] search direction
-  double* red = reinterpret_cast<double*>(sm_p + padded_len(J));  // [2][T/32][4]
-  float2* sm_f = reinterpret_cast<float2*>(red + 2 * (T / 32) * 4);  // [padded J] FFT work (PRE == 1)
+  double* res = reinterpret_cast<double*>(sm_p + padded_len(J));  // [8] sums + [16] CG scalars
+  float* part = reinterpret_cast<float*>(res + 24);                 // [T/32][4] warp partials
+  float2* sm_f = reinterpret_cast<float2*>(part + (T / 32) * 4);    // [padded J] FFT work (PRE == 1)
 
   const int tid = threadIdx.x;
   const int p = blockIdx.x;
   const int j0 = tid * EPT;
   const float2* d2p = d2 + (size_t)p * J;
-  int buf = 0;
 
   constexpr int NMAX = NT > 0 ? NT : kMlMaxTaps;
   float ta[NMAX], tb[NMAX];
@@ -191,8 +204,12 @@ k5_ml_cg(const float2* __restrict__ d2, float2* __restrict__ x2, const uint8_t* 
   uint32_t mbits;
   float2 r[EPT];
   build_rhs<J, T, RMAX>(d2p, mask, prior, N, p, j0, ta, tb, mp.inv_s2, mp.lam, mbits, r);
-  double bn[4];
+  // CG state shared through smem (written by one thread of warp 0):
+  //   st[0..1] alpha, st[2..3] beta, st[4] active flags, st[5..6] |b|, st[7..8] r.z old
+  //   st[9..10] relative residual, st[11..12] iterations
+  double* st = res + 8;
   {
+    float bn[4];
     float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
@@ -201,14 +218,20 @@ k5_ml_cg(const float2* __restrict__ d2, float2* __restrict__ x2, const uint8_t* 
     }
     bn[0] = s0;
     bn[1] = s1;
-    bn[2] = __popc(mbits & 0xFFFFu);
-    bn[3] = __popc(mbits >> 16);
+    bn[2] = (float)__popc(mbits & 0xFFFFu);
+    bn[3] = (float)__popc(mbits >> 16);
+    block_sum_bcast<4, T>(bn, part, res, [](const double* a, double* o) {
+      (void)o;
+    });
   }
-  block_sum<4, T>(bn, red, buf);
-  const double bnorm_a = bn[0] > 0.0 ? sqrt(bn[0]) : 1.0;
-  const double bnorm_b = bn[1] > 0.0 ? sqrt(bn[1]) : 1.0;
-  const float lam_ma = mp.lam * (float)(bn[2] / (double)J);
-  const float lam_mb = mp.lam * (float)(bn[3] / (double)J);
+  if (tid == 0) {
+    st[5] = res[0] > 0.0 ? (double)sqrtf((float)res[0]) : 1.0;
+    st[6] = res[1] > 0.0 ? (double)sqrtf((float)res[1]) : 1.0;
+    st[11] = 0.0;
+    st[12] = 0.0;
+  }
+  const float lam_ma = mp.lam * (float)(res[2] / (double)J);
+  const float lam_mb = mp.lam * (float)(res[3] / (double)J);
 
   // x0 (and r0 = b - A x0)
 #pragma unroll
@@ -236,31 +259,43 @@ k5_ml_cg(const float2* __restrict__ d2, float2* __restrict__ x2, const uint8_t* 
       for (int e = 0; e < EPT; ++e) z[e] = r[e];
     }
   };
-  precondition();
-  double rz[4];
-  {
+  // r.z and r.r of both columns; warp 0 derives the stopping test and beta
+  auto rz_partials = [&](float (&q)[4]) {
     float s0 = 0.0f, s1 = 0.0f, q0 = 0.0f, q1 = 0.0f;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
-      sm_p[pidx(j0 + e)] = z[e];
       s0 = fmaf(r[e].x, z[e].x, s0);
       s1 = fmaf(r[e].y, z[e].y, s1);
       q0 = fmaf(r[e].x, r[e].x, q0);
       q1 = fmaf(r[e].y, r[e].y, q1);
     }
-    rz[0] = s0; rz[1] = s1; rz[2] = q0; rz[3] = q1;
+    q[0] = s0; q[1] = s1; q[2] = q0; q[3] = q1;
+  };
+  const double tol = mp.tol;
+  precondition();
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) sm_p[pidx(j0 + e)] = z[e];
+  {
+    float q[4];
+    rz_partials(q);
+    block_sum_bcast<4, T>(q, part, res, [st, tol](const double* a, double* o) {
+      (void)o;
+      const double rel_a = (double)(sqrtf((float)a[2]) / (float)st[5]);
+      const double rel_b = (double)(sqrtf((float)a[3]) / (float)st[6]);
+      st[9] = rel_a;
+      st[10] = rel_b;
+      st[4] = (double)((rel_a > tol ? 1 : 0) | (rel_b > tol ? 2 : 0));
+      st[7] = a[0];
+      st[8] = a[1];
+    });
   }
-  block_sum<4, T>(rz, red, buf);  // its barrier also publishes sm_p
-  double rel_a = sqrt(rz[2]) / bnorm_a, rel_b = sqrt(rz[3]) / bnorm_b;
-  bool act_a = rel_a > mp.tol, act_b = rel_b > mp.tol;
-  int it_a = 0, it_b = 0;
-  double rzo_a = rz[0], rzo_b = rz[1];
+  int act = (int)st[4];
 
-  for (int it = 0; it < mp.max_iter && (act_a || act_b); ++it) {
+  for (int it = 0; it < mp.max_iter && act; ++it) {
     float2 pw[WIN];
     load_window<J, T, RMAX>(sm_p, j0, pw);
-    double pap[2];
     {
+      float q[2];
       float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {
@@ -268,12 +303,19 @@ k5_ml_cg(const float2* __restrict__ d2, float2* __restrict__ x2, const uint8_t* 
         s0 = fmaf(pw[e + RMAX].x, ape.x, s0);
         s1 = fmaf(pw[e + RMAX].y, ape.y, s1);
       }
-      pap[0] = s0;
-      pap[1] = s1;
+      q[0] = s0;
+      q[1] = s1;
+      block_sum_bcast<2, T>(q, part, res, [st](const double* pap, double* o) {
+        (void)o;
+        const int ac = (int)st[4];
+        // ratios in FP32 (one rounding); the sums themselves were accumulated in FP64
+        st[0] = ((ac & 1) && pap[0] != 0.0) ? (double)((float)st[7] / (float)pap[0]) : 0.0;
+        st[1] = ((ac & 2) && pap[1] != 0.0) ? (double)((float)st[8] / (float)pap[1]) : 0.0;
+        st[11] += (ac & 1) ? 1.0 : 0.0;
+        st[12] += (ac & 2) ? 1.0 : 0.0;
+      });
     }
-    block_sum<2, T>(pap, red, buf);
-    const float al_a = (act_a && pap[0] != 0.0) ? (float)(rzo_a / pap[0]) : 0.0f;
-    const float al_b = (act_b && pap[1] != 0.0) ? (float)(rzo_b / pap[1]) : 0.0f;
+    const float al_a = (float)st[0], al_b = (float)st[1];
     // A p is recomputed here (7 FMA per element) rather than held across the reduction
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
@@ -285,26 +327,32 @@ k5_ml_cg(const float2* __restrict__ d2, float2* __restrict__ x2, const uint8_t* 
       r[e].x = fmaf(-al_a, ape.x, r[e].x);
       r[e].y = fmaf(-al_b, ape.y, r[e].y);
     }
-    it_a += act_a;
-    it_b += act_b;
     precondition();
     {
-      float s0 = 0.0f, s1 = 0.0f, q0 = 0.0f, q1 = 0.0f;
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        s0 = fmaf(r[e].x, z[e].x, s0);
-        s1 = fmaf(r[e].y, z[e].y, s1);
-        q0 = fmaf(r[e].x, r[e].x, q0);
-        q1 = fmaf(r[e].y, r[e].y, q1);
-      }
-      rz[0] = s0; rz[1] = s1; rz[2] = q0; rz[3] = q1;
+      float q[4];
+      rz_partials(q);
+      block_sum_bcast<4, T>(q, part, res, [st, tol](const double* a4, double* o) {
+        (void)o;
+        const int ac = (int)st[4];
+        int nac = 0;
+        if (ac & 1) {
+          st[9] = (double)(sqrtf((float)a4[2]) / (float)st[5]);
+          if (st[9] > tol) nac |= 1;
+        }
+        if (ac & 2) {
+          st[10] = (double)(sqrtf((float)a4[3]) / (float)st[6]);
+          if (st[10] > tol) nac |= 2;
+        }
+        st[2] = ((nac & 1) && st[7] != 0.0) ? (double)((float)a4[0] / (float)st[7]) : 0.0;
+        st[3] = ((nac & 2) && st[8] != 0.0) ? (double)((float)a4[1] / (float)st[8]) : 0.0;
+        if (nac & 1) st[7] = a4[0];
+        if (nac & 2) st[8] = a4[1];
+        st[4] = (double)nac;
+      });
     }
-    block_sum<4, T>(rz, red, buf);  // all reads of sm_p for this iteration are done
-    if (act_a) rel_a = sqrt(rz[2]) / bnorm_a;
-    if (act_b) rel_b = sqrt(rz[3]) / bnorm_b;
-    const bool na = act_a && rel_a > mp.tol, nb = act_b && rel_b > mp.tol;
-    const float be_a = (na && rzo_a != 0.0) ? (float)(rz[0] / rzo_a) : 0.0f;
-    const float be_b = (nb && rzo_b != 0.0) ? (float)(rz[1] / rzo_b) : 0.0f;
+    act = (int)st[4];
+    const float be_a = (float)st[2], be_b = (float)st[3];
+    const bool na = act & 1, nb = act & 2;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       float2 pe = sm_p[pidx(j0 + e)];
@@ -312,10 +360,6 @@ k5_ml_cg(const float2* __restrict__ d2, float2* __restrict__ x2, const uint8_t* 
       if (nb) pe.y = fmaf(be_b, pe.y, z[e].y);
       sm_p[pidx(j0 + e)] = pe;
     }
-    if (na) rzo_a = rz[0];
-    if (nb) rzo_b = rz[1];
-    act_a = na;
-    act_b = nb;
     __syncthreads();  // publish sm_p before the next stencil
   }
 
@@ -326,27 +370,27 @@ k5_ml_cg(const float2* __restrict__ d2, float2* __restrict__ x2, const uint8_t* 
   build_rhs<J, T, RMAX>(d2p, mask, prior, N, p, j0, ta, tb, mp.inv_s2, mp.lam, mb2, b);
   float2 xw[WIN];
   load_window<J, T, RMAX>(sm_x, j0, xw);
-  double tr[2];
   {
+    float q[2];
     float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
-      const float2 q = csub(b[e], apply_A_at<EPT, RMAX>(xw, a, mbits, mp.lam, e));
-      s0 = fmaf(q.x, q.x, s0);
-      s1 = fmaf(q.y, q.y, s1);
+      const float2 qq = csub(b[e], apply_A_at<EPT, RMAX>(xw, a, mbits, mp.lam, e));
+      s0 = fmaf(qq.x, qq.x, s0);
+      s1 = fmaf(qq.y, qq.y, s1);
       x2[(size_t)p * J + j0 + e] = xw[e + RMAX];
     }
-    tr[0] = s0;
-    tr[1] = s1;
+    q[0] = s0;
+    q[1] = s1;
+    block_sum_bcast<2, T>(q, part, res, NoScalars{});
   }
-  block_sum<2, T>(tr, red, buf);
   if (tid == 0) {
-    iters[2 * p] = it_a;
-    iters[2 * p + 1] = it_b;
-    resid[2 * p] = (float)rel_a;
-    resid[2 * p + 1] = (float)rel_b;
-    resid[N + 2 * p] = (float)(sqrt(tr[0]) / bnorm_a);
-    resid[N + 2 * p + 1] = (float)(sqrt(tr[1]) / bnorm_b);
+    iters[2 * p] = (int)st[11];
+    iters[2 * p + 1] = (int)st[12];
+    resid[2 * p] = (float)st[9];
+    resid[2 * p + 1] = (float)st[10];
+    resid[N + 2 * p] = sqrtf((float)res[0]) / (float)st[5];
+    resid[N + 2 * p + 1] = sqrtf((float)res[1]) / (float)st[6];
   }
 }
 
