@@ -178,7 +178,10 @@ k5_ml_cg(const float2* __restrict__ d2, float2* __restrict__ x2, const uint8_t* 
   float2* sm_f = reinterpret_cast<float2*>(part + (T / 32) * 4);    // [padded J] FFT work (PRE == 1)
 
   const int tid = threadIdx.x;
-  const int p = blockIdx.x;
+  // Longest job first: the worst-conditioned sub-filters sit around column N/2
+  // (pair N/4, App. A), so blocks are mapped to pairs by distance from it.
+  const int P = N / 2, pc = P / 2, bi = blockIdx.x;
+  const int p = (pc + ((bi & 1) ? -((bi + 1) >> 1) : (bi >> 1)) + P) % P;
   const int j0 = tid * EPT;
   const float2* d2p = d2 + (size_t)p * J;
 

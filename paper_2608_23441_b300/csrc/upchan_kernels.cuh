@@ -116,18 +116,27 @@ k4_upchan(UpchanSrc src, float2* __restrict__ out, float* __restrict__ x_out) {
       sm[pidx(idx)] = x2[(long long)j * P + p0 + pp];
     }
   } else {
-    // d2[((p*C + r)*S + m)] holds frame C*m + r of pair p; this block is frames [U b, U b + U)
+    // d2[((p*C + r)*S + m)] holds frame C*m + r of pair p; this block is frames
+    // [U b, U b + U).  Each thread reads the mpr consecutive m of one (pair, residue)
+    // with 16-byte loads and scatters them to rows j = C*mm + r; consecutive lanes
+    // take consecutive pairs, so the shared-memory writes are conflict free.
     const int C = src.C;
-    const int mpr = U / C;  // frames per residue in this block
+    const int mpr = U / C;  // frames per residue in this block (8 for U = 64, C = 8)
     const long long mbase = b * (long long)mpr;
-#pragma unroll 8
-    for (int idx = tid; idx < U * PP; idx += T) {
-      const int mm = idx % mpr;
-      const int r = (idx / mpr) % C;
-      const int pp = idx / U;
-      const int j = C * mm + r;
-      const float2 v = src.d2[((long long)(p0 + pp) * C + r) * src.S + mbase + mm];
-      sm[pidx(j * PP + pp)] = v;
+    for (int idx = tid; idx < PP * C; idx += T) {
+      const int pp = idx % PP, r = idx / PP;
+      const float2* srcp = src.d2 + ((long long)(p0 + pp) * C + r) * src.S + mbase;
+      if ((mpr & 1) == 0) {
+        const float4* s4 = reinterpret_cast<const float4*>(srcp);
+#pragma unroll 4
+        for (int h = 0; h < mpr / 2; ++h) {
+          const float4 v = s4[h];
+          sm[pidx((C * (2 * h) + r) * PP + pp)] = make_float2(v.x, v.y);
+          sm[pidx((C * (2 * h + 1) + r) * PP + pp)] = make_float2(v.z, v.w);
+        }
+      } else {
+        for (int mm = 0; mm < mpr; ++mm) sm[pidx((C * mm + r) * PP + pp)] = srcp[mm];
+      }
     }
   }
   __syncthreads();
@@ -144,9 +153,14 @@ k4_upchan(UpchanSrc src, float2* __restrict__ out, float* __restrict__ x_out) {
     auto ld = [](int c, int i) { return sm[pidx(i * PP + c)]; };
     auto st = [](int c, int i, float2 v) { sm[pidx(i * PP + c)] = v; };
     constexpr int RL = last_radix(U);
-    const UpchanTwiddle<RL> post{tw, p0};
-    BatchedFFT<PP, U, T, false, true, 1, decltype(ld), decltype(st), decltype(st), UpchanTwiddle<RL>>::run(
-        tid, ld, st, st, post);
+    if constexpr (CU == 1) {
+      const UpchanTwiddle<RL> post{tw, p0};
+      BatchedFFT<PP, U, T, false, true, 1, decltype(ld), decltype(st), decltype(st), UpchanTwiddle<RL>>::run(
+          tid, ld, st, st, post);
+    } else {
+      // the step-(2) twiddle is applied in the cross stage below
+      BatchedFFT<PP, U, T, false, true, 1, decltype(ld), decltype(st), decltype(st)>::run(tid, ld, st, st);
+    }
   }
   if constexpr (CU > 1) {
     cg::this_cluster().sync();
@@ -155,10 +169,18 @@ k4_upchan(UpchanSrc src, float2* __restrict__ out, float* __restrict__ x_out) {
 #pragma unroll
     for (int q = 0; q < CU; ++q) peer[q] = cg::this_cluster().map_shared_rank(sm, q);
     for (int w = s * T + tid; w < U * PP; w += CU * T) {
-      const int pp = w % PP;
+      const int pp = w % PP, k1 = w / PP;
       float2 v[CU];
 #pragma unroll
       for (int q = 0; q < CU; ++q) v[q] = peer[q][pidx(w)];
+      // step (2): element (k1, p = q P' + p') of CTA q gets exp(-2 pi i p k1 / Q)
+      //   = exp(-2 pi i p' k1 / Q) * exp(-2 pi i P' k1 / Q)^q
+      {
+        const float2 base = tw(2 * pp * k1);
+#pragma unroll
+        for (int q = 0; q < CU; ++q) v[q] = cmul(v[q], base);
+        apply_twiddles<CU>(v, tw(2 * PP * k1));
+      }
       DFT<CU, false>::run(v);
       float2 wr[CU];
       twiddle_powers<CU>(tw(2 * U * pp), wr);  // exp(-2 pi i p' / P)
