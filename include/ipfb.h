@@ -213,6 +213,47 @@ int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, 
                   const void* net, float* x_inout, int use_x0, int* iters, float* resid, void* ws,
                   size_t ws_bytes, void* stream);
 
+/*
+ * Batched inverse PFB of many independent streams of uneven shape (lblock in
+ * {1024, 2048, 4096}, any integer number of frames 1024 <= J <= 16384), each the
+ * Wiener inverse of ipfb_wiener (Eq. decorrelation, Eq. wiener weights).  The
+ * J-point column DFT for arbitrary J uses Bluestein's chirp-z identity with
+ * power-of-two FFTs of length M = next_pow2(2J - 1) on thread-block clusters; the
+ * work (spectra groups, column pairs, output tiles) is pulled from counters by
+ * persistent kernels, longest items first.
+ *
+ * ipfb_batched_plan builds the host-side plan (no device work) and returns the
+ * workspace size; tune_cache (a file path, or NULL) supplies per-M kernel
+ * variants written by ipfb_batched_autotune.  ipfb_batched_prepare uploads the
+ * descriptors and builds the chirp and FFT(chirp) tables in the workspace; it
+ * synchronizes `stream` and cannot be captured.  ipfb_batched_run enqueues the
+ * inversion (a counter reset and the persistent kernels, no host
+ * synchronization); after a prepare with the same workspace it can be captured
+ * in a CUDA graph and replayed.  ipfb_batched_autotune times every kernel
+ * variant per M class on the plan's own work items, keeps the fastest, and
+ * writes the choice to cache_path (if not NULL); it overwrites the outputs.
+ * ipfb_batched_variant reports the variant chosen for M.  Stream descriptors:
+ * device pointers codes [J][N/2], scale [N/2+1], window [ntap][N], x_out [J*N].
+ */
+typedef struct {
+  int lblock;
+  int ntap;
+  int nframes;
+  const uint8_t* codes;
+  const float* scale;
+  const float* window;
+  double noise_level; /* phi^2 of this stream */
+  float* x_out;
+} ipfb_stream_desc;
+
+int ipfb_batched_plan(const ipfb_stream_desc* streams, int nstreams, int normalize, const char* tune_cache,
+                      void** plan, size_t* ws_bytes);
+int ipfb_batched_prepare(void* plan, void* ws, size_t ws_bytes, void* stream);
+int ipfb_batched_run(void* plan, void* ws, size_t ws_bytes, void* stream);
+int ipfb_batched_autotune(void* plan, void* ws, size_t ws_bytes, void* stream, const char* cache_path);
+int ipfb_batched_variant(void* plan, int M, char* name, size_t cap);
+int ipfb_batched_free(void* plan);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,400 @@
+// Batched inverse PFB of many uneven streams: host plan, workspace layout, the
+// autotuner and the launches of the persistent kernels (batched_kernels.cuh).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ipfb.h"
+#define IPFB_BATCHED_HOST_KERNELS
+#include "batched_kernels.cuh"
+
+using namespace ipfb;
+
+namespace {
+
+// kb3 variants the autotuner chooses between: cluster size, threads, max radix
+struct Variant {
+  int C, T, MAXR;
+  const char* name;
+};
+constexpr Variant kVariants[] = {{4, 256, 32, "c4_t256_r32"}, {4, 256, 16, "c4_t256_r16"}, {2, 256, 32, "c2_t256_r32"}};
+constexpr int kNumVariants = 3;
+constexpr int kNumMClass = 5;  // M = 2048 .. 32768
+
+int mclass(int M) {
+  int c = 0;
+  while ((2048 << c) < M) ++c;
+  return c;
+}
+bool variant_ok(int v, int M) { return M / kVariants[v].C <= 8192 && M / kVariants[v].C >= 512; }
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Plan {
+  std::vector<ipfb_stream_desc> in;
+  std::vector<BStream> st;
+  std::vector<BItem> items2, items4;
+  std::vector<BItem> items3[kNumMClass];
+  std::vector<int> Js, Ms;
+  std::vector<int> jidx;  // stream -> distinct J index
+  size_t off_streams = 0, off_items2 = 0, off_items4 = 0, off_items3[kNumMClass] = {}, off_counters = 0;
+  size_t off_Js = 0, off_Ms = 0, off_chirp_ptr = 0, off_bhat_ptr = 0;
+  std::vector<size_t> off_chirp, off_bhat, off_d2;
+  size_t total = 0;
+  int variant[kNumMClass] = {0, 0, 0, 0, 0};
+  const void* prepared_ws = nullptr;
+  int normalize = 1;
+};
+
+thread_local char g_berr[256] = "";
+
+int fail(cudaError_t e, const char* where) {
+  std::snprintf(g_berr, sizeof(g_berr), "%s: %s", where, cudaGetErrorString(e));
+  return IPFB_ERR_CUDA;
+}
+#define BCK(call, where)                          \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return fail(e_, where); \
+  } while (0)
+
+int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+void layout(Plan& P) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  P.off_streams = take(P.st.size() * sizeof(BStream));
+  P.off_items2 = take(P.items2.size() * sizeof(BItem));
+  P.off_items4 = take(P.items4.size() * sizeof(BItem));
+  for (int c = 0; c < kNumMClass; ++c) P.off_items3[c] = take(std::max<size_t>(1, P.items3[c].size()) * sizeof(BItem));
+  P.off_counters = take(16 * sizeof(int));
+  P.off_Js = take(P.Js.size() * sizeof(int));
+  P.off_Ms = take(P.Ms.size() * sizeof(int));
+  P.off_chirp_ptr = take(P.Js.size() * sizeof(float2*));
+  P.off_bhat_ptr = take(P.Js.size() * sizeof(float2*));
+  P.off_chirp.resize(P.Js.size());
+  P.off_bhat.resize(P.Js.size());
+  for (size_t t = 0; t < P.Js.size(); ++t) {
+    P.off_chirp[t] = take((size_t)P.Js[t] * sizeof(float2));
+    P.off_bhat[t] = take((size_t)P.Ms[t] * sizeof(float2));
+  }
+  P.off_d2.resize(P.st.size());
+  for (size_t s = 0; s < P.st.size(); ++s) P.off_d2[s] = take((size_t)P.st[s].J * (P.st[s].N / 2) * sizeof(float2));
+  P.total = o;
+}
+
+}  // namespace
+
+namespace ipfb {
+cudaError_t kb3_launch_v0(const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb3_launch_v1(const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb3_launch_v2(const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+}  // namespace ipfb
+
+namespace {
+
+int launch_kb3(const Plan& P, char* ws, int cls, int v, cudaStream_t stream) {
+  const size_t n = P.items3[cls].size();
+  if (n == 0) return IPFB_OK;
+  const BStream* s = reinterpret_cast<const BStream*>(ws + P.off_streams);
+  const BItem* it = reinterpret_cast<const BItem*>(ws + P.off_items3[cls]);
+  int* ctr = reinterpret_cast<int*>(ws + P.off_counters) + 2 + cls;
+  int nclusters = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (v) {
+    case 0: e = kb3_launch_v0(s, it, (int)n, ctr, stream, &nclusters); break;
+    case 1: e = kb3_launch_v1(s, it, (int)n, ctr, stream, &nclusters); break;
+    case 2: e = kb3_launch_v2(s, it, (int)n, ctr, stream, &nclusters); break;
+  }
+  if (e != cudaSuccess) return fail(e, "kb3_columns");
+  return IPFB_OK;
+}
+
+int prepare(Plan& P, char* ws, cudaStream_t stream) {
+  // device pointers inside the workspace
+  for (size_t s = 0; s < P.st.size(); ++s) {
+    P.st[s].d2 = reinterpret_cast<float2*>(ws + P.off_d2[s]);
+    P.st[s].chirp = reinterpret_cast<const float2*>(ws + P.off_chirp[P.jidx[s]]);
+    P.st[s].bhat = reinterpret_cast<const float2*>(ws + P.off_bhat[P.jidx[s]]);
+  }
+  std::vector<float2*> cp(P.Js.size()), bp(P.Js.size());
+  for (size_t t = 0; t < P.Js.size(); ++t) {
+    cp[t] = reinterpret_cast<float2*>(ws + P.off_chirp[t]);
+    bp[t] = reinterpret_cast<float2*>(ws + P.off_bhat[t]);
+  }
+  auto up = [&](size_t off, const void* src, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(ws + off, src, bytes, cudaMemcpyHostToDevice, stream);
+  };
+  BCK(up(P.off_streams, P.st.data(), P.st.size() * sizeof(BStream)), "upload streams");
+  BCK(up(P.off_items2, P.items2.data(), P.items2.size() * sizeof(BItem)), "upload items");
+  BCK(up(P.off_items4, P.items4.data(), P.items4.size() * sizeof(BItem)), "upload items");
+  for (int c = 0; c < kNumMClass; ++c)
+    BCK(up(P.off_items3[c], P.items3[c].data(), P.items3[c].size() * sizeof(BItem)), "upload items");
+  BCK(up(P.off_Js, P.Js.data(), P.Js.size() * sizeof(int)), "upload J");
+  BCK(up(P.off_Ms, P.Ms.data(), P.Ms.size() * sizeof(int)), "upload M");
+  BCK(up(P.off_chirp_ptr, cp.data(), cp.size() * sizeof(float2*)), "upload ptr");
+  BCK(up(P.off_bhat_ptr, bp.data(), bp.size() * sizeof(float2*)), "upload ptr");
+  // the host vectors above must outlive the copies: make them complete here
+  BCK(cudaStreamSynchronize(stream), "prepare sync");
+  const int nJ = (int)P.Js.size();
+  const int* dJ = reinterpret_cast<const int*>(ws + P.off_Js);
+  const int* dM = reinterpret_cast<const int*>(ws + P.off_Ms);
+  kb_chirp<<<dim3(16, nJ), 256, 0, stream>>>(dJ, reinterpret_cast<float2* const*>(ws + P.off_chirp_ptr), nJ);
+  BCK(cudaGetLastError(), "kb_chirp");
+  {
+    auto kern = kb_bhat<4, 256, 32>;
+    const size_t smem = (size_t)padded_len(8192) * sizeof(float2);
+    BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "kb_bhat smem");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nJ * 4);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 4;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BCK(cudaLaunchKernelEx(&cfg, kern, dJ, dM, reinterpret_cast<const float2* const*>(ws + P.off_chirp_ptr),
+                           reinterpret_cast<float2* const*>(ws + P.off_bhat_ptr), nJ),
+        "kb_bhat");
+  }
+  P.prepared_ws = ws;
+  return IPFB_OK;
+}
+
+size_t kb2_smem() {
+  const size_t a = (size_t)16 * k2_frame_stride(512) + 256;
+  const size_t b = (size_t)8 * k2_frame_stride(1024) + 256;
+  const size_t c = (size_t)4 * k2_frame_stride(2048) + 256;
+  return std::max(a, std::max(b, c)) * sizeof(float2);
+}
+
+int run_all(Plan& P, char* ws, cudaStream_t stream, bool columns_only = false, int only_cls = -1, int only_v = -1) {
+  int* ctr = reinterpret_cast<int*>(ws + P.off_counters);
+  BCK(cudaMemsetAsync(ctr, 0, 16 * sizeof(int), stream), "counters");
+  const BStream* s = reinterpret_cast<const BStream*>(ws + P.off_streams);
+  if (!columns_only && !P.items2.empty()) {
+    const size_t smem = kb2_smem();
+    BCK(cudaFuncSetAttribute(kb2_unpack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "kb2 smem");
+    int per_sm = 0;
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb2_unpack, kKb2Threads, smem), "kb2 occ");
+    int dev = 0, nsm = 0;
+    BCK(cudaGetDevice(&dev), "device");
+    BCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "sm count");
+    const int grid = (int)std::min<size_t>(P.items2.size(), (size_t)std::max(1, per_sm) * nsm);
+    kb2_unpack<<<grid, kKb2Threads, smem, stream>>>(s, reinterpret_cast<const BItem*>(ws + P.off_items2),
+                                                    (int)P.items2.size(), ctr + 0);
+    BCK(cudaGetLastError(), "kb2_unpack");
+  }
+  for (int c = 0; c < kNumMClass; ++c) {
+    if (only_cls >= 0 && c != only_cls) continue;
+    const int v = only_v >= 0 ? only_v : P.variant[c];
+    int rc = launch_kb3(P, ws, c, v, stream);
+    if (rc) return rc;
+  }
+  if (!columns_only && !P.items4.empty()) {
+    int dev = 0, nsm = 0;
+    BCK(cudaGetDevice(&dev), "device");
+    BCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "sm count");
+    const int grid = (int)std::min<size_t>(P.items4.size(), (size_t)nsm * 8);
+    kb4_to_time<<<grid, 256, 0, stream>>>(s, reinterpret_cast<const BItem*>(ws + P.off_items4),
+                                          (int)P.items4.size(), ctr + 1);
+    BCK(cudaGetLastError(), "kb4_to_time");
+  }
+  return IPFB_OK;
+}
+
+void load_cache(Plan& P, const char* path) {
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char line[256];
+  while (std::fgets(line, sizeof(line), f)) {
+    int M = 0;
+    char name[64] = "";
+    if (std::sscanf(line, "%d %63s", &M, name) == 2) {
+      for (int v = 0; v < kNumVariants; ++v)
+        if (!std::strcmp(name, kVariants[v].name) && variant_ok(v, M) && M >= 2048 && M <= 32768)
+          P.variant[mclass(M)] = v;
+    }
+  }
+  std::fclose(f);
+}
+
+}  // namespace
+
+extern "C" int ipfb_batched_plan(const ipfb_stream_desc* streams, int nstreams, int normalize,
+                                 const char* tune_cache, void** plan_out, size_t* ws_bytes) {
+  if (!streams || nstreams < 1 || !plan_out || !ws_bytes) return IPFB_ERR_INVALID;
+  *plan_out = nullptr;
+  Plan* P = new (std::nothrow) Plan();
+  if (!P) return IPFB_ERR_INVALID;
+  P->normalize = normalize ? 1 : 0;
+  std::map<int, int> jmap;
+  struct Cost {
+    double c;
+    BItem it;
+  };
+  std::vector<Cost> c2, c3[kNumMClass], c4;
+  for (int s = 0; s < nstreams; ++s) {
+    const ipfb_stream_desc& d = streams[s];
+    if (!d.codes || !d.scale || !d.window || !d.x_out) {
+      delete P;
+      return IPFB_ERR_INVALID;
+    }
+    if (!(d.lblock == 1024 || d.lblock == 2048 || d.lblock == 4096) || d.ntap != 4 ||
+        d.nframes < 1024 || d.nframes > 16384 || !(d.noise_level >= 0.0) || !std::isfinite(d.noise_level)) {
+      delete P;
+      return IPFB_ERR_UNSUPPORTED;
+    }
+    P->in.push_back(d);
+    BStream b = {};
+    b.N = d.lblock;
+    b.J = d.nframes;
+    b.M = next_pow2(2 * d.nframes - 1);
+    b.ntap = d.ntap;
+    b.phi2 = (float)d.noise_level;
+    b.gnorm = (d.noise_level > 0.0 && normalize) ? (float)(1.0 + d.noise_level) : 1.0f;
+    b.invJ = 1.0f / (float)d.nframes;
+    b.codes = d.codes;
+    b.scale = d.scale;
+    b.window = d.window;
+    b.x_out = d.x_out;
+    auto f = jmap.find(b.J);
+    int ji;
+    if (f == jmap.end()) {
+      ji = (int)P->Js.size();
+      jmap[b.J] = ji;
+      P->Js.push_back(b.J);
+      P->Ms.push_back(b.M);
+    } else {
+      ji = f->second;
+    }
+    P->jidx.push_back(ji);
+    P->st.push_back(b);
+    const int F = 8192 / (b.N / 2) >= 16 ? 16 : 8192 / (b.N / 2);
+    for (int j0 = 0; j0 < b.J; j0 += F) c2.push_back({(double)b.N, {s, j0}});
+    const int cls = mclass(b.M);
+    for (int p = 0; p < b.N / 2; ++p) c3[cls].push_back({(double)b.M, {s, p}});
+    const int ntp = (b.N / 2 + 31) / 32, ntj = (b.J + 63) / 64;
+    for (int t = 0; t < ntp * ntj; ++t) c4.push_back({1.0, {s, t}});
+  }
+  auto sorted = [](std::vector<Cost>& v) {
+    std::stable_sort(v.begin(), v.end(), [](const Cost& a, const Cost& b) { return a.c > b.c; });
+    std::vector<BItem> out;
+    out.reserve(v.size());
+    for (auto& c : v) out.push_back(c.it);
+    return out;
+  };
+  P->items2 = sorted(c2);
+  for (int c = 0; c < kNumMClass; ++c) P->items3[c] = sorted(c3[c]);
+  P->items4 = sorted(c4);
+  for (int c = 0; c < kNumMClass; ++c)
+    if (!variant_ok(P->variant[c], 2048 << c)) P->variant[c] = 0;
+  load_cache(*P, tune_cache);
+  layout(*P);
+  *plan_out = P;
+  *ws_bytes = P->total;
+  return IPFB_OK;
+}
+
+extern "C" int ipfb_batched_prepare(void* plan, void* ws, size_t ws_bytes, void* stream) {
+  Plan* P = static_cast<Plan*>(plan);
+  if (!P || !ws) return IPFB_ERR_INVALID;
+  if (ws_bytes < P->total) return IPFB_ERR_WORKSPACE;
+  return prepare(*P, static_cast<char*>(ws), reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int ipfb_batched_run(void* plan, void* ws, size_t ws_bytes, void* stream) {
+  Plan* P = static_cast<Plan*>(plan);
+  if (!P || !ws) return IPFB_ERR_INVALID;
+  if (ws_bytes < P->total) return IPFB_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (P->prepared_ws != ws) {
+    int rc = prepare(*P, static_cast<char*>(ws), st);
+    if (rc) return rc;
+  }
+  return run_all(*P, static_cast<char*>(ws), st);
+}
+
+extern "C" int ipfb_batched_autotune(void* plan, void* ws, size_t ws_bytes, void* stream, const char* cache_path) {
+  Plan* P = static_cast<Plan*>(plan);
+  if (!P || !ws) return IPFB_ERR_INVALID;
+  if (ws_bytes < P->total) return IPFB_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  if (P->prepared_ws != ws) {
+    int rc = prepare(*P, w, st);
+    if (rc) return rc;
+  }
+  {
+    int rc = run_all(*P, w, st);  // fill the column scratch with real data first
+    if (rc) return rc;
+  }
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0), "event");
+  BCK(cudaEventCreate(&e1), "event");
+  for (int c = 0; c < kNumMClass; ++c) {
+    if (P->items3[c].empty()) continue;
+    float best = 1e30f;
+    int bestv = P->variant[c];
+    for (int v = 0; v < kNumVariants; ++v) {
+      if (!variant_ok(v, 2048 << c)) continue;
+      int rc = run_all(*P, w, st, true, c, v);  // warm-up (also loads the kernel)
+      if (rc) return rc;
+      BCK(cudaEventRecord(e0, st), "record");
+      rc = run_all(*P, w, st, true, c, v);
+      if (rc) return rc;
+      BCK(cudaEventRecord(e1, st), "record");
+      BCK(cudaEventSynchronize(e1), "sync");
+      float ms = 0.0f;
+      BCK(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+      if (ms < best) {
+        best = ms;
+        bestv = v;
+      }
+    }
+    P->variant[c] = bestv;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cache_path) {
+    FILE* f = std::fopen(cache_path, "w");
+    if (f) {
+      for (int c = 0; c < kNumMClass; ++c) std::fprintf(f, "%d %s\n", 2048 << c, kVariants[P->variant[c]].name);
+      std::fclose(f);
+    }
+  }
+  return IPFB_OK;
+}
+
+extern "C" int ipfb_batched_variant(void* plan, int M, char* name, size_t cap) {
+  Plan* P = static_cast<Plan*>(plan);
+  if (!P || !name || cap < 16 || M < 2048 || M > 32768) return IPFB_ERR_INVALID;
+  std::snprintf(name, cap, "%s", kVariants[P->variant[mclass(M)]].name);
+  return IPFB_OK;
+}
+
+extern "C" int ipfb_batched_free(void* plan) {
+  delete static_cast<Plan*>(plan);
+  return IPFB_OK;
+}

@@ -30,21 +30,20 @@ namespace cg = cooperative_groups;
 // F interleaved frames of the transposed store fall in distinct banks
 __host__ __device__ constexpr int k2_frame_stride(int H) { return ((padded_len(H) + 15) / 16) * 16 + 4; }
 
+// One group of F spectra (frames C*(m0 + f) + r, f < nvalid) -> d2.  Called by every
+// thread of the CTA (TPF*F threads); smem holds F frame buffers plus 256 twiddles.
 template <int H, int TPF, int F>
-__global__ void __launch_bounds__(TPF* F)
-k2_unpack_irfft(const uint8_t* __restrict__ codes, const float* __restrict__ scale,
-                float2* __restrict__ d2, int C, int S) {
-  extern __shared__ float2 smem[];
+__device__ __forceinline__ void k2_group(const uint8_t* __restrict__ codes, const float* __restrict__ scale,
+                                         float2* __restrict__ d2, int C, int S, int r, int m0, int nvalid,
+                                         float2* smem) {
   const int f = threadIdx.x / TPF;
   const int tid = threadIdx.x % TPF;
   float2* sm = smem + f * k2_frame_stride(H);
-  const int per_res = S / F;
-  const int r = blockIdx.x / per_res;
-  const int m0 = (blockIdx.x % per_res) * F;
-  const int j = C * (m0 + f) + r;
+  const bool live = f < nvalid;
+  const int j = C * (m0 + (live ? f : 0)) + r;
   const uint8_t* row = codes + (size_t)j * H;
   const float pre = 0.5f / (float)H;
-  // exp(+2 pi i k / N), N = 2H, from two tables of 64 entries shared by the CTA
+  // exp(+2 pi i k / N), N = 2H, from two tables of 128 entries shared by the CTA
   float2* tw_hi = smem + F * k2_frame_stride(H);
   float2* tw_lo = tw_hi + 128;
   twid2_fill<7, true>(tw_hi, tw_lo, 2 * H, threadIdx.x, TPF * F);
@@ -52,7 +51,7 @@ k2_unpack_irfft(const uint8_t* __restrict__ codes, const float* __restrict__ sca
   const Twid2<7> tw{tw_hi, tw_lo};
 
   // pre-processing: each thread forms Z[k] and Z[H-k] for k in [0, H/2]
-  for (int k = tid; k <= H / 2; k += TPF) {
+  for (int k = tid; live && k <= H / 2; k += TPF) {
     const int km = H - k;  // == H for k == 0 (Nyquist lives in byte 0's high nibble)
     const uint8_t bk = row[k];
     const uint8_t bm = row[km == H ? 0 : km];
@@ -83,11 +82,22 @@ k2_unpack_irfft(const uint8_t* __restrict__ codes, const float* __restrict__ sca
   __syncthreads();
   block_fft<H, TPF, true>(sm, tid, SPad{sm}, SPad{sm});
   __syncthreads();
-  // transposed store: for each pair p, F consecutive m of residue r
+  // transposed store: for each pair p, the valid consecutive m of residue r
   for (int idx = threadIdx.x; idx < H * F; idx += TPF * F) {
     const int p = idx / F, ff = idx % F;
-    d2[((size_t)p * C + r) * S + m0 + ff] = smem[ff * k2_frame_stride(H) + pidx(p)];
+    if (ff < nvalid) d2[((size_t)p * C + r) * S + m0 + ff] = smem[ff * k2_frame_stride(H) + pidx(p)];
   }
+}
+
+template <int H, int TPF, int F>
+__global__ void __launch_bounds__(TPF* F)
+k2_unpack_irfft(const uint8_t* __restrict__ codes, const float* __restrict__ scale,
+                float2* __restrict__ d2, int C, int S) {
+  extern __shared__ float2 smem[];
+  const int per_res = S / F;
+  const int r = blockIdx.x / per_res;
+  const int m0 = (blockIdx.x % per_res) * F;
+  k2_group<H, TPF, F>(codes, scale, d2, C, S, r, m0, F, smem);
 }
 
 // ----------------------------------------------------------------------------

@@ -36,6 +36,12 @@ class MLParams(ctypes.Structure):
 PRECOND = {"none": 0, "wiener": 1, "learned": 2}
 
 
+class StreamDesc(ctypes.Structure):
+    _fields_ = [("lblock", ctypes.c_int), ("ntap", ctypes.c_int), ("nframes", ctypes.c_int),
+                ("codes", ctypes.c_void_p), ("scale", ctypes.c_void_p), ("window", ctypes.c_void_p),
+                ("noise_level", ctypes.c_double), ("x_out", ctypes.c_void_p)]
+
+
 class IpfbError(RuntimeError):
     def __init__(self, fn: str, rc: int):
         self.rc = rc
@@ -66,6 +72,13 @@ _SIGS = {
     "ipfb_wiener": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _D, _I, _P, _P, _SZ, _P]),
     "upchannelize": (_I, [_P, _I64, _I64, _P, _P, _SZ, _P]),
     "ipfb_wiener_upchannelize": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _D, _I, _I, _P, _P, _P, _SZ, _P]),
+    "ipfb_batched_plan": (_I, [ctypes.POINTER(StreamDesc), _I, _I, ctypes.c_char_p, ctypes.POINTER(_P),
+                               ctypes.POINTER(_SZ)]),
+    "ipfb_batched_prepare": (_I, [_P, _P, _SZ, _P]),
+    "ipfb_batched_run": (_I, [_P, _P, _SZ, _P]),
+    "ipfb_batched_autotune": (_I, [_P, _P, _SZ, _P, ctypes.c_char_p]),
+    "ipfb_batched_variant": (_I, [_P, _I, ctypes.c_char_p, _SZ]),
+    "ipfb_batched_free": (_I, [_P]),
     "ipfb_ml_solve": (_I, [ctypes.POINTER(Geom), _P, _P, _P, ctypes.POINTER(MLParams), _P, _P, _P, _P, _I, _P, _P,
                            _P, _SZ, _P]),
 }
@@ -301,3 +314,65 @@ def ml_solve(codes, scale, window, noise_var: float, mask, prior, prior_weight: 
                                                 int(x0 is not None), _ptr(iters), _ptr(resid), _ptr(ws), wsb,
                                                 _stream()))
     return x, iters, resid
+
+
+class BatchedPlan:
+    """Many independent streams inverted together (ipfb_batched_*).  Each stream is
+    a dict with CUDA tensors codes uint8 [J, N/2], scale float32 [N/2+1], window
+    float32 [4, N] and a float noise_level; outputs are allocated here (x[i],
+    float32 [J*N]).  run() is capturable in a CUDA graph after prepare()."""
+
+    def __init__(self, streams, normalize: bool = True, tune_cache: str | None = None):
+        torch = _torch()
+        self._keep = []
+        self.x = []
+        descs = (StreamDesc * len(streams))()
+        for i, st in enumerate(streams):
+            codes = _dev(st["codes"], torch.uint8, "codes")
+            scale = _dev(st["scale"], torch.float32, "scale")
+            window = _dev(st["window"], torch.float32, "window")
+            p, N = window.shape
+            J = codes.shape[0]
+            x = torch.empty(J * N, dtype=torch.float32, device=codes.device)
+            self.x.append(x)
+            self._keep += [codes, scale, window]
+            descs[i] = StreamDesc(N, p, J, codes.data_ptr(), scale.data_ptr(), window.data_ptr(),
+                                  float(st["noise_level"]), x.data_ptr())
+        self._descs = descs
+        plan = _P()
+        nbytes = _SZ(0)
+        cache = tune_cache.encode() if tune_cache else None
+        _check("ipfb_batched_plan", lib().ipfb_batched_plan(descs, len(streams), int(bool(normalize)), cache,
+                                                            ctypes.byref(plan), ctypes.byref(nbytes)))
+        self.plan = plan
+        self.ws = torch.empty(max(1, nbytes.value), dtype=torch.uint8, device=streams[0]["codes"].device)
+        self.ws_bytes = nbytes.value
+
+    def prepare(self):
+        _check("ipfb_batched_prepare", lib().ipfb_batched_prepare(self.plan, _ptr(self.ws), self.ws_bytes,
+                                                                  _stream()))
+
+    def run(self):
+        _check("ipfb_batched_run", lib().ipfb_batched_run(self.plan, _ptr(self.ws), self.ws_bytes, _stream()))
+        return self.x
+
+    def autotune(self, cache_path: str | None = None):
+        c = cache_path.encode() if cache_path else None
+        _check("ipfb_batched_autotune", lib().ipfb_batched_autotune(self.plan, _ptr(self.ws), self.ws_bytes,
+                                                                    _stream(), c))
+
+    def variant(self, M: int) -> str:
+        buf = ctypes.create_string_buffer(64)
+        _check("ipfb_batched_variant", lib().ipfb_batched_variant(self.plan, int(M), buf, 64))
+        return buf.value.decode()
+
+    def close(self):
+        if getattr(self, "plan", None):
+            lib().ipfb_batched_free(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -136,3 +136,13 @@ def random_scale(nchan: int, seed: int) -> np.ndarray:
     """Positive per-channel quantizer steps, float32, log-uniform over [0.5, 2]."""
     rng = np.random.default_rng(seed + 122949823)
     return np.exp(rng.uniform(np.log(0.5), np.log(2.0), size=nchan)).astype(np.float32)
+
+
+def gaussian_stream_torch(nsamples: int, seed: int, device):
+    """White standard-normal stream generated on a torch device (float32) with a
+    seeded torch.Generator; for large benchmark batches, where host generation would
+    dominate.  Not bit-identical to gaussian_stream."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return torch.randn(int(nsamples), generator=g, device=device, dtype=torch.float32)
