@@ -110,6 +110,25 @@ k2_unpack_irfft(const uint8_t* __restrict__ codes, const float* __restrict__ sca
 constexpr float kFp64Below = 1e-4f;
 constexpr int kMaxTaps = 16;
 
+// FP64 re-evaluation of one gain where |W|^2 is tiny (near-zero eigenvalues of
+// nearly symmetric windows, App. A).  Kept out of line: it runs for a few modes per
+// million, and inlining its FP64 code into the FP32 loop slows every mode.
+static __device__ __noinline__ float2 gain_fp64(const float* taps, int ntap, int k, GainParams gp) {
+  double s, c;
+  sincospi(2.0 * (double)k / (double)gp.J, &s, &c);
+  double wx = 0.0, wy = 0.0;
+  for (int t = ntap - 1; t >= 0; --t) {
+    const double nx = wx * c + wy * s;  // (wx + i wy)(c - i s)
+    const double ny = wy * c - wx * s;
+    wx = nx + (double)taps[t];
+    wy = ny;
+  }
+  const double den = wx * wx + wy * wy + (double)gp.phi2;
+  if (den == 0.0) return make_float2(0.0f, 0.0f);
+  const double g = (double)gp.gnorm * (double)gp.invJ / den;
+  return make_float2((float)(wx * g), (float)(wy * g));
+}
+
 template <int NT>
 __device__ __forceinline__ float2 gain_at(const float* taps, int k, float2 e1, const GainParams& gp) {
   // Horner in e1 = e^{-2 pi i k/J}.  NT > 0: exactly NT taps (compile time);
@@ -123,25 +142,8 @@ __device__ __forceinline__ float2 gain_at(const float* taps, int k, float2 e1, c
       W.x += taps[t];
     }
   }
-  float a2 = fmaf(W.x, W.x, W.y * W.y);
-  if (a2 < kFp64Below) {
-    double s, c;
-    sincospi(2.0 * (double)k / (double)gp.J, &s, &c);
-    double wx = 0.0, wy = 0.0;
-#pragma unroll
-    for (int t = NMAX - 1; t >= 0; --t) {
-      if (NT > 0 || t < gp.ntap) {
-        const double nx = wx * c + wy * s;  // (wx + i wy)(c - i s)
-        const double ny = wy * c - wx * s;
-        wx = nx + (double)taps[t];
-        wy = ny;
-      }
-    }
-    const double den = wx * wx + wy * wy + (double)gp.phi2;
-    if (den == 0.0) return make_float2(0.0f, 0.0f);
-    const double g = (double)gp.gnorm * (double)gp.invJ / den;
-    return make_float2((float)(wx * g), (float)(wy * g));
-  }
+  const float a2 = fmaf(W.x, W.x, W.y * W.y);
+  if (a2 < kFp64Below) return gain_fp64(taps, NT > 0 ? NT : gp.ntap, k, gp);
   const float g = __fdividef(gp.gnorm * gp.invJ, a2 + gp.phi2);
   return make_float2(W.x * g, W.y * g);
 }
