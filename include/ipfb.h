@@ -14,7 +14,9 @@
  *   4-bit codes: folded layout, N/2 bytes per spectrum: byte c (0 < c < N/2) =
  *     Re_c (low nibble) | Im_c (high nibble), two's complement in [-7, 7];
  *     byte 0 = Re_0 (low) | Re_{N/2} (high).  DC and Nyquist have no
- *     imaginary part in a real PFB, so nothing is lost.
+ *     imaginary part in a real PFB, so nothing is lost.  Code arrays read by
+ *     the inverse calls must start on a 16-byte boundary (they are read with
+ *     16-byte loads); an unaligned pointer is refused with IPFB_ERR_INVALID.
  *
  * Ownership: every array pointer is owned by the caller.  Unless stated
  *   otherwise pointers are DEVICE pointers on the current CUDA device.  The

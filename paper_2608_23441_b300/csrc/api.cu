@@ -18,6 +18,8 @@ using namespace ipfb;
 namespace {
 
 thread_local char g_cuda_err[256] = "";
+
+bool misaligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; }
 std::atomic<int> g_max_column_run{8192};
 
 // ---------------------------------------------------------------- stage timing
@@ -286,7 +288,7 @@ int ipfb_wiener(const ipfb_geom* g, const uint8_t* codes, const float* scale, co
                 double noise_level, int normalize, float* x_out, void* ws, size_t ws_bytes, void* stream) {
   int rc = check_geom(g, true);
   if (rc) return rc;
-  if (!codes || !scale || !window || !x_out) return IPFB_ERR_INVALID;
+  if (!codes || !scale || !window || !x_out || misaligned16(codes)) return IPFB_ERR_INVALID;
   if ((rc = check_noise(noise_level))) return rc;
   size_t need = 0;
   ipfb_workspace_size(g, IPFB_OP_WIENER, &need);
@@ -323,7 +325,7 @@ int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const flo
                              size_t ws_bytes, void* stream) {
   int rc = check_geom(g, true);
   if (rc) return rc;
-  if (!codes || !scale || !window || !out) return IPFB_ERR_INVALID;
+  if (!codes || !scale || !window || !out || misaligned16(codes)) return IPFB_ERR_INVALID;
   if ((rc = check_noise(noise_level))) return rc;
   if (upfactor < 1 || !is_pow2(upfactor)) return IPFB_ERR_UNSUPPORTED;
   const long long L = (long long)upfactor * g->lblock;
@@ -352,7 +354,8 @@ int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, 
                   float* x_inout, int use_x0, int* iters, float* resid, void* ws, size_t ws_bytes, void* stream) {
   int rc = check_geom(g, true);
   if (rc) return rc;
-  if (!codes || !scale || !window || !prm || !prior_mask || !prior_values || !x_inout || !iters || !resid)
+  if (!codes || !scale || !window || !prm || !prior_mask || !prior_values || !x_inout || !iters || !resid ||
+      misaligned16(codes))
     return IPFB_ERR_INVALID;
   if (!(prm->noise_var > 0.0) || !std::isfinite(prm->noise_var) || !(prm->prior_weight >= 0.0) ||
       !std::isfinite(prm->prior_weight) || !(prm->tol >= 0.0) || prm->max_iter < 0)

@@ -182,10 +182,10 @@ int prepare(Plan& P, char* ws, cudaStream_t stream) {
 }
 
 size_t kb2_smem() {
-  const size_t a = (size_t)16 * k2_frame_stride(512) + 256;
-  const size_t b = (size_t)8 * k2_frame_stride(1024) + 256;
-  const size_t c = (size_t)4 * k2_frame_stride(2048) + 256;
-  return std::max(a, std::max(b, c)) * sizeof(float2);
+  auto one = [](size_t F, size_t H) {
+    return ((size_t)F * k2_frame_stride((int)H) + 256) * sizeof(float2) + F * H + (H + 4) * sizeof(float);
+  };
+  return std::max(one(16, 512), std::max(one(8, 1024), one(4, 2048)));
 }
 
 int run_all(Plan& P, char* ws, cudaStream_t stream, bool columns_only = false, int only_cls = -1, int only_v = -1) {
@@ -257,7 +257,7 @@ extern "C" int ipfb_batched_plan(const ipfb_stream_desc* streams, int nstreams, 
   std::vector<Cost> c2, c3[kNumMClass], c4;
   for (int s = 0; s < nstreams; ++s) {
     const ipfb_stream_desc& d = streams[s];
-    if (!d.codes || !d.scale || !d.window || !d.x_out) {
+    if (!d.codes || !d.scale || !d.window || !d.x_out || (reinterpret_cast<uintptr_t>(d.codes) & 15)) {
       delete P;
       return IPFB_ERR_INVALID;
     }

@@ -40,15 +40,28 @@ __device__ __forceinline__ void k2_group(const uint8_t* __restrict__ codes, cons
   const int tid = threadIdx.x % TPF;
   float2* sm = smem + f * k2_frame_stride(H);
   const bool live = f < nvalid;
-  const int j = C * (m0 + (live ? f : 0)) + r;
-  const uint8_t* row = codes + (size_t)j * H;
   const float pre = 0.5f / (float)H;
   // exp(+2 pi i k / N), N = 2H, from two tables of 128 entries shared by the CTA
   float2* tw_hi = smem + F * k2_frame_stride(H);
   float2* tw_lo = tw_hi + 128;
+  // the F code rows (H bytes each) and the H+1 channel steps, staged with 16-byte loads
+  uint8_t* crow = reinterpret_cast<uint8_t*>(tw_lo + 128);
+  float* sscale = reinterpret_cast<float*>(crow + F * H);
   twid2_fill<7, true>(tw_hi, tw_lo, 2 * H, threadIdx.x, TPF * F);
+  {
+    constexpr int V = H / 16;  // 16-byte vectors per row
+    for (int i = threadIdx.x; i < F * V; i += TPF * F) {
+      const int ff = i / V, c = i % V;
+      if (ff < nvalid) {
+        const size_t jj = (size_t)C * (m0 + ff) + r;
+        reinterpret_cast<uint4*>(crow + ff * H)[c] = reinterpret_cast<const uint4*>(codes + jj * H)[c];
+      }
+    }
+    for (int i = threadIdx.x; i <= H; i += TPF * F) sscale[i] = scale[i];
+  }
   __syncthreads();
   const Twid2<7> tw{tw_hi, tw_lo};
+  const uint8_t* row = crow + f * H;
 
   // pre-processing: each thread forms Z[k] and Z[H-k] for k in [0, H/2]
   for (int k = tid; live && k <= H / 2; k += TPF) {
@@ -61,11 +74,11 @@ __device__ __forceinline__ void k2_group(const uint8_t* __restrict__ codes, cons
     };
     float2 yk, ym;
     if (k == 0) {
-      yk = make_float2(nib(bk, 0) * scale[0], 0.0f);
-      ym = make_float2(nib(bk, 1) * scale[H], 0.0f);
+      yk = make_float2(nib(bk, 0) * sscale[0], 0.0f);
+      ym = make_float2(nib(bk, 1) * sscale[H], 0.0f);
     } else {
-      yk = make_float2(nib(bk, 0) * scale[k], nib(bk, 1) * scale[k]);
-      ym = make_float2(nib(bm, 0) * scale[km], nib(bm, 1) * scale[km]);
+      yk = make_float2(nib(bk, 0) * sscale[k], nib(bk, 1) * sscale[k]);
+      ym = make_float2(nib(bm, 0) * sscale[km], nib(bm, 1) * sscale[km]);
     }
     // E, O at k:   E = (yk + conj ym)/2, O = (yk - conj ym) w/2, w = e^{+2 pi i k/N}
     const float2 w = tw(k);

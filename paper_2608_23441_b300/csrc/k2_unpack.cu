@@ -8,7 +8,7 @@ namespace {
 template <int H>
 cudaError_t k2(const uint8_t* codes, const float* scale, float2* d2, int C, int S, cudaStream_t st) {
   constexpr int TPF = tpf_for(H), F = fpc_for(H);
-  const size_t smem = ((size_t)F * k2_frame_stride(H) + 256) * sizeof(float2);
+  const size_t smem = ((size_t)F * k2_frame_stride(H) + 256) * sizeof(float2) + (size_t)F * H + (size_t)(H + 4) * sizeof(float);
   auto kern = k2_unpack_irfft<H, TPF, F>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

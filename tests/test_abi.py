@@ -75,6 +75,9 @@ def test_host_validation_rejects_before_launch():
     assert L.ipfb_wiener_upchannelize(ctypes.byref(g_up), fake, fake, fake, 0.01, 1, 3, fake, None, fake,
                                       1 << 30, None) == ipfb.ERR_UNSUPPORTED
     assert ipfb.lib().ipfb_set_max_column_run(1000) == ipfb.ERR_INVALID
+    # code arrays are read with 16-byte loads: an unaligned start is refused
+    odd = ctypes.c_void_p(0x1008)
+    assert L.ipfb_wiener(G, odd, fake, fake, 0.01, 1, fake, fake, 1 << 30, None) == ipfb.ERR_INVALID
 
 
 def test_binding_refuses_cpu_tensors():
