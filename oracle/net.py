@@ -12,7 +12,8 @@ Readings:
     weights applied as the ML preconditioner) scaled by its RMS s, and the prior
     mask m; output z = u + s * g(u / s, m)  (a learned correction of the Wiener
     preconditioner);
-  * GELU in its tanh form, 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3)));
+  * GELU in its exact form x Phi(x) = 0.5 x (1 + erf(x / sqrt 2)) (Hendrycks and
+    Gimpel 2016), the standard normal CDF Phi written through erf;
   * training target: the CG error e = x* - x_k of the residual r_k = A e; loss
     mean over positions of (g - (e - u)/s)^2;
   * the preconditioner is nonlinear, so the outer iteration is flexible CG with
@@ -24,11 +25,13 @@ from __future__ import annotations
 import math
 
 import numpy as np
+from scipy.special import erf
 
 K = 9
 HALF = K // 2
 C0, C1, C2, C3 = 2, 32, 32, 1
-SQ2PI = math.sqrt(2.0 / math.pi)
+INV_SQRT2 = 1.0 / math.sqrt(2.0)
+INV_SQRT2PI = 1.0 / math.sqrt(2.0 * math.pi)
 
 
 def n_params() -> int:
@@ -74,13 +77,13 @@ def bf16(x: np.ndarray) -> np.ndarray:
 
 
 def gelu(x):
-    return 0.5 * x * (1.0 + np.tanh(SQ2PI * (x + 0.044715 * x ** 3)))
+    """x Phi(x), Phi the standard normal CDF."""
+    return 0.5 * x * (1.0 + erf(x * INV_SQRT2))
 
 
 def gelu_grad(x):
-    t = np.tanh(SQ2PI * (x + 0.044715 * x ** 3))
-    dt = (1.0 - t * t) * SQ2PI * (1.0 + 3 * 0.044715 * x * x)
-    return 0.5 * (1.0 + t) + 0.5 * x * dt
+    """d/dx [x Phi(x)] = Phi(x) + x phi(x), phi the standard normal density."""
+    return 0.5 * (1.0 + erf(x * INV_SQRT2)) + x * INV_SQRT2PI * np.exp(-0.5 * x * x)
 
 
 def conv(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:

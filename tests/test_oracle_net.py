@@ -43,6 +43,13 @@ def test_gelu_and_its_derivative():
     assert np.allclose(net.gelu_grad(x), (net.gelu(x + h) - net.gelu(x - h)) / (2 * h), atol=1e-8)
     assert net.gelu(np.array([0.0]))[0] == 0.0
     assert abs(net.gelu(np.array([10.0]))[0] - 10.0) < 1e-12
+    # x Phi(x) against the normal CDF integrated by quadrature (no erf involved)
+    from scipy.integrate import quad
+    for v in (-2.3, -0.7, 0.4, 1.9):
+        phi_int, _ = quad(lambda t: np.exp(-0.5 * t * t) / np.sqrt(2 * np.pi), -np.inf, v)
+        assert abs(net.gelu(np.array([v]))[0] - v * phi_int) < 1e-12
+    # odd part: gelu(x) - gelu(-x) = x
+    assert np.allclose(net.gelu(x) - net.gelu(-x), x, atol=1e-14)
 
 
 def test_gradients_match_finite_differences():
