@@ -52,6 +52,8 @@ extern "C" {
 #define IPFB_OP_WIENER 2
 #define IPFB_OP_WIENER_UPCHAN 3
 #define IPFB_OP_ML 4
+#define IPFB_OP_ML_LEARNED 5 /* ipfb_ml_solve with precond = 2        */
+#define IPFB_OP_ML_PAIRS 6   /* ipfb_ml_training_pairs                 */
 
 typedef struct {
   int lblock;   /* N: power of two, 32 <= N <= 16384                              */
@@ -193,7 +195,14 @@ int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const flo
  * reduced in FP64, vectors are FP32.  Each column stops on its own when
  * ||b - A x|| / ||b|| <= tol (recursively updated residual), or after max_iter.
  * precond: 0 none; 1 Wiener, z = F^dagger[F r / (|W_n|^2/sigma^2 + lam mean(M_n))];
- * 2 learned (net != NULL; see ipfb_precond_*).
+ * 2 learned: net = device pointer to the net parameters (float [IPFB_NET_NPARAMS],
+ * see ipfb_net_forward), z = u + s g(u/s, m) with u the Wiener z above, s = RMS(u)
+ * over the column (1 if u = 0), m the column's prior mask; the outer iteration is
+ * then flexible CG (Notay 2000) with the Polak-Ribiere beta
+ * r_new.(z_new - z_old) / r_old.z_old.  precond 2 requires ntap = 4, runs two
+ * launches per iteration and synchronizes the stream every fourth iteration to
+ * test for completion (it cannot be captured in a CUDA graph); its workspace is
+ * ipfb_workspace_size(g, IPFB_OP_ML_LEARNED).
  * prior_mask: uint8 [J*N] time order (nonzero = saved sample); prior_values:
  * float [J*N]; x_inout: float [J*N], the initial guess when use_x0 != 0 (else
  * zero is used), the solution on return.  iters: int [N] iterations per column;
@@ -214,6 +223,56 @@ int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, 
                   const ipfb_ml_params* prm, const uint8_t* prior_mask, const float* prior_values,
                   const void* net, float* x_inout, int use_x0, int* iters, float* resid, void* ws,
                   size_t ws_bytes, void* stream);
+
+/*
+ * Learned preconditioner net.  The paper has no learned component: this is the
+ * learned variant of the Sec. 4.2 solve.  Per column (a sequence of J frames) a
+ * 1-D convolutional net along the frame axis with circular padding:
+ *   a1 = GELU(conv(x0, w1) + b1)   2 -> 32 channels, 9 taps
+ *   a2 = GELU(conv(a1, w2) + b2)   32 -> 32
+ *   y  = conv(a2, w3) + b3         32 -> 1
+ * conv(x, w)[co][j] = sum_{ci,t} w[co][ci][t] x[ci][(j + t - 4) mod J];
+ * GELU(x) = x Phi(x) = 0.5 x (1 + erf(x / sqrt 2)).
+ * theta: device float [IPFB_NET_NPARAMS] = w1[32][2][9], b1[32], w2[32][32][9],
+ * b2[32], w3[1][32][9], b3[1].  Weights and the activations x0, a1, a2 are rounded
+ * to BF16 (nearest even) and every convolution accumulates in FP32 on the tensor
+ * cores; biases, GELU and the loss are FP32.
+ * xin: device float [nslots][2][J] (channel 0 = u/s, channel 1 = mask);
+ * y, target: device float [nslots][J].
+ *
+ * ipfb_net_forward: y = net(xin).  Workspace ipfb_net_workspace_size(IPFB_NET_FORWARD).
+ * ipfb_net_grad: loss = sum over slots and frames of (y - target)^2 / (nslots J)
+ *   (device float [1], may be NULL) and its gradient with respect to theta
+ *   (device float [IPFB_NET_NPARAMS], may be NULL), the BF16 rounding of weights
+ *   and activations treated as the identity in the backward pass; partial sums
+ *   are reduced in a fixed order, so results are deterministic.
+ *   Workspace ipfb_net_workspace_size(IPFB_NET_GRAD).
+ * ipfb_net_adam: one Adam step (Kingma and Ba 2015) on theta with moment buffers
+ *   m, v (device float [n], zero before step 1); step counts from 1.
+ * ipfb_ml_training_pairs: training examples for the net from two iterates of a
+ *   solve with the same operator (g, window, prm: noise_var, prior_weight): for
+ *   each listed column pair i (pair_index: HOST int [npairs], npairs <= N/2, each
+ *   0 <= p < N/2, checked before anything is enqueued; pair p = columns 2p, 2p+1)
+ *   and h = 0, 1: e = x_star - x_k, r = A e, u = M_W r, s = RMS(u),
+ *   xin[2i+h] = (u/s, mask), target[2i+h] = (e - u)/s, i.e. what the net has to
+ *   add so that z = u + s g = A^{-1} r.  x_star, x_k: device float [J*N] time
+ *   order.  Requires ntap = 4.  Workspace ipfb_workspace_size(g, IPFB_OP_ML_PAIRS).
+ */
+#define IPFB_NET_NPARAMS 10145
+#define IPFB_NET_FORWARD 1
+#define IPFB_NET_GRAD 2
+
+int ipfb_net_nparams(void);
+int ipfb_net_workspace_size(int op, int nslots, int nframes, size_t* bytes);
+int ipfb_net_forward(const float* theta, int nslots, int nframes, const float* xin, float* y, void* ws,
+                     size_t ws_bytes, void* stream);
+int ipfb_net_grad(const float* theta, int nslots, int nframes, const float* xin, const float* target, float* loss,
+                  float* grad, void* ws, size_t ws_bytes, void* stream);
+int ipfb_net_adam(float* theta, float* m, float* v, const float* grad, int n, int step, double lr, double beta1,
+                  double beta2, double eps, void* stream);
+int ipfb_ml_training_pairs(const ipfb_geom* g, const float* window, const ipfb_ml_params* prm,
+                           const uint8_t* prior_mask, const float* x_star, const float* x_k, const int* pair_index,
+                           int npairs, float* xin, float* target, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * Batched inverse PFB of many independent streams of uneven shape (lblock in

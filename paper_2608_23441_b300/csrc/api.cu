@@ -20,6 +20,34 @@ namespace {
 thread_local char g_cuda_err[256] = "";
 
 bool misaligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; }
+
+size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Workspace of the learned-preconditioner solve: the pair-packed data d, the
+// flexible-CG vectors, the net requests and outputs, per-column state, two request
+// counters and the packed BF16 weights.
+struct FcgLayout {
+  size_t d2, X, R, P, Z, U, Y, netin, cs, cnt, pack, total;
+};
+FcgLayout fcg_layout(int N, int J) {
+  const size_t vec = (size_t)J * (size_t)N * sizeof(float);
+  FcgLayout L;
+  size_t o = 0;
+  for (size_t* f : {&L.d2, &L.X, &L.R, &L.P, &L.Z, &L.U, &L.Y}) {
+    *f = o;
+    o = al256(o + vec);
+  }
+  L.netin = o;
+  o = al256(o + 2 * vec);
+  L.cs = o;
+  o = al256(o + (size_t)N * fcg_col_bytes());
+  L.cnt = o;
+  o = al256(o + 4 * sizeof(int));
+  L.pack = o;
+  o = al256(o + net_pack_bytes());
+  L.total = o;
+  return L;
+}
 std::atomic<int> g_max_column_run{8192};
 
 // ---------------------------------------------------------------- stage timing
@@ -225,6 +253,15 @@ int ipfb_workspace_size(const ipfb_geom* g, int op, size_t* bytes) {
       if (g->nframes < 128 || g->nframes > 8192) return IPFB_ERR_UNSUPPORTED;
       *bytes = 2 * (size_t)g->nframes * (size_t)g->lblock * sizeof(float);
       return IPFB_OK;
+    case IPFB_OP_ML_LEARNED:
+    case IPFB_OP_ML_PAIRS:
+      rc = check_geom(g, true);
+      if (rc) return rc;
+      if (g->nframes < 128 || g->nframes > 8192 || g->ntap != 4) return IPFB_ERR_UNSUPPORTED;
+      *bytes = op == IPFB_OP_ML_LEARNED
+                   ? fcg_layout(g->lblock, g->nframes).total
+                   : 2 * (size_t)g->nframes * (size_t)g->lblock * sizeof(float) + al256((size_t)g->lblock / 2 * 4);
+      return IPFB_OK;
   }
   return IPFB_ERR_INVALID;
 }
@@ -349,6 +386,105 @@ int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const flo
   return IPFB_OK;
 }
 
+}  // extern "C"
+
+namespace {
+MLParams ml_params(const ipfb_geom* g, const ipfb_ml_params* prm, int use_x0) {
+  MLParams mp;
+  mp.inv_s2 = (float)(1.0 / prm->noise_var);
+  mp.lam = (float)prm->prior_weight;
+  mp.tol = (float)prm->tol;
+  mp.max_iter = prm->max_iter;
+  mp.ntap = g->ntap;
+  mp.precond = prm->precond;
+  mp.use_x0 = use_x0 ? 1 : 0;
+  return mp;
+}
+
+// Flexible CG with the learned preconditioner: two launches per iteration (the CG
+// step with its preconditioner request, then the net over the requests); the host
+// reads the number of open requests every fourth iteration and stops at zero.
+int ml_solve_learned(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
+                     const ipfb_ml_params* prm, const uint8_t* mask, const float* prior, const float* theta,
+                     float* x_inout, int use_x0, int* iters, float* resid, void* ws, size_t ws_bytes,
+                     cudaStream_t st) {
+  size_t need = 0;
+  int rc = ipfb_workspace_size(g, IPFB_OP_ML_LEARNED, &need);
+  if (rc) return rc;
+  if (!ws || ws_bytes < need) return IPFB_ERR_WORKSPACE;
+  const int N = g->lblock, J = g->nframes;
+  const FcgLayout L = fcg_layout(N, J);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  const float2* d2 = reinterpret_cast<const float2*>(w + L.d2);
+  FcgBufs b;
+  b.X = reinterpret_cast<float2*>(w + L.X);
+  b.R = reinterpret_cast<float2*>(w + L.R);
+  b.P = reinterpret_cast<float2*>(w + L.P);
+  b.Z = reinterpret_cast<float2*>(w + L.Z);
+  b.U = reinterpret_cast<float2*>(w + L.U);
+  b.Y = reinterpret_cast<float*>(w + L.Y);
+  b.netin = reinterpret_cast<float*>(w + L.netin);
+  b.cs = reinterpret_cast<FcgCol*>(w + L.cs);
+  int* cnt = reinterpret_cast<int*>(w + L.cnt);
+  uint8_t* packed = w + L.pack;
+  {
+    Stage t("k2_unpack_irfft", st);
+    CK(launch_k2(N / 2, codes, scale, const_cast<float2*>(d2), 1, J, st), "k2_unpack_irfft");
+    t.done();
+  }
+  if (use_x0) {
+    Stage t("k_time_to_pairs", st);
+    CK(launch_time_to_pairs(x_inout, b.X, N, J, st), "k_time_to_pairs");
+    t.done();
+  }
+  {
+    Stage t("k6_net_pack", st);
+    CK(launch_net_pack(theta, packed, st), "k6_net_pack");
+    t.done();
+  }
+  CK(cudaMemsetAsync(cnt, 0, 4 * sizeof(int), st), "cudaMemsetAsync");
+  const MLParams mp = ml_params(g, prm, use_x0);
+  {
+    Stage t("k5_fcg_step", st);
+    CK(launch_fcg_step(J, 0, d2, b, mask, prior, window, N, mp, cnt, st), "k5_fcg_step");
+    t.done();
+  }
+  int parity = 0;
+  for (int it = 0; it < prm->max_iter; ++it) {
+    {
+      Stage t("k6_net_forward", st);
+      CK(launch_net_forward(packed, b.netin, b.Y, J, 0, cnt + parity, cnt + (parity ^ 1), N, st),
+         "k6_net_forward");
+      t.done();
+    }
+    {
+      Stage t("k5_fcg_step", st);
+      CK(launch_fcg_step(J, it == 0 ? 1 : 2, d2, b, mask, prior, window, N, mp, cnt + (parity ^ 1), st),
+         "k5_fcg_step");
+      t.done();
+    }
+    parity ^= 1;
+    if ((it & 3) == 3) {
+      int open = 0;
+      CK(cudaMemcpyAsync(&open, cnt + parity, sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+      CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+      if (open == 0) break;
+    }
+  }
+  {
+    Stage t("k5_fcg_finish", st);
+    CK(launch_fcg_finish(J, d2, b, mask, prior, window, N, mp, iters, resid, st), "k5_fcg_finish");
+    t.done();
+  }
+  Stage t("k_pairs_to_time", st);
+  CK(launch_pairs_to_time(b.X, x_inout, N, 1, J, st), "k_pairs_to_time");
+  t.done();
+  return IPFB_OK;
+}
+}  // namespace
+
+extern "C" {
+
 int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
                   const ipfb_ml_params* prm, const uint8_t* prior_mask, const float* prior_values, const void* net,
                   float* x_inout, int use_x0, int* iters, float* resid, void* ws, size_t ws_bytes, void* stream) {
@@ -361,7 +497,11 @@ int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, 
       !std::isfinite(prm->prior_weight) || !(prm->tol >= 0.0) || prm->max_iter < 0)
     return IPFB_ERR_INVALID;
   if (prm->precond < 0 || prm->precond > 2) return IPFB_ERR_INVALID;
-  if (prm->precond == 2) return IPFB_ERR_UNSUPPORTED;
+  if (prm->precond == 2) {
+    if (!net) return IPFB_ERR_INVALID;
+    return ml_solve_learned(g, codes, scale, window, prm, prior_mask, prior_values, static_cast<const float*>(net),
+                            x_inout, use_x0, iters, resid, ws, ws_bytes, as_stream(stream));
+  }
   (void)net;
   size_t need = 0;
   if ((rc = ipfb_workspace_size(g, IPFB_OP_ML, &need))) return rc;
@@ -381,14 +521,7 @@ int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, 
     CK(launch_time_to_pairs(x_inout, x2, N, J, st), "k_time_to_pairs");
     t.done();
   }
-  MLParams mp;
-  mp.inv_s2 = (float)(1.0 / prm->noise_var);
-  mp.lam = (float)prm->prior_weight;
-  mp.tol = (float)prm->tol;
-  mp.max_iter = prm->max_iter;
-  mp.ntap = g->ntap;
-  mp.precond = prm->precond;
-  mp.use_x0 = use_x0 ? 1 : 0;
+  const MLParams mp = ml_params(g, prm, use_x0);
   {
     Stage t("k5_ml_cg", st);
     CK(launch_k5(J, d2, x2, prior_mask, prior_values, window, N, mp, iters, resid, st), "k5_ml_cg");
@@ -396,6 +529,107 @@ int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, 
   }
   Stage t("k_pairs_to_time", st);
   CK(launch_pairs_to_time(x2, x_inout, N, 1, J, st), "k_pairs_to_time");
+  t.done();
+  return IPFB_OK;
+}
+
+int ipfb_ml_training_pairs(const ipfb_geom* g, const float* window, const ipfb_ml_params* prm,
+                           const uint8_t* prior_mask, const float* x_star, const float* x_k, const int* pair_index,
+                           int npairs, float* xin, float* target, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_geom(g, true);
+  if (rc) return rc;
+  if (!window || !prm || !prior_mask || !x_star || !x_k || !pair_index || !xin || !target || npairs < 0 ||
+      npairs > g->lblock / 2)
+    return IPFB_ERR_INVALID;
+  for (int i = 0; i < npairs; ++i)
+    if (pair_index[i] < 0 || pair_index[i] >= g->lblock / 2) return IPFB_ERR_INVALID;
+  if (!(prm->noise_var > 0.0) || !std::isfinite(prm->noise_var) || !(prm->prior_weight >= 0.0) ||
+      !std::isfinite(prm->prior_weight))
+    return IPFB_ERR_INVALID;
+  size_t need = 0;
+  if ((rc = ipfb_workspace_size(g, IPFB_OP_ML_PAIRS, &need))) return rc;
+  if (!ws || ws_bytes < need) return IPFB_ERR_WORKSPACE;
+  if (npairs == 0) return IPFB_OK;
+  const int N = g->lblock, J = g->nframes;
+  cudaStream_t st = as_stream(stream);
+  float2* xs2 = reinterpret_cast<float2*>(ws);
+  float2* xk2 = xs2 + (size_t)J * (N / 2);
+  int* pl = reinterpret_cast<int*>(xk2 + (size_t)J * (N / 2));
+  CK(cudaMemcpyAsync(pl, pair_index, (size_t)npairs * sizeof(int), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+  CK(launch_time_to_pairs(x_star, xs2, N, J, st), "k_time_to_pairs");
+  CK(launch_time_to_pairs(x_k, xk2, N, J, st), "k_time_to_pairs");
+  const MLParams mp = ml_params(g, prm, 0);
+  Stage t("k5_net_pairs", st);
+  CK(launch_net_pairs(J, xs2, xk2, pl, npairs, prior_mask, window, N, mp, xin, target, st), "k5_net_pairs");
+  t.done();
+  return IPFB_OK;
+}
+
+int ipfb_net_nparams(void) { return net_nparams(); }
+
+int ipfb_net_workspace_size(int op, int nslots, int nframes, size_t* bytes) {
+  if (!bytes || nslots < 1 || nframes < 1) return IPFB_ERR_INVALID;
+  *bytes = 0;
+  if (op == IPFB_NET_FORWARD) {
+    *bytes = al256(net_pack_bytes());
+    return IPFB_OK;
+  }
+  if (op == IPFB_NET_GRAD) {
+    *bytes = al256(net_pack_bytes()) + (size_t)net_bwd_items(nslots, nframes) * (size_t)(net_nparams() + 1) * 4;
+    return IPFB_OK;
+  }
+  return IPFB_ERR_INVALID;
+}
+
+int ipfb_net_forward(const float* theta, int nslots, int nframes, const float* xin, float* y, void* ws,
+                     size_t ws_bytes, void* stream) {
+  if (!theta || !xin || !y || nslots < 1 || nframes < 1) return IPFB_ERR_INVALID;
+  size_t need = 0;
+  int rc = ipfb_net_workspace_size(IPFB_NET_FORWARD, nslots, nframes, &need);
+  if (rc) return rc;
+  if (!ws || ws_bytes < need) return IPFB_ERR_WORKSPACE;
+  cudaStream_t st = as_stream(stream);
+  uint8_t* packed = static_cast<uint8_t*>(ws);
+  CK(launch_net_pack(theta, packed, st), "k6_net_pack");
+  Stage t("k6_net_forward", st);
+  CK(launch_net_forward(packed, xin, y, nframes, nslots, nullptr, nullptr, nslots, st), "k6_net_forward");
+  t.done();
+  return IPFB_OK;
+}
+
+int ipfb_net_grad(const float* theta, int nslots, int nframes, const float* xin, const float* target, float* loss,
+                  float* grad, void* ws, size_t ws_bytes, void* stream) {
+  if (!theta || !xin || !target || (!loss && !grad) || nslots < 1 || nframes < 1) return IPFB_ERR_INVALID;
+  size_t need = 0;
+  int rc = ipfb_net_workspace_size(IPFB_NET_GRAD, nslots, nframes, &need);
+  if (rc) return rc;
+  if (!ws || ws_bytes < need) return IPFB_ERR_WORKSPACE;
+  cudaStream_t st = as_stream(stream);
+  uint8_t* packed = static_cast<uint8_t*>(ws);
+  float* part = reinterpret_cast<float*>(packed + al256(net_pack_bytes()));
+  const double n = (double)nslots * (double)nframes;
+  CK(launch_net_pack(theta, packed, st), "k6_net_pack");
+  {
+    Stage t("k6_net_backward", st);
+    CK(launch_net_backward(packed, xin, target, nframes, nslots, (float)(1.0 / n), part, st), "k6_net_backward");
+    t.done();
+  }
+  Stage t("k6_net_reduce", st);
+  CK(launch_net_reduce(part, net_bwd_items(nslots, nframes), grad, loss, st), "k6_net_reduce");
+  t.done();
+  return IPFB_OK;
+}
+
+int ipfb_net_adam(float* theta, float* m, float* v, const float* grad, int n, int step, double lr, double beta1,
+                  double beta2, double eps, void* stream) {
+  if (!theta || !m || !v || !grad || n < 1 || step < 1) return IPFB_ERR_INVALID;
+  if (!(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
+    return IPFB_ERR_INVALID;
+  const double c1 = 1.0 - std::pow(beta1, step), c2 = 1.0 - std::pow(beta2, step);
+  cudaStream_t st = as_stream(stream);
+  Stage t("k6_adam", st);
+  CK(launch_adam(theta, m, v, grad, n, (float)lr, (float)beta1, (float)beta2, (float)eps, (float)c1, (float)c2, st),
+     "k6_adam");
   t.done();
   return IPFB_OK;
 }

@@ -1,4 +1,5 @@
 // ML conjugate-gradient launches and the time-order -> column-pair transpose.
+#define IPFB_ML_HOST_KERNELS
 #include "launch.h"
 #include "ml_kernels.cuh"
 

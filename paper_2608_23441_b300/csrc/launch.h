@@ -46,7 +46,7 @@ struct MLParams {
   float tol;     // relative residual target per column
   int max_iter;
   int ntap;
-  int precond;   // 0 none, 1 Wiener
+  int precond;   // 0 none, 1 Wiener, 2 learned (flexible CG)
   int use_x0;    // 1: x2 holds the initial guess
 };
 
@@ -55,5 +55,36 @@ cudaError_t launch_k5(int J, const float2* d2, float2* x2, const uint8_t* mask, 
 cudaError_t launch_time_to_pairs(const float* x, float2* x2, int N, int J, cudaStream_t st);
 cudaError_t launch_upchan(const UpchanSrc& src, int L, long long nblocks, float2* out, float* x_out,
                           cudaStream_t st);
+
+// ---- learned preconditioner: flexible CG state and the net
+struct FcgCol;
+struct FcgBufs {
+  float2 *X, *R, *P, *Z, *U;  // [P][J] column-pair vectors
+  FcgCol* cs;                 // [N] per-column state
+  float* Y;                   // [N][J] net outputs (request slots)
+  float* netin;               // [N][2][J] net inputs (request slots)
+};
+size_t fcg_col_bytes();
+cudaError_t launch_fcg_step(int J, int phase, const float2* d2, const FcgBufs& b, const uint8_t* mask,
+                            const float* prior, const float* window, int N, const MLParams& mp, int* counter,
+                            cudaStream_t st);
+cudaError_t launch_fcg_finish(int J, const float2* d2, const FcgBufs& b, const uint8_t* mask, const float* prior,
+                              const float* window, int N, const MLParams& mp, int* iters, float* resid,
+                              cudaStream_t st);
+cudaError_t launch_net_pairs(int J, const float2* xs, const float2* xk, const int* pl, int npairs,
+                             const uint8_t* mask, const float* window, int N, const MLParams& mp, float* xin,
+                             float* target, cudaStream_t st);
+size_t net_pack_bytes();
+int net_nparams();
+long long net_bwd_items(int nslots, int J);
+long long net_fwd_items(int nslots, int J);
+cudaError_t launch_net_pack(const float* theta, uint8_t* packed, cudaStream_t st);
+cudaError_t launch_net_forward(const uint8_t* packed, const float* in, float* y, int J, int nslots_host,
+                               const int* count, int* zero_other, int max_slots, cudaStream_t st);
+cudaError_t launch_net_backward(const uint8_t* packed, const float* in, const float* target, int J, int nslots,
+                                float inv_n, float* part, cudaStream_t st);
+cudaError_t launch_net_reduce(const float* part, long long nitems, float* grad, float* loss, cudaStream_t st);
+cudaError_t launch_adam(float* theta, float* m, float* v, const float* g, int n, float lr, float beta1, float beta2,
+                        float eps, float c1, float c2, cudaStream_t st);
 
 }  // namespace ipfb

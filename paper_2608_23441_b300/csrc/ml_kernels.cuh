@@ -397,6 +397,7 @@ k5_ml_cg(const float2* __restrict__ d2, float2* __restrict__ x2, const uint8_t* 
   }
 }
 
+#ifdef IPFB_ML_HOST_KERNELS
 // time order [J][N] -> pair-packed [P][J] (initial guess)
 __global__ void k_time_to_pairs(const float* __restrict__ x, float2* __restrict__ x2, int N, int J) {
   __shared__ float2 tile[32][33];
@@ -413,5 +414,7 @@ __global__ void k_time_to_pairs(const float* __restrict__ x, float2* __restrict_
     if (p0 + pp < H && j0 + jj < J) x2[(size_t)(p0 + pp) * J + j0 + jj] = tile[jj][pp];
   }
 }
+
+#endif  // IPFB_ML_HOST_KERNELS
 
 }  // namespace ipfb

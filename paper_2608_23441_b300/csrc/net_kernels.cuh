@@ -1,0 +1,520 @@
+// Learned conjugate-gradient preconditioner net (the workload's learned variant of
+// the ML solve of Sec. 4.2; the paper itself has no learned component).
+//
+// Per column a 1-D convolutional net along the frame axis, circular padding:
+//   z1 = conv(x0, w1) + b1   (2 -> 32 channels, 9 taps)    a1 = GELU(z1)
+//   z2 = conv(a1, w2) + b2   (32 -> 32)                     a2 = GELU(z2)
+//   y  = conv(a2, w3) + b3   (32 -> 1)
+// conv(x, w)[co, j] = sum_{ci, t} w[co, ci, t] x[ci, (j + t - 4) mod J]  (cross-correlation),
+// GELU(x) = x Phi(x) = 0.5 x (1 + erf(x / sqrt 2)).
+// Parameters theta (FP32 master copy) are laid out w1[32][2][9], b1[32],
+// w2[32][32][9], b2[32], w3[1][32][9], b3[1]: 10145 values.
+//
+// Precision: weights and activations x0, a1, a2 are rounded to BF16 (round to
+// nearest even) and every convolution is a BF16 x BF16 -> FP32 tensor-core
+// contraction (mma.sync m16n8k16); biases, pre-activations, GELU and the loss are
+// FP32.  Each convolution is a GEMM over positions: row = position, K = (tap,
+// input channel), so the tap shift is a row offset into a [position][channel]
+// tile in shared memory.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace ipfb {
+namespace netk {
+
+constexpr int KW = 9;
+constexpr int HALF = 4;
+constexpr int CH = 32;
+constexpr int OW1 = 0, OB1 = 576, OW2 = 608, OB2 = 9824, OW3 = 9856, OB3 = 10144, NPARAM = 10145;
+
+// Packed BF16 weights.  Row strides of 40 and 296 elements (80 B and 592 B) put
+// the 8 rows that one ldmatrix phase reads into distinct 16-byte bank groups.
+constexpr int S32 = 40;
+constexpr int S288 = 296;
+constexpr int PW1 = 0;                 // [32 co][S32]   k = 2t + ci   (k < 18, rest 0)
+constexpr int PW2 = PW1 + 32 * S32;    // [32 co][S288]  k = 32t + ci
+constexpr int PW3 = PW2 + 32 * S288;   // [8][S288]      row 0: k = 32t + ci; rows 1..7 zero
+constexpr int PW2T = PW3 + 8 * S288;   // [32 ci][S288]  k = 32t' + co: w2[co][ci][8 - t']
+constexpr int NPACK_BF = PW2T + 32 * S288;          // 22592 bf16
+constexpr int NFWD_BF = PW2T;                       // forward needs W1, W2, W3
+constexpr size_t PACK_BIAS_OFF = (size_t)NPACK_BF * 2;  // bytes; FP32 b1[32] b2[32] b3[1] pad[3]
+constexpr size_t PACK_BYTES = PACK_BIAS_OFF + 68 * sizeof(float);
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// d/dx x Phi(x) = Phi(x) + x phi(x)
+__device__ __forceinline__ float gelu_grad_f(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo (low 16 bits), .y = hi
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+__device__ __forceinline__ float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
+__device__ __forceinline__ float bf_at(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t& r0, uint32_t& r1, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(smem_u32(p)));
+}
+// D += A B, A 16x16 (row-major fragments), B 16x8 (column-major fragments), FP32 accumulators
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Lane address of an ldmatrix.x4 A tile (16 rows x 16 k) of a row-major [row][k] array:
+// matrices (rows 0-7, k 0-7), (rows 8-15, k 0-7), (rows 0-7, k 8-15), (rows 8-15, k 8-15).
+__device__ __forceinline__ const __nv_bfloat16* a_tile_addr(const __nv_bfloat16* base, int stride, int row0, int k0,
+                                                          int lane) {
+  const int mi = lane >> 3, ri = lane & 7;
+  return base + (row0 + ri + (mi & 1) * 8) * stride + k0 + (mi >> 1) * 8;
+}
+// Lane address of an ldmatrix.x4 B pair (two n-tiles of 8 x 16 k) of an [n][k] array:
+// registers 0,1 = (b0, b1) of n-tile n0, registers 2,3 = (b0, b1) of n-tile n0 + 8.
+__device__ __forceinline__ const __nv_bfloat16* b_pair_addr(const __nv_bfloat16* base, int stride, int n0, int k0,
+                                                          int lane) {
+  const int mi = lane >> 3, ri = lane & 7;
+  return base + (n0 + ri + (mi >> 1) * 8) * stride + k0 + (mi & 1) * 8;
+}
+
+// theta (FP32) -> packed BF16 weights + FP32 biases
+__global__ void k6_net_pack(const float* __restrict__ theta, uint8_t* __restrict__ packed) {
+  __nv_bfloat16* pw = reinterpret_cast<__nv_bfloat16*>(packed);
+  float* pb = reinterpret_cast<float*>(packed + PACK_BIAS_OFF);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NPACK_BF + 68; i += gridDim.x * blockDim.x) {
+    if (i >= NPACK_BF) {
+      const int b = i - NPACK_BF;
+      float v = 0.0f;
+      if (b < 32) v = theta[OB1 + b];
+      else if (b < 64) v = theta[OB2 + b - 32];
+      else if (b == 64) v = theta[OB3];
+      pb[b] = v;
+      continue;
+    }
+    float v = 0.0f;
+    if (i < PW2) {
+      const int co = i / S32, k = i % S32;
+      if (k < 18) v = theta[OW1 + (co * 2 + (k & 1)) * KW + (k >> 1)];
+    } else if (i < PW3) {
+      const int co = (i - PW2) / S288, k = (i - PW2) % S288;
+      if (k < 288) v = theta[OW2 + (co * CH + (k & 31)) * KW + (k >> 5)];
+    } else if (i < PW2T) {
+      const int row = (i - PW3) / S288, k = (i - PW3) % S288;
+      if (row == 0 && k < 288) v = theta[OW3 + (k & 31) * KW + (k >> 5)];
+    } else {
+      const int ci = (i - PW2T) / S288, k = (i - PW2T) % S288;
+      if (k < 288) v = theta[OW2 + ((k & 31) * CH + ci) * KW + (8 - (k >> 5))];
+    }
+    pw[i] = __float2bfloat16_rn(v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Shared pieces of the forward and backward kernels
+// ---------------------------------------------------------------------------
+// Copy packed BF16 rows [0, nbf) and the biases into shared memory (16-byte copies).
+__device__ __forceinline__ void load_pack(const uint8_t* __restrict__ packed, __nv_bfloat16* wsm, float* bsm, int nbf,
+                                          int nbf_off = 0) {
+  const uint4* src = reinterpret_cast<const uint4*>(packed + (size_t)nbf_off * 2);
+  uint4* dst = reinterpret_cast<uint4*>(wsm);
+  for (int i = threadIdx.x; i < nbf / 8; i += blockDim.x) dst[i] = src[i];
+  const float* pb = reinterpret_cast<const float*>(packed + PACK_BIAS_OFF);
+  for (int i = threadIdx.x; i < 68; i += blockDim.x) bsm[i] = pb[i];
+}
+
+// x0 rows: x0s[i] = (bf16 ch0, bf16 ch1) at position (q0 + i) mod J, i < nrows
+__device__ __forceinline__ void load_x0(const float* __restrict__ in, int J, int q0, int nrows, uint32_t* x0s) {
+  for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+    int q = (q0 + i) % J;
+    if (q < 0) q += J;
+    x0s[i] = pack_bf2(__ldg(in + q), __ldg(in + J + q));
+  }
+}
+
+// im2col of layer 1: A1[i][2t + ci] = x0[i + t][ci] (t < 9), zero for k in [18, 32)
+__device__ __forceinline__ void build_a1col(const uint32_t* x0s, int nrows, __nv_bfloat16* A1s) {
+  for (int idx = threadIdx.x; idx < nrows * 16; idx += blockDim.x) {
+    const int i = idx >> 4, t = idx & 15;
+    reinterpret_cast<uint32_t*>(A1s + i * S32)[t] = t < KW ? x0s[i + t] : 0u;
+  }
+}
+
+// One conv layer as MT m-tiles (16 output rows each) x 4 n-tiles (32 output channels)
+// for this warp: rows [m0, m0 + 16) of the output use A rows m0 + t + [0, 16) (tap t)
+// when TAPS, else rows m0 + [0, 16) with K contiguous.  KSTEPS = K / 16.
+// The epilogue receives (row, col, v0, v1) for columns col, col + 1.
+template <int KSTEPS, bool TAPS, class EPI>
+__device__ __forceinline__ void conv_layer_warp(const __nv_bfloat16* A, int astride, const __nv_bfloat16* B,
+                                                int bstride, int m0, int lane, EPI epi) {
+  float acc[4][4];
+#pragma unroll
+  for (int n = 0; n < 4; ++n)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[n][q] = 0.0f;
+#pragma unroll 2
+  for (int ks = 0; ks < KSTEPS; ++ks) {
+    // with taps: k-step ks covers tap ks / 2, input channels 16 (ks % 2) .. + 15
+    const int arow = TAPS ? m0 + (ks >> 1) : m0;
+    const int acol = TAPS ? (ks & 1) * 16 : ks * 16;
+    uint32_t a[4], b01[4], b23[4];
+    ldsm_x4(a, a_tile_addr(A, astride, arow, acol, lane));
+    ldsm_x4(b01, b_pair_addr(B, bstride, 0, ks * 16, lane));
+    ldsm_x4(b23, b_pair_addr(B, bstride, 16, ks * 16, lane));
+    mma_bf16(acc[0], a, b01[0], b01[1]);
+    mma_bf16(acc[1], a, b01[2], b01[3]);
+    mma_bf16(acc[2], a, b23[0], b23[1]);
+    mma_bf16(acc[3], a, b23[2], b23[3]);
+  }
+  const int g = lane >> 2, c = lane & 3;
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    epi(m0 + g, n * 8 + 2 * c, acc[n][0], acc[n][1]);
+    epi(m0 + g + 8, n * 8 + 2 * c, acc[n][2], acc[n][3]);
+  }
+}
+
+// Layer 3 (one output channel, padded to an 8-wide n-tile) for one m-tile:
+// returns through epi(row, value) for the rows this lane holds (lanes with c == 0).
+template <class EPI>
+__device__ __forceinline__ void conv_out_warp(const __nv_bfloat16* A, const __nv_bfloat16* W3, int m0, int lane,
+                                              EPI epi) {
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const int l16 = lane & 15;
+#pragma unroll 2
+  for (int ks = 0; ks < 18; ++ks) {
+    uint32_t a[4], b0, b1;
+    ldsm_x4(a, a_tile_addr(A, S32, m0 + (ks >> 1), (ks & 1) * 16, lane));
+    // x2: lanes 0-7 address rows 0-7 at k0, lanes 8-15 rows 0-7 at k0 + 8
+    ldsm_x2(b0, b1, W3 + (l16 & 7) * S288 + ks * 16 + (l16 >> 3) * 8);
+    mma_bf16(acc, a, b0, b1);
+  }
+  const int g = lane >> 2, c = lane & 3;
+  if (c == 0) {
+    epi(m0 + g, acc[0]);
+    epi(m0 + g + 8, acc[2]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward: y[slot][j] for slots [0, nslots) (nslots from *count if count != null).
+// Work item = (slot, tile of FT outputs); persistent CTAs of 256 threads.
+// Rows: x0 i <-> p0 - 12 + i (264), a1 i <-> p0 - 8 + i (256, +8 zero rows),
+//       a2 i <-> p0 - 4 + i (256, first 248 used), y i <-> p0 + i (240).
+// ---------------------------------------------------------------------------
+constexpr int FT = 240;
+constexpr int F_X0 = FT + 24;   // 264
+constexpr int F_A1 = FT + 16;   // 256 computed rows of a1
+constexpr int F_A2 = FT + 16;   // 256 computed rows of a2 (248 valid)
+constexpr size_t fwd_smem_bytes() {
+  return (size_t)NFWD_BF * 2 + 68 * 4 + (size_t)F_X0 * 4 + (size_t)(F_A1 + 8) * S32 * 2 + (size_t)F_A2 * S32 * 2;
+}
+
+__global__ void __launch_bounds__(256)
+k6_net_forward(const uint8_t* __restrict__ packed, const float* __restrict__ in, float* __restrict__ y, int J,
+               int nslots_host, const int* __restrict__ count, int* __restrict__ zero_other) {
+  extern __shared__ __align__(16) uint8_t smraw[];
+  __nv_bfloat16* wsm = reinterpret_cast<__nv_bfloat16*>(smraw);
+  float* bsm = reinterpret_cast<float*>(smraw + (size_t)NFWD_BF * 2);
+  uint32_t* x0s = reinterpret_cast<uint32_t*>(bsm + 68);
+  __nv_bfloat16* a1s = reinterpret_cast<__nv_bfloat16*>(x0s + F_X0);
+  __nv_bfloat16* a2s = a1s + (F_A1 + 8) * S32;  // also the layer-1 im2col
+  const __nv_bfloat16* W1 = wsm + PW1;
+  const __nv_bfloat16* W2 = wsm + PW2;
+  const __nv_bfloat16* W3 = wsm + PW3;
+
+  if (zero_other && blockIdx.x == 0 && threadIdx.x == 0) *zero_other = 0;
+  const int nslots = count ? *count : nslots_host;
+  const int ntile = (J + FT - 1) / FT;
+  const long long nitems = (long long)nslots * ntile;
+  if ((long long)blockIdx.x >= nitems) return;
+
+  load_pack(packed, wsm, bsm, NFWD_BF);
+  // the 8 rows past a1 (read by the unused a2 rows 248..255) stay zero
+  for (int i = threadIdx.x; i < 8 * S32 / 2; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(a1s + F_A1 * S32)[i] = 0u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int slot = (int)(item / ntile), tile = (int)(item % ntile);
+    const int p0 = tile * FT;
+    __syncthreads();  // previous item's readers are done
+    load_x0(in + (size_t)slot * 2 * J, J, p0 - 12, F_X0, x0s);
+    __syncthreads();
+    build_a1col(x0s, F_A1, a2s);
+    __syncthreads();
+    // layer 1: m-tiles warp, warp + 8
+#pragma unroll 1
+    for (int mt = warp; mt < F_A1 / 16; mt += 8)
+      conv_layer_warp<2, false>(a2s, S32, W1, S32, mt * 16, lane, [&](int r, int cc, float v0, float v1) {
+        v0 = gelu_f(v0 + bsm[cc]);
+        v1 = gelu_f(v1 + bsm[cc + 1]);
+        *reinterpret_cast<uint32_t*>(a1s + r * S32 + cc) = pack_bf2(v0, v1);
+      });
+    __syncthreads();
+    // layer 2
+#pragma unroll 1
+    for (int mt = warp; mt < F_A2 / 16; mt += 8)
+      conv_layer_warp<18, true>(a1s, S32, W2, S288, mt * 16, lane, [&](int r, int cc, float v0, float v1) {
+        v0 = gelu_f(v0 + bsm[32 + cc]);
+        v1 = gelu_f(v1 + bsm[32 + cc + 1]);
+        *reinterpret_cast<uint32_t*>(a2s + r * S32 + cc) = pack_bf2(v0, v1);
+      });
+    __syncthreads();
+    // layer 3
+    float* yo = y + (size_t)slot * J;
+    const float b3 = bsm[64];
+#pragma unroll 1
+    for (int mt = warp; mt < FT / 16; mt += 8)
+      conv_out_warp(a2s, W3, mt * 16, lane, [&](int r, float v) {
+        if (p0 + r < J) yo[p0 + r] = v + b3;
+      });
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Backward (loss = sum over all positions of (y - target)^2 * inv_n): per work item
+// the tile's forward is recomputed with the halo the gradients need, then
+//   dy -> dW3, db3;  da2 = conv^T(dy, w3), dz2 = da2 GELU'(z2) -> dW2, db2;
+//   da1 = conv^T(dz2, w2) (tensor cores), dz1 = da1 GELU'(z1) -> dW1, db1.
+// Each item writes its partial gradient (NPARAM values) and loss to part[item].
+// Rows (tile positions [p0, p0 + BT)):
+//   x0  i <-> p0 - 20 + i  (264)      a1  i <-> p0 - 16 + i  (256 + 8 zero)
+//   a2  i <-> p0 - 12 + i  (256, 248 valid)   y/dy i <-> p0 - 8 + i (240)
+//   dz2 i <-> p0 - 4 + i   (232)      dz1 i <-> p0 + i (224)
+// ---------------------------------------------------------------------------
+constexpr int BT = 224;
+constexpr int B_X0 = BT + 40;   // 264
+constexpr int B_A1 = BT + 32;   // 256
+constexpr int B_A2 = BT + 32;   // 256 computed, 248 valid
+constexpr int B_Y = BT + 16;    // 240
+constexpr int B_DZ2 = BT + 8;   // 232
+constexpr int GP_STRIDE = 33;   // FP32 rows of 32 channels, padded
+
+struct BwdSmem {
+  static constexpr size_t w = 0;                                        // packed bf16 (all, incl. W2T)
+  static constexpr size_t b = w + (size_t)NPACK_BF * 2;                 // 68 floats
+  static constexpr size_t x0 = b + 68 * 4;                              // [264] u32
+  static constexpr size_t a1 = x0 + (size_t)B_X0 * 4;                   // [264][S32] bf16
+  static constexpr size_t a2 = a1 + (size_t)(B_A1 + 8) * S32 * 2;       // [256][S32] bf16
+  static constexpr size_t dz2 = a2 + (size_t)B_A2 * S32 * 2;            // [256][S32] bf16 (also im2col)
+  static constexpr size_t gp2 = dz2 + (size_t)B_A1 * S32 * 2;           // [232][33] f32 GELU'(z2)
+  static constexpr size_t gp1 = gp2 + (size_t)B_DZ2 * GP_STRIDE * 4;    // [224][33] f32 GELU'(z1), then dz1
+  static constexpr size_t dy = gp1 + (size_t)BT * GP_STRIDE * 4;        // [240] f32
+  static constexpr size_t red = dy + (size_t)B_Y * 4;                   // [8 warps][8] f32
+  static constexpr size_t total = red + 64 * 4;
+};
+
+__global__ void __launch_bounds__(256, 1)
+k6_net_backward(const uint8_t* __restrict__ packed, const float* __restrict__ in, const float* __restrict__ target,
+                int J, int nslots, float inv_n, float* __restrict__ part) {
+  extern __shared__ __align__(16) uint8_t smraw[];
+  __nv_bfloat16* wsm = reinterpret_cast<__nv_bfloat16*>(smraw + BwdSmem::w);
+  float* bsm = reinterpret_cast<float*>(smraw + BwdSmem::b);
+  uint32_t* x0s = reinterpret_cast<uint32_t*>(smraw + BwdSmem::x0);
+  __nv_bfloat16* a1s = reinterpret_cast<__nv_bfloat16*>(smraw + BwdSmem::a1);
+  __nv_bfloat16* a2s = reinterpret_cast<__nv_bfloat16*>(smraw + BwdSmem::a2);
+  __nv_bfloat16* dz2s = reinterpret_cast<__nv_bfloat16*>(smraw + BwdSmem::dz2);
+  float* gp2 = reinterpret_cast<float*>(smraw + BwdSmem::gp2);
+  float* gp1 = reinterpret_cast<float*>(smraw + BwdSmem::gp1);
+  float* dys = reinterpret_cast<float*>(smraw + BwdSmem::dy);
+  float* red = reinterpret_cast<float*>(smraw + BwdSmem::red);
+  const __nv_bfloat16* W1 = wsm + PW1;
+  const __nv_bfloat16* W2 = wsm + PW2;
+  const __nv_bfloat16* W3 = wsm + PW3;
+  const __nv_bfloat16* W2T = wsm + PW2T;
+
+  const int ntile = (J + BT - 1) / BT;
+  const long long nitems = (long long)nslots * ntile;
+  if ((long long)blockIdx.x >= nitems) return;
+  load_pack(packed, wsm, bsm, NPACK_BF);
+  for (int i = threadIdx.x; i < 8 * S32 / 2; i += blockDim.x) reinterpret_cast<uint32_t*>(a1s + B_A1 * S32)[i] = 0u;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int slot = (int)(item / ntile), tile = (int)(item % ntile);
+    const int p0 = tile * BT;
+    const float* tg = target + (size_t)slot * J;
+    float* pg = part + (size_t)item * (NPARAM + 1);
+    __syncthreads();
+    load_x0(in + (size_t)slot * 2 * J, J, p0 - 20, B_X0, x0s);
+    __syncthreads();
+    build_a1col(x0s, B_A1, dz2s);
+    __syncthreads();
+    // ---- forward recompute; keep GELU'(z) on the rows the backward uses
+#pragma unroll 1
+    for (int mt = warp; mt < B_A1 / 16; mt += 8)
+      conv_layer_warp<2, false>(dz2s, S32, W1, S32, mt * 16, lane, [&](int r, int cc, float v0, float v1) {
+        v0 += bsm[cc];
+        v1 += bsm[cc + 1];
+        // a1 row r <-> dz1 row r - 16
+        if (r >= 16 && r < 16 + BT) {
+          gp1[(r - 16) * GP_STRIDE + cc] = gelu_grad_f(v0);
+          gp1[(r - 16) * GP_STRIDE + cc + 1] = gelu_grad_f(v1);
+        }
+        *reinterpret_cast<uint32_t*>(a1s + r * S32 + cc) = pack_bf2(gelu_f(v0), gelu_f(v1));
+      });
+    __syncthreads();
+#pragma unroll 1
+    for (int mt = warp; mt < B_A2 / 16; mt += 8)
+      conv_layer_warp<18, true>(a1s, S32, W2, S288, mt * 16, lane, [&](int r, int cc, float v0, float v1) {
+        v0 += bsm[32 + cc];
+        v1 += bsm[32 + cc + 1];
+        // a2 row r <-> dz2 row r - 8
+        if (r >= 8 && r < 8 + B_DZ2) {
+          gp2[(r - 8) * GP_STRIDE + cc] = gelu_grad_f(v0);
+          gp2[(r - 8) * GP_STRIDE + cc + 1] = gelu_grad_f(v1);
+        }
+        *reinterpret_cast<uint32_t*>(a2s + r * S32 + cc) = pack_bf2(gelu_f(v0), gelu_f(v1));
+      });
+    __syncthreads();
+    float loss_part = 0.0f;
+    {
+      const float b3 = bsm[64];
+#pragma unroll 1
+      for (int mt = warp; mt < B_Y / 16; mt += 8)
+        conv_out_warp(a2s, W3, mt * 16, lane, [&](int r, float v) {
+          // y row r <-> position p0 - 8 + r
+          int q = (p0 - 8 + r) % J;
+          if (q < 0) q += J;
+          const float diff = v + b3 - __ldg(tg + q);
+          dys[r] = 2.0f * inv_n * diff;
+          if (r >= 8 && r < 8 + BT && p0 + r - 8 < J) loss_part = fmaf(diff * inv_n, diff, loss_part);
+        });
+    }
+    __syncthreads();
+    // positions past J in the last tile contribute no gradient
+    const int nvalid = min(BT, J - p0);
+    // ---- dW3[ci][t] = sum_pos dy[pos] a2[pos + t - 4][ci]: dy row i + 8, a2 row i + 8 + t
+    for (int o = tid; o < 288 + 1; o += blockDim.x) {
+      float s = 0.0f;
+      if (o < 288) {
+        const int ci = o / KW, t = o % KW;
+        for (int i = 0; i < nvalid; ++i) s = fmaf(dys[i + 8], bf_at(a2s + (i + 8 + t) * S32 + ci), s);
+        pg[OW3 + o] = s;
+      } else {
+        for (int i = 0; i < nvalid; ++i) s += dys[i + 8];
+        pg[OB3] = s;
+      }
+    }
+    // ---- dz2[i][ci] = GELU'(z2) * sum_t w3[ci][t] dy[i + 8 - t]  (i < 232)
+    for (int idx = tid; idx < B_DZ2 * 16; idx += blockDim.x) {
+      const int i = idx >> 4, c2 = (idx & 15) * 2;
+      float d0 = 0.0f, d1 = 0.0f;
+#pragma unroll
+      for (int t = 0; t < KW; ++t) {
+        const float dyv = dys[i + 8 - t];
+        d0 = fmaf(bf_at(W3 + t * 32 + c2), dyv, d0);
+        d1 = fmaf(bf_at(W3 + t * 32 + c2 + 1), dyv, d1);
+      }
+      d0 *= gp2[i * GP_STRIDE + c2];
+      d1 *= gp2[i * GP_STRIDE + c2 + 1];
+      // dz2 rows outside the valid positions (beyond J in the last tile) are real
+      // gradients of neighbouring positions only through the circular wrap; keep them
+      // (they feed da1 of valid rows) but exclude them from the weight sums below.
+      gp2[i * GP_STRIDE + c2] = d0;
+      gp2[i * GP_STRIDE + c2 + 1] = d1;
+      *reinterpret_cast<uint32_t*>(dz2s + i * S32 + c2) = pack_bf2(d0, d1);
+    }
+    __syncthreads();
+    // ---- da1 = conv^T(dz2, w2) on the tile rows (tensor cores), dz1 = da1 GELU'(z1)
+#pragma unroll 1
+    for (int mt = warp; mt < BT / 16; mt += 8)
+      conv_layer_warp<18, true>(dz2s, S32, W2T, S288, mt * 16, lane, [&](int r, int cc, float v0, float v1) {
+        gp1[r * GP_STRIDE + cc] *= v0;
+        gp1[r * GP_STRIDE + cc + 1] *= v1;
+      });
+    // ---- db2, dW2[co][ci][t] = sum_pos dz2[pos][co] a1[pos + t - 4][ci]
+    //   dz2 row i + 4 (FP32 in gp2), a1 row i + 12 + t, i < nvalid
+    for (int o = tid; o < CH * CH * KW + CH; o += blockDim.x) {
+      float s = 0.0f;
+      if (o < CH * CH * KW) {
+        const int co = o / (CH * KW), rem = o % (CH * KW), ci = rem / KW, t = rem % KW;
+        for (int i = 0; i < nvalid; ++i)
+          s = fmaf(gp2[(i + 4) * GP_STRIDE + co], bf_at(a1s + (i + 12 + t) * S32 + ci), s);
+        pg[OW2 + o] = s;
+      } else {
+        const int co = o - CH * CH * KW;
+        for (int i = 0; i < nvalid; ++i) s += gp2[(i + 4) * GP_STRIDE + co];
+        pg[OB2 + co] = s;
+      }
+    }
+    __syncthreads();
+    // ---- db1, dW1[co][ci][t] = sum_pos dz1[pos][co] x0[pos + t - 4][ci]: dz1 row i, x0 row i + 16 + t
+    for (int o = tid; o < CH * 2 * KW + CH; o += blockDim.x) {
+      float s = 0.0f;
+      if (o < CH * 2 * KW) {
+        const int co = o / (2 * KW), ci = (o / KW) & 1, t = o % KW;
+        for (int i = 0; i < nvalid; ++i) {
+          const uint32_t xv = x0s[i + 16 + t];
+          s = fmaf(gp1[i * GP_STRIDE + co], ci ? bf_hi(xv) : bf_lo(xv), s);
+        }
+        pg[OW1 + o] = s;
+      } else {
+        const int co = o - CH * 2 * KW;
+        for (int i = 0; i < nvalid; ++i) s += gp1[i * GP_STRIDE + co];
+        pg[OB1 + co] = s;
+      }
+    }
+    // ---- loss of the tile
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) loss_part += __shfl_xor_sync(0xffffffffu, loss_part, o);
+    if (lane == 0) red[warp] = loss_part;
+    __syncthreads();
+    if (tid == 0) {
+      float s = 0.0f;
+      for (int w = 0; w < 8; ++w) s += red[w];
+      pg[NPARAM] = s;
+    }
+  }
+}
+
+// grad[k] = sum over items of part[item][k] (k <= NPARAM: the last entry is the loss),
+// FP64 accumulation in item order (deterministic)
+__global__ void k6_net_reduce(const float* __restrict__ part, long long nitems, float* __restrict__ grad,
+                              float* __restrict__ loss) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > NPARAM) return;
+  double s = 0.0;
+  for (long long i = 0; i < nitems; ++i) s += (double)part[(size_t)i * (NPARAM + 1) + k];
+  if (k < NPARAM) {
+    if (grad) grad[k] = (float)s;
+  } else if (loss) {
+    *loss = (float)s;
+  }
+}
+
+// Adam (Kingma and Ba 2015) with bias corrections c1 = 1 - beta1^t, c2 = 1 - beta2^t
+__global__ void k6_adam(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
+                        const float* __restrict__ g, int n, float lr, float beta1, float beta2, float eps, float c1,
+                        float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = fmaf(beta1, m[i], (1.0f - beta1) * gi);
+  const float vi = fmaf(beta2, v[i], (1.0f - beta2) * gi * gi);
+  m[i] = mi;
+  v[i] = vi;
+  theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+}  // namespace netk
+}  // namespace ipfb

@@ -20,7 +20,9 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "ipfb.h")
 
 OK = 0
 ERR_INVALID, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA = -1, -2, -3, -4, -5, -6
-OP_FORWARD, OP_WIENER, OP_WIENER_UPCHAN, OP_ML = 1, 2, 3, 4
+OP_FORWARD, OP_WIENER, OP_WIENER_UPCHAN, OP_ML, OP_ML_LEARNED, OP_ML_PAIRS = 1, 2, 3, 4, 5, 6
+NET_FORWARD, NET_GRAD = 1, 2
+NET_NPARAMS = 10145
 
 
 class Geom(ctypes.Structure):
@@ -81,6 +83,13 @@ _SIGS = {
     "ipfb_batched_free": (_I, [_P]),
     "ipfb_ml_solve": (_I, [ctypes.POINTER(Geom), _P, _P, _P, ctypes.POINTER(MLParams), _P, _P, _P, _P, _I, _P, _P,
                            _P, _SZ, _P]),
+    "ipfb_net_nparams": (_I, []),
+    "ipfb_net_workspace_size": (_I, [_I, _I, _I, ctypes.POINTER(_SZ)]),
+    "ipfb_net_forward": (_I, [_P, _I, _I, _P, _P, _P, _SZ, _P]),
+    "ipfb_net_grad": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _SZ, _P]),
+    "ipfb_net_adam": (_I, [_P, _P, _P, _P, _I, _I, _D, _D, _D, _D, _P]),
+    "ipfb_ml_training_pairs": (_I, [ctypes.POINTER(Geom), _P, ctypes.POINTER(MLParams), _P, _P, _P, _P, _I, _P, _P,
+                                    _P, _SZ, _P]),
 }
 
 
@@ -308,12 +317,107 @@ def ml_solve(codes, scale, window, noise_var: float, mask, prior, prior_weight: 
     iters = torch.empty(N, dtype=torch.int32, device=codes.device)
     resid = torch.empty((2, N), dtype=torch.float32, device=codes.device)
     prm = MLParams(float(noise_var), float(prior_weight), float(tol), int(max_iter), PRECOND[precond])
-    ws, wsb = _workspace(workspace_size(g, OP_ML), codes.device, workspace)
+    if precond == "learned":
+        if net is None:
+            raise ValueError("precond='learned' needs net (float32 CUDA tensor of NET_NPARAMS parameters)")
+        net = _dev(net, torch.float32, "net")
+        if net.numel() != NET_NPARAMS:
+            raise ValueError(f"net has {net.numel()} parameters, expected {NET_NPARAMS}")
+    ws, wsb = _workspace(workspace_size(g, OP_ML_LEARNED if precond == "learned" else OP_ML), codes.device,
+                         workspace)
     _check("ipfb_ml_solve", lib().ipfb_ml_solve(ctypes.byref(g), _ptr(codes), _ptr(scale), _ptr(window),
                                                 ctypes.byref(prm), _ptr(mask), _ptr(prior), _ptr(net), _ptr(x),
                                                 int(x0 is not None), _ptr(iters), _ptr(resid), _ptr(ws), wsb,
                                                 _stream()))
     return x, iters, resid
+
+
+def net_workspace_size(op: int, nslots: int, nframes: int) -> int:
+    n = _SZ(0)
+    _check("ipfb_net_workspace_size", lib().ipfb_net_workspace_size(int(op), int(nslots), int(nframes),
+                                                                    ctypes.byref(n)))
+    return n.value
+
+
+def _net_args(theta, xin):
+    torch = _torch()
+    theta = _dev(theta, torch.float32, "theta")
+    if theta.numel() != NET_NPARAMS:
+        raise ValueError(f"theta has {theta.numel()} values, expected {NET_NPARAMS}")
+    xin = _dev(xin, torch.float32, "xin")
+    if xin.dim() != 3 or xin.shape[1] != 2:
+        raise ValueError("xin must be [nslots, 2, J]")
+    return theta, xin
+
+
+def net_forward(theta, xin, workspace=None):
+    """Net output y [nslots, J] for inputs xin [nslots, 2, J] (ipfb_net_forward)."""
+    torch = _torch()
+    theta, xin = _net_args(theta, xin)
+    ns, _, J = xin.shape
+    y = torch.empty((ns, J), dtype=torch.float32, device=xin.device)
+    ws, wsb = _workspace(net_workspace_size(NET_FORWARD, ns, J), xin.device, workspace)
+    _check("ipfb_net_forward", lib().ipfb_net_forward(_ptr(theta), ns, J, _ptr(xin), _ptr(y), _ptr(ws), wsb,
+                                                      _stream()))
+    return y
+
+
+def net_grad(theta, xin, target, workspace=None):
+    """(loss [1], grad [NET_NPARAMS]) of the mean squared error of net(xin) against
+    target [nslots, J] (ipfb_net_grad)."""
+    torch = _torch()
+    theta, xin = _net_args(theta, xin)
+    target = _dev(target, torch.float32, "target")
+    ns, _, J = xin.shape
+    if tuple(target.shape) != (ns, J):
+        raise ValueError("target must be [nslots, J]")
+    loss = torch.empty(1, dtype=torch.float32, device=xin.device)
+    grad = torch.empty(NET_NPARAMS, dtype=torch.float32, device=xin.device)
+    ws, wsb = _workspace(net_workspace_size(NET_GRAD, ns, J), xin.device, workspace)
+    _check("ipfb_net_grad", lib().ipfb_net_grad(_ptr(theta), ns, J, _ptr(xin), _ptr(target), _ptr(loss),
+                                                _ptr(grad), _ptr(ws), wsb, _stream()))
+    return loss, grad
+
+
+def net_adam(theta, m, v, grad, step: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+             eps: float = 1e-8):
+    """One Adam step in place on theta, m, v (ipfb_net_adam)."""
+    torch = _torch()
+    theta = _dev(theta, torch.float32, "theta")
+    m = _dev(m, torch.float32, "m")
+    v = _dev(v, torch.float32, "v")
+    grad = _dev(grad, torch.float32, "grad")
+    n = theta.numel()
+    if not (m.numel() == v.numel() == grad.numel() == n):
+        raise ValueError("theta, m, v, grad must have the same size")
+    _check("ipfb_net_adam", lib().ipfb_net_adam(_ptr(theta), _ptr(m), _ptr(v), _ptr(grad), n, int(step),
+                                                float(lr), float(beta1), float(beta2), float(eps), _stream()))
+
+
+def ml_training_pairs(window, noise_var: float, mask, x_star, x_k, pair_index, prior_weight: float = 1.0,
+                      workspace=None):
+    """Net training examples (xin [2 npairs, 2, J], target [2 npairs, J]) from two
+    iterates x_star, x_k [J*N] of the ML solve (ipfb_ml_training_pairs); pair_index
+    is a host sequence of column-pair indices."""
+    torch = _torch()
+    window = _dev(window, torch.float32, "window")
+    mask = _dev(mask, torch.uint8, "mask")
+    x_star = _dev(x_star, torch.float32, "x_star")
+    x_k = _dev(x_k, torch.float32, "x_k")
+    pair_index = np.ascontiguousarray(np.asarray(pair_index, dtype=np.int32))
+    p, N = window.shape
+    J = x_star.numel() // N
+    g = geom(N, p, J)
+    npairs = pair_index.size
+    xin = torch.empty((2 * npairs, 2, J), dtype=torch.float32, device=window.device)
+    target = torch.empty((2 * npairs, J), dtype=torch.float32, device=window.device)
+    prm = MLParams(float(noise_var), float(prior_weight), 0.0, 0, 0)
+    ws, wsb = _workspace(workspace_size(g, OP_ML_PAIRS), window.device, workspace)
+    _check("ipfb_ml_training_pairs", lib().ipfb_ml_training_pairs(
+        ctypes.byref(g), _ptr(window), ctypes.byref(prm), _ptr(mask), _ptr(x_star), _ptr(x_k),
+        pair_index.ctypes.data_as(ctypes.c_void_p),
+        npairs, _ptr(xin), _ptr(target), _ptr(ws), wsb, _stream()))
+    return xin, target
 
 
 class BatchedPlan:

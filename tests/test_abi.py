@@ -41,6 +41,24 @@ def test_workspace_sizes():
     assert e.value.rc == ipfb.ERR_UNSUPPORTED
 
 
+def test_learned_workspace_sizes():
+    g = ipfb.geom(4096, 4, 8192)
+    ml = ipfb.workspace_size(g, ipfb.OP_ML)
+    learned = ipfb.workspace_size(g, ipfb.OP_ML_LEARNED)
+    vec = 4096 * 8192 * 4
+    # d, five FCG vectors, net outputs (one vector) and inputs (two), plus small state
+    assert 9 * vec <= learned <= 9 * vec + (1 << 20)
+    assert ml == 2 * vec
+    assert ipfb.workspace_size(g, ipfb.OP_ML_PAIRS) == 2 * vec + 2048 * 4
+    with pytest.raises(ipfb.IpfbError):
+        ipfb.workspace_size(ipfb.geom(4096, 8, 8192), ipfb.OP_ML_LEARNED)
+    fwd = ipfb.net_workspace_size(ipfb.NET_FORWARD, 16, 8192)
+    grad = ipfb.net_workspace_size(ipfb.NET_GRAD, 16, 8192)
+    assert fwd >= 2 * 22592
+    # one partial gradient (+ loss) per 224-frame tile of every slot
+    assert grad - fwd == 16 * ((8192 + 223) // 224) * (ipfb.NET_NPARAMS + 1) * 4
+
+
 def test_library_window_matches_oracle_window():
     for N, p in ((64, 4), (256, 4), (4096, 4), (128, 3)):
         w = ipfb.sinc_hamming_window(N, p)
@@ -75,6 +93,25 @@ def test_host_validation_rejects_before_launch():
     assert L.ipfb_wiener_upchannelize(ctypes.byref(g_up), fake, fake, fake, 0.01, 1, 3, fake, None, fake,
                                       1 << 30, None) == ipfb.ERR_UNSUPPORTED
     assert ipfb.lib().ipfb_set_max_column_run(1000) == ipfb.ERR_INVALID
+    # learned-preconditioner entry points
+    assert L.ipfb_net_nparams() == ipfb.NET_NPARAMS == 10145
+    assert L.ipfb_net_forward(None, 1, 16, fake, fake, fake, 1 << 20, None) == ipfb.ERR_INVALID
+    assert L.ipfb_net_forward(fake, 0, 16, fake, fake, fake, 1 << 20, None) == ipfb.ERR_INVALID
+    assert L.ipfb_net_forward(fake, 1, 16, fake, fake, fake, 16, None) == ipfb.ERR_WORKSPACE
+    assert L.ipfb_net_grad(fake, 1, 16, fake, fake, None, None, fake, 1 << 20, None) == ipfb.ERR_INVALID
+    assert L.ipfb_net_adam(fake, fake, fake, fake, 10, 0, 1e-3, 0.9, 0.999, 1e-8, None) == ipfb.ERR_INVALID
+    assert L.ipfb_net_adam(fake, fake, fake, fake, 10, 1, 1e-3, 1.0, 0.999, 1e-8, None) == ipfb.ERR_INVALID
+    prm = ipfb.MLParams(0.1, 1.0, 1e-6, 10, 2)
+    g_ml = ipfb.geom(256, 4, 512)
+    assert L.ipfb_ml_solve(ctypes.byref(g_ml), fake, fake, fake, ctypes.byref(prm), fake, fake, None, fake, 0,
+                           fake, fake, fake, 1 << 40, None) == ipfb.ERR_INVALID      # learned needs the net
+    assert L.ipfb_ml_solve(ctypes.byref(g_ml), fake, fake, fake, ctypes.byref(prm), fake, fake, fake, fake, 0,
+                           fake, fake, fake, 16, None) == ipfb.ERR_WORKSPACE
+    assert L.ipfb_ml_training_pairs(ctypes.byref(g_ml), fake, ctypes.byref(prm), fake, fake, fake, fake, -1,
+                                    fake, fake, fake, 1 << 30, None) == ipfb.ERR_INVALID
+    bad = (ctypes.c_int * 2)(3, 128)    # pair 128 does not exist for lblock 256
+    assert L.ipfb_ml_training_pairs(ctypes.byref(g_ml), fake, ctypes.byref(prm), fake, fake, fake, bad, 2,
+                                    fake, fake, fake, 1 << 30, None) == ipfb.ERR_INVALID
     # code arrays are read with 16-byte loads: an unaligned start is refused
     odd = ctypes.c_void_p(0x1008)
     assert L.ipfb_wiener(G, odd, fake, fake, 0.01, 1, fake, fake, 1 << 30, None) == ipfb.ERR_INVALID

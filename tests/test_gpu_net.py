@@ -1,0 +1,207 @@
+"""GPU parity of the learned preconditioner (net forward, gradients, Adam, training
+pairs, flexible CG) against the FP64 oracle with BF16 emulation, through the C ABI.
+
+Tolerances: net outputs within 5e-3 and gradients within 1e-2 relative (RMS over
+each parameter group) of the oracle with the same BF16 rounding of weights and
+activations; the remaining differences are FP32 accumulation order and the rare
+BF16 rounding decision that flips between an FP32 and an FP64 pre-activation."""
+import numpy as np
+import pytest
+
+from oracle import ml as oml
+from oracle import net as onet
+from oracle import pfb as opfb
+from paper_2608_23441_b300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2608_23441_b300 import ipfb  # noqa: E402
+
+
+def cuda(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def _theta(seed, scale3=1.0, jitter=0.05):
+    rng = np.random.default_rng(seed + 100)
+    p = onet.init_params(seed, scale3=scale3)
+    for k in p:
+        p[k] = p[k] + jitter * rng.standard_normal(p[k].shape)
+    return onet.flatten(p)
+
+
+def _xin(ns, J, seed):
+    rng = np.random.default_rng(seed)
+    x = np.empty((ns, 2, J))
+    x[:, 0] = rng.standard_normal((ns, J))
+    x[:, 1] = (rng.uniform(size=(ns, J)) < 0.2)
+    return x
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("ns,J", [(3, 500), (2, 37), (1, 8192), (2, 240)])
+def test_net_forward_matches_oracle(ns, J):
+    th = _theta(1).astype(np.float32)
+    xin = _xin(ns, J, 2).astype(np.float32)
+    y = ipfb.net_forward(cuda(th), cuda(xin)).cpu().numpy().astype(np.float64)
+    ref = onet.forward(onet.unflatten(th.astype(np.float64)), xin.astype(np.float64), emulate_bf16=True)
+    assert y.shape == ref.shape
+    assert _rel(y, ref) <= 5e-3, _rel(y, ref)
+    # every position computed (ragged last tile, wrap-around halos)
+    assert np.all(np.abs(y - ref) <= 0.05 * np.abs(ref).max())
+
+
+def test_zero_output_layer_gives_bias():
+    th = _theta(3).astype(np.float32)
+    p = onet.unflatten(th.astype(np.float64))
+    p["w3"][:] = 0.0
+    p["b3"][:] = 0.25
+    th = onet.flatten(p).astype(np.float32)
+    y = ipfb.net_forward(cuda(th), cuda(_xin(2, 300, 4).astype(np.float32))).cpu().numpy()
+    assert np.all(y == np.float32(0.25))
+
+
+@pytest.mark.parametrize("ns,J", [(2, 300), (1, 100), (3, 448)])
+def test_net_grad_matches_oracle(ns, J):
+    th = _theta(5, scale3=1.0).astype(np.float32)
+    xin = _xin(ns, J, 6).astype(np.float32)
+    tgt = np.random.default_rng(7).standard_normal((ns, J)).astype(np.float32)
+    loss, grad = ipfb.net_grad(cuda(th), cuda(xin), cuda(tgt))
+    loss = float(loss.cpu().numpy()[0])
+    grad = grad.cpu().numpy().astype(np.float64)
+    L, g = onet.loss_and_grad(onet.unflatten(th.astype(np.float64)), xin.astype(np.float64),
+                              tgt.astype(np.float64), emulate_bf16=True)
+    assert abs(loss - L) <= 5e-3 * abs(L), (loss, L)
+    gu = onet.unflatten(grad)
+    for k in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        assert _rel(gu[k], g[k]) <= 1e-2, (k, _rel(gu[k], g[k]))
+
+
+def test_net_grad_is_deterministic():
+    th = cuda(_theta(8).astype(np.float32))
+    xin = cuda(_xin(4, 700, 9).astype(np.float32))
+    tgt = cuda(np.random.default_rng(10).standard_normal((4, 700)).astype(np.float32))
+    l1, g1 = ipfb.net_grad(th, xin, tgt)
+    l2, g2 = ipfb.net_grad(th, xin, tgt)
+    assert torch.equal(l1, l2) and torch.equal(g1, g2)
+
+
+def test_adam_matches_oracle():
+    rng = np.random.default_rng(11)
+    n = ipfb.NET_NPARAMS
+    th0 = rng.standard_normal(n)
+    grads = [rng.standard_normal(n) for _ in range(3)]
+    th = cuda(th0.astype(np.float32))
+    m = torch.zeros(n, dtype=torch.float32, device="cuda")
+    v = torch.zeros(n, dtype=torch.float32, device="cuda")
+    opt = onet.Adam(n, lr=1e-2)
+    ref = th0.astype(np.float32).astype(np.float64)
+    for k, gk in enumerate(grads):
+        g32 = gk.astype(np.float32)
+        ipfb.net_adam(th, m, v, cuda(g32), step=k + 1, lr=1e-2)
+        ref = opt.step(ref, g32.astype(np.float64))
+    out = th.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(out - ref)) <= 1e-5
+
+
+def _instance(N, J, seed, frac=0.1, nchunks=8):
+    x = synth.stream_config(N, J, seed)
+    w = opfb.sinc_hamming_window(N, 4).astype(np.float32).astype(np.float64)
+    codes, scale, spec = opfb.pfb_forward(x, w)
+    d = oml.polyphase_data(codes, scale, N)
+    sig2 = float(np.var(d - opfb.polyphase_sum(x, w)))
+    starts, L = synth.prior_chunks(N * J, nchunks, frac, seed)
+    mask = synth.mask_from_chunks(N * J, starts, L)
+    prior = x.astype(np.float32)
+    return x, w, codes, scale, d, sig2, mask, prior
+
+
+def test_training_pairs_match_oracle():
+    N, J = 64, 256
+    x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 21)
+    w32 = cuda(w.astype(np.float32))
+    xs, _, _ = ipfb.ml_solve(cuda(codes), cuda(scale), w32, sig2, cuda(mask), cuda(prior), precond="wiener",
+                             tol=1e-6, max_iter=500)
+    xk, _, _ = ipfb.ml_solve(cuda(codes), cuda(scale), w32, sig2, cuda(mask), cuda(prior), precond="wiener",
+                             tol=0.0, max_iter=2)
+    pairs = np.array([N // 4, 0, N // 2 - 1, 5], dtype=np.int32)
+    xin, tgt = ipfb.ml_training_pairs(w32, sig2, cuda(mask), xs, xk, pairs)
+    xin = xin.cpu().numpy().astype(np.float64)
+    tgt = tgt.cpu().numpy().astype(np.float64)
+    Xs = xs.cpu().numpy().reshape(J, N).astype(np.float64)
+    Xk = xk.cpu().numpy().reshape(J, N).astype(np.float64)
+    M = mask.reshape(J, N).astype(np.float64)
+    cols = np.stack([2 * pairs, 2 * pairs + 1], axis=1).reshape(-1)
+    E = (Xs - Xk)[:, cols]
+    A = lambda V: oml.normal_operator_fft(w[:, cols], V, sig2, M[:, cols], 1.0)  # noqa: E731
+    U = oml.wiener_precond(w[:, cols], A(E), sig2, M[:, cols], 1.0)
+    ref_in, s = onet.net_input(U, M[:, cols])
+    ref_t = ((E - U) / s).T
+    assert np.array_equal(xin[:, 1], ref_in[:, 1])
+    for c in range(len(cols)):
+        assert _rel(xin[c, 0], ref_in[c, 0]) <= 1e-4, c
+        assert np.max(np.abs(tgt[c] - ref_t[c])) <= 1e-4 * np.sqrt(np.mean((E[:, c] / s[c]) ** 2)), c
+
+
+def test_learned_with_zero_net_is_wiener_pcg():
+    N, J = 64, 256
+    x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 22)
+    p = onet.unflatten(_theta(23))
+    p["w3"][:] = 0.0
+    p["b3"][:] = 0.0
+    th = cuda(onet.flatten(p).astype(np.float32))
+    args = (cuda(codes), cuda(scale), cuda(w.astype(np.float32)), sig2, cuda(mask), cuda(prior))
+    xw, itw, rw = ipfb.ml_solve(*args, precond="wiener", tol=1e-6, max_iter=500)
+    xl, itl, rl = ipfb.ml_solve(*args, precond="learned", net=th, tol=1e-6, max_iter=500)
+    itw, itl = itw.cpu().numpy(), itl.cpu().numpy()
+    assert np.all(np.abs(itw - itl) <= 1), np.abs(itw - itl).max()
+    assert np.all(rl.cpu().numpy()[0] <= 1e-6)
+    assert _rel(xl.cpu().numpy(), xw.cpu().numpy()) <= 1e-4
+
+
+@pytest.mark.parametrize("N,J", [(64, 128), (64, 512)])
+def test_learned_fcg_matches_oracle(N, J):
+    x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 24)
+    th = _theta(25, scale3=0.2, jitter=0.01)
+    tol = 1e-6
+    xl, itl, rl = ipfb.ml_solve(cuda(codes), cuda(scale), cuda(w.astype(np.float32)), sig2, cuda(mask),
+                                cuda(prior), precond="learned", net=cuda(th.astype(np.float32)), tol=tol,
+                                max_iter=2000)
+    xl = xl.cpu().numpy().reshape(J, N).astype(np.float64)
+    itl, rl = itl.cpu().numpy(), rl.cpu().numpy()
+    M = mask.reshape(J, N).astype(np.float64)
+    P = prior.reshape(J, N).astype(np.float64)
+    A = lambda V: oml.normal_operator_fft(w, V, sig2, M, 1.0)  # noqa: E731
+    B = oml.rhs(w, d, sig2, M, P, 1.0)
+    pr = onet.unflatten(th.astype(np.float32).astype(np.float64))
+    pre = lambda R: onet.apply_precond(pr, oml.wiener_precond(w, R, sig2, M, 1.0), M, emulate_bf16=True)  # noqa
+    Xo, ito, _ = onet.fcg(A, B, np.zeros_like(B), pre, tol, 2000)
+    assert np.all(rl[0] <= tol)
+    tr = oml.true_relative_residual(d, w, sig2, M, P, 1.0, xl)
+    assert np.all(tr <= 5 * tol), tr.max()
+    assert np.all(np.abs(itl - ito) <= np.maximum(3, 0.25 * ito)), (itl, ito)
+    # the same reconstruction as the oracle's solve (both at tol)
+    xt = x.reshape(J, N)
+    e_gpu = np.linalg.norm(xl - xt) / np.linalg.norm(xt)
+    e_or = np.linalg.norm(Xo - xt) / np.linalg.norm(xt)
+    assert abs(e_gpu - e_or) <= 1e-3 * e_or
+
+
+def test_learned_requires_net_and_ntap4():
+    N, J = 64, 128
+    x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 26)
+    args = (cuda(codes), cuda(scale), cuda(w.astype(np.float32)), sig2, cuda(mask), cuda(prior))
+    with pytest.raises(ValueError):
+        ipfb.ml_solve(*args, precond="learned", net=None)
+    L = ipfb.lib()
+    g = ipfb.geom(N, 8, J)
+    n = ipfb.ctypes.c_size_t(0)
+    assert L.ipfb_workspace_size(ipfb.ctypes.byref(g), ipfb.OP_ML_LEARNED, ipfb.ctypes.byref(n)) == \
+        ipfb.ERR_UNSUPPORTED
