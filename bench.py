@@ -279,26 +279,51 @@ def ml_inputs(torch, ipfb, dev, seed=4):
     return codes, scale, w, mask, xg, sig2
 
 
-def run_ml(torch, ipfb, dev, reps=3):
+def train_learned(torch, dev, epochs=8, seeds=range(1000, 1008)):
+    """Learned-preconditioner training with the library's kernels (config-5 recipe,
+    8 seeded instances x 5 plain-CG iterates x 50 column pairs = 2000 pairs)."""
+    from paper_2608_23441_b300 import precond_train as pt
+    t0 = time.time()
+    xin, tgt, info = pt.make_training_set(torch, dev, list(seeds))
+    torch.cuda.synchronize()
+    t1 = time.time()
+    theta, hist = pt.train(torch, dev, xin, tgt, epochs=epochs)
+    torch.cuda.synchronize()
+    t2 = time.time()
+    info.update({"epochs": epochs, "batch": 16, "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
+                 "data_s": t1 - t0, "train_s": t2 - t1, "loss": "mean (g - (e - u)/s)^2",
+                 "seeds": f"{min(seeds)}-{max(seeds)}"})
+    del xin, tgt
+    return theta, info
+
+
+def run_ml(torch, ipfb, dev, reps=3, theta=None):
+    """Time to relative residual 1e-6 per column on the config-4 instance (seed 4, held
+    out from training): plain CG, Wiener-PCG and, with theta, the learned FCG."""
     codes, scale, w, mask, prior, sig2 = ml_inputs(torch, ipfb, dev)
     out = {"workload": "ML CG lblock=4096 ntap=4 nframes=8192, 10% prior in 64 chunks, tol 1e-6 per column",
            "noise_var": sig2}
     stream = torch.cuda.current_stream()
-    for name in ("none", "wiener"):
-        ws = torch.empty(ipfb.workspace_size(ipfb.geom(ML_LBLOCK, NTAP, ML_NFRAMES), ipfb.OP_ML),
-                         dtype=torch.uint8, device=dev)
-        ipfb.ml_solve(codes, scale, w, sig2, mask, prior, precond=name, tol=1e-6, max_iter=4000, workspace=ws)
+    g = ipfb.geom(ML_LBLOCK, NTAP, ML_NFRAMES)
+    names = ("none", "wiener") + (("learned",) if theta is not None else ())
+    for name in names:
+        op = ipfb.OP_ML_LEARNED if name == "learned" else ipfb.OP_ML
+        ws = torch.empty(ipfb.workspace_size(g, op), dtype=torch.uint8, device=dev)
+        kw = dict(precond=name, tol=1e-6, max_iter=4000, workspace=ws, net=theta if name == "learned" else None)
+        ipfb.ml_solve(codes, scale, w, sig2, mask, prior, **kw)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
-            x, it, res = ipfb.ml_solve(codes, scale, w, sig2, mask, prior, precond=name, tol=1e-6, max_iter=4000,
-                                       workspace=ws)
+            x, it, res = ipfb.ml_solve(codes, scale, w, sig2, mask, prior, **kw)
         e1.record(stream)
         torch.cuda.synchronize()
         err = float(torch.linalg.norm(x - prior) / torch.linalg.norm(prior))
         out[name] = {"ms": e0.elapsed_time(e1) / reps, "iters_max": int(it.max()), "iters_mean": float(it.float().mean()),
                      "resid_true_max": float(res[1].max()), "rel_error_vs_truth": err}
+        del ws
+    if theta is not None:
+        out["learned_vs_plain_time"] = out["learned"]["ms"] / out["none"]["ms"]
     return out
 
 
@@ -475,7 +500,10 @@ def run_ours(args):
         "clocks": clk.summary(),
     }
     if not args.no_ml:
-        result["ml"] = run_ml(torch, ipfb, dev)
+        theta, tinfo = (None, None) if args.no_learned else train_learned(torch, dev)
+        result["ml"] = run_ml(torch, ipfb, dev, theta=theta)
+        if tinfo is not None:
+            result["ml"]["training"] = tinfo
     if not args.no_batched:
         del xg
         torch.cuda.empty_cache()
@@ -515,6 +543,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ml", action="store_true", help="skip the ML (config-4) timing")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip training the learned preconditioner and its ML timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-streams timing")
     ap.add_argument("--profile-case", nargs=3, type=int, metavar=("LBLOCK", "NFRAMES", "REPS"),
                     help="run a smaller case of the pipeline (for ncu captures) and exit")

@@ -1,0 +1,136 @@
+"""Training of the learned conjugate-gradient preconditioner with the library's own
+kernels (the learned variant of the Sec. 4.2 solve; the paper has no learned
+component).
+
+Recipe: seeded instances of the ML workload (lblock 4096, ntap 4, 8192 spectra,
+prior fraction U[2 %, 20 %] in 64 contiguous chunks); for each, the converged
+solution x* and plain-CG iterates x_k at a few iteration counts; training pairs
+(u/s, m) -> (e - u)/s from ipfb_ml_training_pairs for column pairs drawn with a
+bias toward the ill-conditioned sub-filters around column N/2 (App. A); the mean
+squared error and its gradient from ipfb_net_grad; Adam from ipfb_net_adam.
+Every compute step runs in libipfb; torch only holds device memory.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import ipfb, synth
+
+NTAP = 4
+
+
+def init_theta(seed: int, scale3: float = 0.1) -> np.ndarray:
+    """He-style uniform initial weights (biases zero); the output layer is scaled by
+    `scale3` so that training starts close to the Wiener preconditioner (g = 0)."""
+    rng = np.random.default_rng(seed)
+
+    def u(n, fan_in):
+        b = math.sqrt(6.0 / fan_in)
+        return rng.uniform(-b, b, size=n)
+
+    parts = [u(32 * 2 * 9, 2 * 9), np.zeros(32), u(32 * 32 * 9, 32 * 9), np.zeros(32),
+             u(32 * 9, 32 * 9) * scale3, np.zeros(1)]
+    th = np.concatenate(parts).astype(np.float32)
+    assert th.size == ipfb.NET_NPARAMS
+    return th
+
+
+def noise_var(torch, ipfb_mod, codes, scale, w, x, lblock: int, nframes: int) -> float:
+    """sigma^2 of the quantization noise in the units of d: with x_r the exact inverse
+    of the codes, d - C x = C (x_r - x) in the periodic model, so sigma^2 =
+    var(sum_r w_r e[j + r]) with e = x_r - x (setup arithmetic, FP64)."""
+    xr = ipfb_mod.ipfb_wiener(codes, scale, w, 0.0)
+    e = (xr - x).reshape(nframes, lblock).double()
+    wd = w.double()
+    ce = sum(wd[r][None, :] * torch.roll(e, -r, dims=0) for r in range(w.shape[0]))
+    return float(ce.var())
+
+
+def instance(torch, dev, seed: int, fraction: float | None = None, lblock: int = 4096, nframes: int = 8192,
+             nchunks: int = 64):
+    """One seeded instance: white Gaussian stream generated on the device, forward PFB
+    with 4-bit codes (pfb_forward), prior mask of `nchunks` chunks covering `fraction`
+    of the samples (drawn U[2 %, 20 %] when None), prior values = the true stream."""
+    if fraction is None:
+        fraction = synth.prior_fraction_draw(seed)
+    T = lblock * nframes
+    x = synth.gaussian_stream_torch(T, seed, dev)
+    w = torch.from_numpy(ipfb.sinc_hamming_window(lblock, NTAP)).to(dev)
+    codes, scale, _ = ipfb.pfb_forward(x, w)
+    starts, L = synth.prior_chunks(T, nchunks, fraction, seed)
+    mask = torch.from_numpy(synth.mask_from_chunks(T, starts, L)).to(dev)
+    sig2 = noise_var(torch, ipfb, codes, scale, w, x, lblock, nframes)
+    return {"codes": codes, "scale": scale, "w": w, "mask": mask, "x": x, "sig2": sig2, "fraction": fraction}
+
+
+def draw_pairs(rng, npair_total: int, count: int, spread: float = 0.0625) -> np.ndarray:
+    """`count` distinct column-pair indices, Gaussian around pair P/2 (columns near N/2,
+    where |W_n| is smallest) with standard deviation spread * P."""
+    centre = npair_total // 2
+    out: list[int] = []
+    seen = set()
+    while len(out) < count:
+        p = int(round(rng.normal(centre, spread * npair_total))) % npair_total
+        if p not in seen:
+            seen.add(p)
+            out.append(p)
+    return np.array(out, dtype=np.int32)
+
+
+def make_training_set(torch, dev, seeds, iters=(1, 3, 8, 20, 50), pairs_per: int = 50, lblock: int = 4096,
+                      nframes: int = 8192, log=None):
+    """Training pairs from plain-CG iterates of every instance in `seeds`:
+    len(seeds) * len(iters) * pairs_per column pairs (two columns each).
+    Returns xin [S, 2, J], target [S, J] (device float32) and a summary."""
+    xs_all, ts_all = [], []
+    rng = np.random.default_rng(12345)
+    t0 = time.time()
+    for seed in seeds:
+        inst = instance(torch, dev, seed, lblock=lblock, nframes=nframes)
+        args = (inst["codes"], inst["scale"], inst["w"], inst["sig2"], inst["mask"], inst["x"])
+        x_star, _, _ = ipfb.ml_solve(*args, precond="wiener", tol=1e-6, max_iter=4000)
+        for k in iters:
+            x_k, _, _ = ipfb.ml_solve(*args, precond="none", tol=0.0, max_iter=int(k))
+            pl = draw_pairs(rng, lblock // 2, pairs_per)
+            xin, tgt = ipfb.ml_training_pairs(inst["w"], inst["sig2"], inst["mask"], x_star, x_k, pl)
+            xs_all.append(xin)
+            ts_all.append(tgt)
+        if log:
+            log(f"training instance {seed}: fraction {inst['fraction']:.3f}, {time.time() - t0:.1f} s")
+        del inst
+    xin = torch.cat(xs_all)
+    target = torch.cat(ts_all)
+    return xin, target, {"instances": len(seeds), "iterates": list(iters), "column_pairs": len(seeds) * len(iters)
+                         * pairs_per, "columns": int(xin.shape[0]), "frames": int(xin.shape[2])}
+
+
+def train(torch, dev, xin, target, epochs: int = 10, batch: int = 16, lr: float = 2e-3, seed: int = 0,
+          theta0: np.ndarray | None = None, log=None):
+    """Adam on mini-batches of `batch` consecutive training columns (batch / 2 randomly
+    drawn column pairs of one instance and iterate), the batches visited in a new
+    random order every epoch; returns (theta device tensor, per-epoch mean loss)."""
+    n = xin.shape[0]
+    theta = torch.from_numpy(init_theta(seed) if theta0 is None else theta0.astype(np.float32)).to(dev)
+    m = torch.zeros_like(theta)
+    v = torch.zeros_like(theta)
+    ws = torch.empty(ipfb.net_workspace_size(ipfb.NET_GRAD, batch, xin.shape[2]), dtype=torch.uint8, device=dev)
+    rng = np.random.default_rng(seed + 1)
+    step = 0
+    hist = []
+    nb = n // batch
+    for ep in range(epochs):
+        losses = []
+        for bi in rng.permutation(nb):
+            b0 = int(bi) * batch
+            loss, grad = ipfb.net_grad(theta, xin[b0:b0 + batch], target[b0:b0 + batch], workspace=ws)
+            step += 1
+            ipfb.net_adam(theta, m, v, grad, step, lr=lr)
+            losses.append(loss)
+        ep_loss = float(np.mean(torch.cat(losses).cpu().numpy()))
+        hist.append(ep_loss)
+        if log:
+            log(f"epoch {ep}: loss {ep_loss:.5f}")
+    return theta, hist
