@@ -205,3 +205,25 @@ def test_learned_requires_net_and_ntap4():
     n = ipfb.ctypes.c_size_t(0)
     assert L.ipfb_workspace_size(ipfb.ctypes.byref(g), ipfb.OP_ML_LEARNED, ipfb.ctypes.byref(n)) == \
         ipfb.ERR_UNSUPPORTED
+
+
+def test_learned_fullsize_config4_properties():
+    """lblock 4096, ntap 4, 8192 spectra, 10 % prior: the learned FCG (an untrained,
+    small-output net) reaches the per-column tolerance, the true residual recomputed
+    from its final x stays within 5x of it, and it reconstructs the stream as well as
+    Wiener-PCG (same system, same tolerance: errors equal within 1e-3 relative)."""
+    from paper_2608_23441_b300 import precond_train as pt
+    dev = torch.device("cuda", 0)
+    inst = pt.instance(torch, dev, 4, fraction=0.1)
+    args = (inst["codes"], inst["scale"], inst["w"], inst["sig2"], inst["mask"], inst["x"])
+    th = cuda(_theta(31, scale3=0.1, jitter=0.0).astype(np.float32))
+    xl, itl, rl = ipfb.ml_solve(*args, precond="learned", net=th, tol=1e-6, max_iter=4000)
+    xw, itw, rw = ipfb.ml_solve(*args, precond="wiener", tol=1e-6, max_iter=4000)
+    rl = rl.cpu().numpy()
+    assert np.all(rl[0] <= 1e-6)
+    assert np.all(rl[1] <= 5e-6), rl[1].max()
+    x = inst["x"]
+    el = float(torch.linalg.norm(xl - x) / torch.linalg.norm(x))
+    ew = float(torch.linalg.norm(xw - x) / torch.linalg.norm(x))
+    assert abs(el - ew) <= 1e-3 * ew, (el, ew)
+    assert int(itl.max()) < 4000
