@@ -43,6 +43,8 @@ KERNEL_FILES = {
     "k2_unpack_irfft": ["ipfb_kernels.cuh", "common.cuh", "k2_unpack.cu"],
     "k3_column_wiener": ["ipfb_kernels.cuh", "common.cuh", "k3_launch.cuh", "k3_cl_nt4.cu"],
     "k4_upchan": ["upchan_kernels.cuh", "common.cuh", "k4_upchan.cu"],
+    "k4a_upchan_frames": ["upchan2_kernels.cuh", "common.cuh", "k4ab_upchan.cu"],
+    "k4b_upchan_pairs": ["upchan2_kernels.cuh", "common.cuh", "k4ab_upchan.cu"],
     "k1_pfb_power": ["pfb_kernels.cuh", "common.cuh", "k1_forward.cu"],
     "k1_pfb_quant": ["pfb_kernels.cuh", "common.cuh", "k1_forward.cu"],
 }
@@ -463,6 +465,10 @@ def run_ours(args):
         "k2_unpack_irfft": T * 0.5 + T * 4.0,
         "k3_column_wiener": T * 8.0,
         "k4_upchan": T * 4.0 + nb * (L // 2 + 1) * 8.0,
+        # the two-pass up-channelizer: each pass reads and writes the whole block set
+        # once (scratch in, scratch out in place; scratch in, spectra out)
+        "k4a_upchan_frames": T * 8.0,
+        "k4b_upchan_pairs": T * 4.0 + nb * (L // 2 + 1) * 8.0,
     }
     per_kernel = {}
     for k, (tot, cnt) in stages.items():

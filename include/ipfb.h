@@ -177,7 +177,8 @@ int upchannelize(const float* x, int64_t nsamples, int64_t block, float* out, vo
  * ipfb_wiener followed by upchannelize with block = upfactor * lblock, without
  * a round trip of the reconstructed stream through time order.  x_out (time
  * order) is optional (NULL = not written).  out: float2 [J/upfactor][L/2 + 1].
- * Workspace: ipfb_workspace_size(g, IPFB_OP_WIENER_UPCHAN).
+ * Workspace: ipfb_workspace_size(g, IPFB_OP_WIENER_UPCHAN) (2 J N floats: the
+ * column-pair scratch and the up-channelizer's intermediate).
  */
 int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const float* scale,
                              const float* window, double noise_level, int normalize,

@@ -245,7 +245,8 @@ int ipfb_workspace_size(const ipfb_geom* g, int op, size_t* bytes) {
     case IPFB_OP_WIENER_UPCHAN:
       rc = check_geom(g, true);
       if (rc) return rc;
-      *bytes = (size_t)g->nframes * (size_t)g->lblock * sizeof(float);
+      // the up-channelizer's two passes keep their intermediate in a second buffer
+      *bytes = (size_t)g->nframes * (size_t)g->lblock * sizeof(float) * (op == IPFB_OP_WIENER_UPCHAN ? 2 : 1);
       return IPFB_OK;
     case IPFB_OP_ML:
       rc = check_geom(g, true);
@@ -379,6 +380,20 @@ int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const flo
   if (rc) return rc;
   const long long nb = (long long)g->nframes / upfactor;
   if (nb == 0) return IPFB_OK;
+  if (upchan2_supported(g->lblock, C, upfactor)) {
+    // two passes: frames DFT + pa DFT into the second half of the workspace, then
+    // the pb DFTs with the real-input split and contiguous stores
+    float2* W = d2 + (size_t)g->nframes * (size_t)(g->lblock / 2);
+    {
+      Stage ta("k4a_upchan_frames", st);
+      CK(launch_k4a(d2, g->lblock, C, S, nb, W, x_out, st), "k4a_upchan_frames");
+      ta.done();
+    }
+    Stage tb("k4b_upchan_pairs", st);
+    CK(launch_k4b(W, g->lblock, nb, reinterpret_cast<float2*>(out), st), "k4b_upchan_pairs");
+    tb.done();
+    return IPFB_OK;
+  }
   UpchanSrc src{nullptr, d2, g->lblock, C, S};
   Stage t("k4_upchan", st);
   CK(launch_upchan(src, (int)L, nb, reinterpret_cast<float2*>(out), x_out, st), "k4_upchan");

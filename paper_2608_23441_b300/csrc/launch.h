@@ -55,6 +55,12 @@ cudaError_t launch_k5(int J, const float2* d2, float2* x2, const uint8_t* mask, 
 cudaError_t launch_time_to_pairs(const float* x, float2* x2, int N, int J, cudaStream_t st);
 cudaError_t launch_upchan(const UpchanSrc& src, int L, long long nblocks, float2* out, float* x_out,
                           cudaStream_t st);
+// Two-pass up-channelizer of the column-pair scratch (k4a: d2 -> W, then k4b: W ->
+// spectra), upfactor 64, lblock 1024/2048/4096; W holds nblocks * 32 N complex values.
+bool upchan2_supported(int N, int C, int U);
+cudaError_t launch_k4a(const float2* d2, int N, int C, int S, long long nblocks, float2* W, float* x_out,
+                       cudaStream_t st);
+cudaError_t launch_k4b(const float2* W, int N, long long nblocks, float2* out, cudaStream_t st);
 
 // ---- learned preconditioner: flexible CG state and the net
 struct FcgCol;

@@ -1,0 +1,270 @@
+// Up-channelization of the column-pair scratch in two passes through HBM (Sec. 4.3:
+// re-channelize the reconstructed stream with frames L = 64 N samples long; here a
+// plain real DFT of consecutive blocks).
+//
+// One block of L = 2Q real samples is Q complex values z[u] = x[2u] + i x[2u+1],
+// u = j P + p: 64 frames j of P = N/2 column pairs p.  The Q-point DFT factors as
+// 64 (frames) x PA x PB with p = PB pa + pb (PB = 64, PA = P / 64) and output index
+//   k = k1 + 64 k2,   k2 = k2a + PA k2b:
+//   Z[k] = sum_pb w_PB^(pb k2b) [ w_P^(pb k2a) sum_pa w_PA^(pa k2a)
+//                                   [ w_Q^(p k1) sum_j w_64^(j k1) z[j P + p] ] ]
+// (w_n = exp(-2 pi i / n)), then the real-input post-processing
+//   X[k] = E + exp(-2 pi i k / L) O,  E = (Z[k] + conj Z[Q-k]) / 2,
+//   O = -i (Z[k] - conj Z[Q-k]) / 2,  X[Q] = Re Z[0] - Im Z[0].
+//
+// k4a: per tile (block b, NPB = 128 / PA consecutive pb, all pa: 128 pairs) the
+//   64-point frames DFT, the w_Q twiddle, the PA-point DFT over pa and the w_P
+//   twiddle; writes W[b][k2a][k1][pb] (NPB-element runs).
+// k4b: per CTA (block b, a < PA/2) the 64-point DFTs over pb of the 128 rows
+//   (k2a, k1) with k2a in {a, PA-1-a} (both contiguous 32 KB slabs of W), which
+//   holds the partner Z[Q-k] of every output it writes (k1 != 0: row (PA-1-k2a,
+//   64-k1)); for k1 = 0 the partner rows k2a' = PA - k2a are loaded as two extra
+//   rows.  Outputs for fixed (k2a, k2b) are the 64 consecutive k1: contiguous runs.
+// Both are ordinary kernels (no clusters); the cross-CTA exchange of a one-pass
+// design is replaced by one round trip of the block set through HBM.
+#pragma once
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace ipfb {
+
+constexpr int kK4aThreads = 256;
+constexpr int kK4bThreads = 256;
+
+template <int P>
+struct K4Shape {
+  static constexpr int PB = 64;
+  static constexpr int PA = P / PB;
+  static constexpr int NPB = 128 / PA;  // pb per k4a tile (128 pairs per tile)
+  static constexpr int Q = 64 * P;
+  static_assert(PA >= 2 && PA <= 128 && NPB >= 1, "P in [128, 8192]");
+};
+
+// ---------------------------------------------------------------------------
+// k4a.  Shared array [64 rows][128 columns] (no padding), column swizzled per row:
+// rows hold the frames-DFT state (row = 8 k1a + rt, then 8 k1a + k1b: each thread
+// reads and writes the same 8 slots), column = local pair q = pa NPB + pbl.  The
+// XOR swizzle puts the PA-point reads of k4a's last stage (lanes = pbl fastest,
+// then k1) into distinct banks.
+// ---------------------------------------------------------------------------
+template <int NPB>
+__device__ __forceinline__ int k4a_slot(int row, int q) {
+  constexpr int KM = 16 / NPB > 1 ? 16 / NPB - 1 : 0;
+  return row * 128 + (q ^ (((row >> 3) & KM) * NPB));
+}
+
+template <int P>
+__global__ void __launch_bounds__(kK4aThreads)
+k4a_frames(const float2* __restrict__ d2, int C, int S, long long nblocks, float2* __restrict__ W,
+           float2* __restrict__ x2_out) {
+  using K = K4Shape<P>;
+  constexpr int T = kK4aThreads;
+  constexpr int Q = K::Q, PA = K::PA, NPB = K::NPB;
+  extern __shared__ float2 smk4a[];
+  float2* buf = smk4a;                // 8192
+  float2* tw_hi = buf + 64 * 128;     // Q >> 9
+  float2* tw_lo = tw_hi + (Q >> 9);   // 512
+  const int tid = threadIdx.x;
+  twid2_fill<9, false>(tw_hi, tw_lo, Q, tid, T);
+  __syncthreads();
+  const Twid2<9> tw{tw_hi, tw_lo};
+  const long long ntiles = nblocks * (K::PB / NPB);
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long b = tile % nblocks;
+    const int pb0 = (int)(tile / nblocks) * NPB;
+    // ---- (a) load 8 frames t = 8 m' + rt of one pair, DFT over m', twiddle w_64^(rt k1a)
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int q = tid & 127, rt = (tid >> 7) + 2 * it;
+      const int p = K::PB * (q / NPB) + pb0 + (q % NPB);
+      float2 v[8];
+      if (C == 8) {
+        const float4* src = reinterpret_cast<const float4*>(d2 + ((long long)p * 8 + rt) * S + b * 8);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const float4 u = src[h];
+          v[2 * h] = make_float2(u.x, u.y);
+          v[2 * h + 1] = make_float2(u.z, u.w);
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const long long j = b * 64 + 8 * m + rt;
+          v[m] = d2[((long long)p * C + (int)(j % C)) * S + j / C];
+        }
+      }
+      if (x2_out) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) x2_out[(b * 64 + 8 * m + rt) * P + p] = v[m];
+      }
+      DFT<8, false>::run(v);
+      if (rt) apply_twiddles<8>(v, tw(rt * P));  // w_64^rt = w_Q^(rt P)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) buf[k4a_slot<NPB>(8 * k + rt, q)] = v[k];
+    }
+    __syncthreads();
+    // ---- (b) DFT over rt (k1 = k1a + 8 k1b), twiddle w_Q^(p k1); same 8 slots
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int q = tid & 127, k1a = (tid >> 7) + 2 * it;
+      const int p = K::PB * (q / NPB) + pb0 + (q % NPB);
+      float2 v[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[r] = buf[k4a_slot<NPB>(8 * k1a + r, q)];
+      DFT<8, false>::run(v);
+      const float2 base = tw(p * k1a), step = tw(p * 8);
+      v[0] = cmul(v[0], base);
+      float2 w = base;
+#pragma unroll
+      for (int k = 1; k < 8; ++k) {
+        w = cmul(w, step);
+        v[k] = cmul(v[k], w);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) buf[k4a_slot<NPB>(8 * k1a + k, q)] = v[k];
+    }
+    __syncthreads();
+    // ---- (c) PA-point DFT over pa for each (k1, pbl), twiddle w_P^(pb k2a), store W
+    constexpr int NIT = (64 * NPB + T - 1) / T;
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+      const int item = tid + it * T;
+      if (item < 64 * NPB) {
+        const int pbl = item % NPB, k1 = item / NPB;
+        const int row = 8 * (k1 & 7) + (k1 >> 3);
+        float2 v[PA];
+#pragma unroll
+        for (int pa = 0; pa < PA; ++pa) v[pa] = buf[k4a_slot<NPB>(row, pa * NPB + pbl)];
+        DFT<PA, false>::run(v);
+        const int pb = pb0 + pbl;
+        apply_twiddles<PA>(v, tw(64 * pb));  // w_P^pb = w_Q^(64 pb)
+        float2* wb = W + ((b * PA) * 64 + k1) * 64 + pb;
+#pragma unroll
+        for (int k2a = 0; k2a < PA; ++k2a) wb[(long long)k2a * 64 * 64] = v[k2a];
+      }
+    }
+    __syncthreads();  // buf is reused by the next tile
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k4b.  Rows rho (stride RS = 65, odd, so that consecutive rows at one column hit
+// distinct banks in the post-processing): 0..63 = (a, k1), 64..127 = (PA-1-a, k1), 128 = (PA-a mod PA,
+// 0), 129 = (a+1 mod PA, 0).  Tables: w_128^n (the 64-point FFT twiddles and the
+// k2b part of exp(-2 pi i k / L)) and w_L^(k1 + 64 k2a) per row.
+// ---------------------------------------------------------------------------
+constexpr int kK4bRS = 65;
+constexpr int kK4bRows = 130;
+
+template <int P>
+constexpr size_t k4b_smem_bytes() {
+  return (size_t)(kK4bRows * kK4bRS + 128 + kK4bRows) * sizeof(float2);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kK4bThreads)
+k4b_pairs(const float2* __restrict__ W, float2* __restrict__ out) {
+  using K = K4Shape<P>;
+  constexpr int T = kK4bThreads;
+  constexpr int Q = K::Q, PA = K::PA, L = 2 * Q;
+  constexpr int RS = kK4bRS;
+  extern __shared__ float2 smk4b[];
+  float2* rows = smk4b;
+  float2* t128 = rows + kK4bRows * RS;
+  float2* rb = t128 + 128;
+  const int tid = threadIdx.x;
+  const long long b = blockIdx.x / (PA / 2);
+  const int a = blockIdx.x % (PA / 2);
+  const int ka[4] = {a, PA - 1 - a, (PA - a) % PA, (a + 1) % PA};
+  for (int i = tid; i < 128; i += T) t128[i] = twiddle<false>(i, 128);
+  for (int i = tid; i < kK4bRows; i += T) {
+    const int k1 = i < 128 ? (i & 63) : 0;
+    const int k2a = ka[i < 128 ? (i >> 6) : (i - 126)];
+    rb[i] = twiddle<false>(k1 + 64 * k2a, L);
+  }
+  // ---- load: two 4096-element slabs (rows 0..127) and two 64-element rows
+  {
+    constexpr int NV = 2 * 2048 + 2 * 32;  // float4 (two elements each)
+#pragma unroll 4
+    for (int f = tid; f < NV; f += T) {
+      int rho, pb, k2a, k1;
+      if (f < 4096) {
+        const int s = f >> 11, e = f & 2047;
+        k1 = e >> 5;
+        pb = (e & 31) * 2;
+        rho = s * 64 + k1;
+        k2a = ka[s];
+      } else {
+        const int x = (f - 4096) >> 5;
+        k1 = 0;
+        pb = ((f - 4096) & 31) * 2;
+        rho = 128 + x;
+        k2a = ka[2 + x];
+      }
+      const float4 u = *reinterpret_cast<const float4*>(W + ((b * PA + k2a) * 64 + k1) * 64 + pb);
+      rows[rho * RS + pb] = make_float2(u.x, u.y);
+      rows[rho * RS + pb + 1] = make_float2(u.z, u.w);
+    }
+  }
+  __syncthreads();
+  // ---- 64-point forward DFT of every row: two radix-8 Stockham passes, 8 lanes per
+  // row (4 rows per warp), synchronised within the warp only
+  {
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int rg = warp; rg < (kK4bRows + 3) / 4; rg += T / 32) {
+      const int rho = rg * 4 + (lane >> 3), bf = lane & 7;
+      const bool ok = rho < kK4bRows;
+      float2* row = rows + (ok ? rho : 0) * RS;
+      float2 v[8];
+      if (ok) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = row[bf + 8 * r];
+        DFT<8, false>::run(v);
+      }
+      __syncwarp();
+      if (ok) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) row[8 * bf + r] = v[r];  // Ns = 1: output 8 bf + r
+      }
+      __syncwarp();
+      if (ok) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = row[bf + 8 * r];
+        if (bf) apply_twiddles<8>(v, t128[2 * bf]);  // w_64^bf
+        DFT<8, false>::run(v);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) row[bf + 8 * r] = v[r];  // Ns = 8: output bf + 8 r
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // ---- post-processing and contiguous stores: w = (half, k2b, k1), k1 fastest
+  float2* ob = out + b * (long long)(Q + 1);
+#pragma unroll 4
+  for (int w = tid; w < 2 * 64 * 64; w += T) {
+    const int k1 = w & 63, k2b = (w >> 6) & 63, hf = w >> 12;
+    const int rho = hf * 64 + k1;
+    const int k2a = ka[hf];
+    int rp, k2bp;
+    if (k1 != 0) {
+      rp = (1 - hf) * 64 + (64 - k1);
+      k2bp = 63 - k2b;
+    } else {
+      const int kp = (PA - k2a) % PA;
+      k2bp = k2a == 0 ? ((64 - k2b) & 63) : 63 - k2b;
+      rp = kp == ka[0] ? 0 : (kp == ka[1] ? 64 : (kp == ka[2] ? 128 : 129));
+    }
+    const float2 zk = rows[rho * RS + k2b];
+    const float2 zm = rows[rp * RS + k2bp];
+    const float2 E = cscale(cadd(zk, cconj(zm)), 0.5f);
+    const float2 dd = csub(zk, cconj(zm));
+    const float2 O = make_float2(0.5f * dd.y, -0.5f * dd.x);
+    const long long k = k1 + 64 * k2a + 64LL * PA * k2b;
+    ob[k] = cadd(E, cmul(cmul(rb[rho], t128[k2b]), O));
+    if (k == 0) ob[Q] = make_float2(zk.x - zk.y, 0.0f);
+  }
+}
+
+}  // namespace ipfb

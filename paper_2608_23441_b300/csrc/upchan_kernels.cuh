@@ -235,7 +235,13 @@ k4_upchan(UpchanSrc src, float2* __restrict__ out, float* __restrict__ x_out) {
     ob[k] = cadd(E, cmul(wk, O));
     if (k == 0) ob[Q] = make_float2(zk.x - zk.y, 0.0f);
   }
-  if constexpr (CU > 1) cg::this_cluster().sync();  // peers may still read this CTA's smem
+  // Peers may still read this CTA's shared memory: wait for them before exiting.  The
+  // arrive is relaxed (no release fence): nothing written here is read after the
+  // barrier, and a release would hold every thread until its output stores drain.
+  if constexpr (CU > 1) {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
+  }
 }
 
 }  // namespace ipfb

@@ -28,7 +28,7 @@ def test_strerror_codes():
 def test_workspace_sizes():
     g = ipfb.geom(4096, 4, 65536)
     assert ipfb.workspace_size(g, ipfb.OP_WIENER) == 65536 * 4096 * 4
-    assert ipfb.workspace_size(g, ipfb.OP_WIENER_UPCHAN) == 65536 * 4096 * 4
+    assert ipfb.workspace_size(g, ipfb.OP_WIENER_UPCHAN) == 2 * 65536 * 4096 * 4
     assert ipfb.workspace_size(g, ipfb.OP_FORWARD) == 2 * 2049 * 8
     with pytest.raises(ipfb.IpfbError) as e:
         ipfb.workspace_size(ipfb.geom(4096, 4, 65537), ipfb.OP_WIENER)
