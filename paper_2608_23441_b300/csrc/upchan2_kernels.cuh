@@ -73,27 +73,34 @@ k4a_frames(const float2* __restrict__ d2, int C, int S, long long nblocks, float
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long b = tile % nblocks;
     const int pb0 = (int)(tile / nblocks) * NPB;
-    // ---- (a) load 8 frames t = 8 m' + rt of one pair, DFT over m', twiddle w_64^(rt k1a)
+    // ---- (a) load 8 frames t = 8 m' + rt of one pair (all of a thread's loads in
+    // flight together), DFT over m', twiddle w_64^(rt k1a)
+    float2 v4[4][8];
 #pragma unroll
     for (int it = 0; it < 4; ++it) {
       const int q = tid & 127, rt = (tid >> 7) + 2 * it;
       const int p = K::PB * (q / NPB) + pb0 + (q % NPB);
-      float2 v[8];
       if (C == 8) {
         const float4* src = reinterpret_cast<const float4*>(d2 + ((long long)p * 8 + rt) * S + b * 8);
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
           const float4 u = src[h];
-          v[2 * h] = make_float2(u.x, u.y);
-          v[2 * h + 1] = make_float2(u.z, u.w);
+          v4[it][2 * h] = make_float2(u.x, u.y);
+          v4[it][2 * h + 1] = make_float2(u.z, u.w);
         }
       } else {
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
           const long long j = b * 64 + 8 * m + rt;
-          v[m] = d2[((long long)p * C + (int)(j % C)) * S + j / C];
+          v4[it][m] = d2[((long long)p * C + (int)(j % C)) * S + j / C];
         }
       }
+    }
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int q = tid & 127, rt = (tid >> 7) + 2 * it;
+      const int p = K::PB * (q / NPB) + pb0 + (q % NPB);
+      float2* v = v4[it];
       if (x2_out) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) x2_out[(b * 64 + 8 * m + rt) * P + p] = v[m];
@@ -156,6 +163,9 @@ k4a_frames(const float2* __restrict__ d2, int C, int S, long long nblocks, float
 // ---------------------------------------------------------------------------
 constexpr int kK4bRS = 65;
 constexpr int kK4bRows = 130;
+// column swizzle inside a row: the radix-8 passes access columns 8 bf + r and bf + 8 r
+// (lanes bf); c ^ ((c >> 3) & 7) maps both onto distinct banks
+__device__ __forceinline__ int k4b_col(int c) { return c ^ ((c >> 3) & 7); }
 
 template <int P>
 constexpr size_t k4b_smem_bytes() {
@@ -176,35 +186,53 @@ k4b_pairs(const float2* __restrict__ W, float2* __restrict__ out) {
   const int tid = threadIdx.x;
   const long long b = blockIdx.x / (PA / 2);
   const int a = blockIdx.x % (PA / 2);
-  const int ka[4] = {a, PA - 1 - a, (PA - a) % PA, (a + 1) % PA};
+  // k2a of the four row groups: a, PA-1-a, and the k1 = 0 partners PA-a, a+1 (mod PA)
+  auto ka = [a](int i) { return i == 0 ? a : (i == 1 ? PA - 1 - a : (i == 2 ? (PA - a) % PA : (a + 1) % PA)); };
   for (int i = tid; i < 128; i += T) t128[i] = twiddle<false>(i, 128);
   for (int i = tid; i < kK4bRows; i += T) {
     const int k1 = i < 128 ? (i & 63) : 0;
-    const int k2a = ka[i < 128 ? (i >> 6) : (i - 126)];
+    const int k2a = ka(i < 128 ? (i >> 6) : (i - 126));
     rb[i] = twiddle<false>(k1 + 64 * k2a, L);
   }
-  // ---- load: two 4096-element slabs (rows 0..127) and two 64-element rows
+  // ---- load: two 4096-element slabs (rows 0..127) and two 64-element rows, eight
+  // 16-byte loads in flight per thread
   {
     constexpr int NV = 2 * 2048 + 2 * 32;  // float4 (two elements each)
-#pragma unroll 4
-    for (int f = tid; f < NV; f += T) {
-      int rho, pb, k2a, k1;
+    auto src_of = [&](int f, int& rho, int& pb) -> const float4* {
+      int k2a, k1;
       if (f < 4096) {
         const int s = f >> 11, e = f & 2047;
         k1 = e >> 5;
         pb = (e & 31) * 2;
         rho = s * 64 + k1;
-        k2a = ka[s];
+        k2a = ka(s);
       } else {
         const int x = (f - 4096) >> 5;
         k1 = 0;
         pb = ((f - 4096) & 31) * 2;
         rho = 128 + x;
-        k2a = ka[2 + x];
+        k2a = ka(2 + x);
       }
-      const float4 u = *reinterpret_cast<const float4*>(W + ((b * PA + k2a) * 64 + k1) * 64 + pb);
-      rows[rho * RS + pb] = make_float2(u.x, u.y);
-      rows[rho * RS + pb + 1] = make_float2(u.z, u.w);
+      return reinterpret_cast<const float4*>(W + ((b * PA + k2a) * 64 + k1) * 64 + pb);
+    };
+    for (int f0 = tid; f0 < NV; f0 += 8 * T) {
+      float4 u[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int f = f0 + i * T;
+        int rho, pb;
+        if (f < NV) u[i] = *src_of(f, rho, pb);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int f = f0 + i * T;
+        int rho, pb;
+        if (f < NV) {
+          (void)src_of(f, rho, pb);
+          rows[rho * RS + k4b_col(pb)] = make_float2(u[i].x, u[i].y);
+          rows[rho * RS + k4b_col(pb + 1)] = make_float2(u[i].z, u[i].w);
+        }
+      }
     }
   }
   __syncthreads();
@@ -219,22 +247,22 @@ k4b_pairs(const float2* __restrict__ W, float2* __restrict__ out) {
       float2 v[8];
       if (ok) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) v[r] = row[bf + 8 * r];
+        for (int r = 0; r < 8; ++r) v[r] = row[k4b_col(bf + 8 * r)];
         DFT<8, false>::run(v);
       }
       __syncwarp();
       if (ok) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) row[8 * bf + r] = v[r];  // Ns = 1: output 8 bf + r
+        for (int r = 0; r < 8; ++r) row[k4b_col(8 * bf + r)] = v[r];  // Ns = 1: output 8 bf + r
       }
       __syncwarp();
       if (ok) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) v[r] = row[bf + 8 * r];
+        for (int r = 0; r < 8; ++r) v[r] = row[k4b_col(bf + 8 * r)];
         if (bf) apply_twiddles<8>(v, t128[2 * bf]);  // w_64^bf
         DFT<8, false>::run(v);
 #pragma unroll
-        for (int r = 0; r < 8; ++r) row[bf + 8 * r] = v[r];  // Ns = 8: output bf + 8 r
+        for (int r = 0; r < 8; ++r) row[k4b_col(bf + 8 * r)] = v[r];  // Ns = 8: output bf + 8 r
       }
       __syncwarp();
     }
@@ -246,7 +274,7 @@ k4b_pairs(const float2* __restrict__ W, float2* __restrict__ out) {
   for (int w = tid; w < 2 * 64 * 64; w += T) {
     const int k1 = w & 63, k2b = (w >> 6) & 63, hf = w >> 12;
     const int rho = hf * 64 + k1;
-    const int k2a = ka[hf];
+    const int k2a = ka(hf);
     int rp, k2bp;
     if (k1 != 0) {
       rp = (1 - hf) * 64 + (64 - k1);
@@ -254,10 +282,10 @@ k4b_pairs(const float2* __restrict__ W, float2* __restrict__ out) {
     } else {
       const int kp = (PA - k2a) % PA;
       k2bp = k2a == 0 ? ((64 - k2b) & 63) : 63 - k2b;
-      rp = kp == ka[0] ? 0 : (kp == ka[1] ? 64 : (kp == ka[2] ? 128 : 129));
+      rp = kp == ka(0) ? 0 : (kp == ka(1) ? 64 : (kp == ka(2) ? 128 : 129));
     }
-    const float2 zk = rows[rho * RS + k2b];
-    const float2 zm = rows[rp * RS + k2bp];
+    const float2 zk = rows[rho * RS + k4b_col(k2b)];
+    const float2 zm = rows[rp * RS + k4b_col(k2bp)];
     const float2 E = cscale(cadd(zk, cconj(zm)), 0.5f);
     const float2 dd = csub(zk, cconj(zm));
     const float2 O = make_float2(0.5f * dd.y, -0.5f * dd.x);
