@@ -80,16 +80,51 @@ def ncu_traffic(name: str):
 
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
+    """SM clock and clock-event reasons during the timed region: NVML polled every
+    5 ms from a background thread (read-only queries), with an nvidia-smi -lms 200
+    sampler beside it as a fallback for when NVML is not importable."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASON_BITS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+                   "sw_power_cap": 0x4, "hw_power_brake_slowdown": 0x80}
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, pci_bus_id: str | None = None):
         self.idx = gpu_index
+        self.pci = pci_bus_id
         self.proc = None
         self.path = os.path.join("/tmp", f"ipfb_clocks_{os.getpid()}.csv")
+        self.nv = []          # (sm_mhz, max_mhz, reasons bitmask)
+        self._stop = None
+        self._thr = None
+
+    def _nvml_loop(self):
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            h = None
+            if self.pci:
+                try:
+                    h = pynvml.nvmlDeviceGetHandleByPciBusId(self.pci)
+                except Exception:
+                    h = None
+            if h is None:
+                h = pynvml.nvmlDeviceGetHandleByIndex(self.idx)
+            mx = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
+            while not self._stop.is_set():
+                sm = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
+                rs = pynvml.nvmlDeviceGetCurrentClocksEventReasons(h)
+                self.nv.append((sm, mx, rs))
+                self._stop.wait(0.005)
+            pynvml.nvmlShutdown()
+        except Exception:
+            pass
 
     def __enter__(self):
+        import threading
+        self._stop = threading.Event()
+        self._thr = threading.Thread(target=self._nvml_loop, daemon=True)
+        self._thr.start()
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
@@ -100,6 +135,9 @@ class ClockSampler:
         return self
 
     def __exit__(self, *a):
+        if self._stop is not None:
+            self._stop.set()
+            self._thr.join(timeout=5)
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -109,6 +147,11 @@ class ClockSampler:
             self.fh.close()
 
     def summary(self):
+        if self.nv:
+            sm = [x[0] for x in self.nv]
+            reasons = sorted({nm for _, _, rs in self.nv for nm, bit in self.REASON_BITS.items() if rs & bit})
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(x[1] for x in self.nv), "reasons": reasons,
+                    "samples": len(sm), "source": "nvml, 5 ms"}
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         sm, smax, reasons = [], [], set()
@@ -128,7 +171,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi, 200 ms"}
 
 
 # --------------------------------------------------------------------------- distributed
@@ -407,12 +450,15 @@ def run_ours(args):
     # ---- device-timed region (inputs resident; every buffer > L2, so no flush needed)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ipfb.stage_timing(True)
-    with ClockSampler(local) as clk:
+    props = torch.cuda.get_device_properties(dev)
+    pci = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+    with ClockSampler(local, pci) as clk:
         barrier(dist, torch)
         e0.record(stream)
         for _ in range(args.steps):
             step()
         e1.record(stream)
+        torch.cuda.synchronize()   # the sampler runs until the timed work has finished
         barrier(dist, torch)
     ms = e0.elapsed_time(e1) / args.steps
     stages = ipfb.stage_times()
@@ -420,25 +466,53 @@ def run_ours(args):
     ms_max = max_over_ranks(dist, torch, ms)
     launches = sum(c for _, c in stages.values())
 
-    # ---- end to end through host buffers (pinned), copies inside the timed region
+    # ---- end to end through host buffers (pinned), copies inside the timed region.
+    # A streaming pipeline over steps: step i's codes go up on one stream, its
+    # inverse + up-channelization runs on a second, its spectra come back on a third,
+    # so step i's read-back overlaps step i+1's upload and compute.  Two device slots
+    # for codes and spectra; every step copies its own inputs in and its own result out.
     h_codes = torch.empty(codes.shape, dtype=codes.dtype, pin_memory=True)
     h_codes.copy_(codes)
     h_out = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
-    d_codes = torch.empty_like(codes)
-    for _ in range(2):
-        d_codes.copy_(h_codes, non_blocking=True)
-        ipfb.ipfb_wiener_upchannelize(d_codes, scale, w, phi2, UPFACTOR, out=out, workspace=wsp)
-        h_out.copy_(out, non_blocking=True)
+    d_codes = [torch.empty_like(codes) for _ in range(2)]
+    d_out = [out, torch.empty_like(out)]
+    s_up, s_cmp, s_down = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev_up = [torch.cuda.Event() for _ in range(2)]
+    ev_cmp = [torch.cuda.Event() for _ in range(2)]
+    ev_down = [torch.cuda.Event() for _ in range(2)]
+
+    def e2e_steps(n):
+        for i in range(n):
+            k = i % 2
+            with torch.cuda.stream(s_up):
+                if i >= 2:
+                    s_up.wait_event(ev_cmp[k])          # slot k's codes consumed
+                d_codes[k].copy_(h_codes, non_blocking=True)
+                ev_up[k].record(s_up)
+            with torch.cuda.stream(s_cmp):
+                s_cmp.wait_event(ev_up[k])
+                if i >= 2:
+                    s_cmp.wait_event(ev_down[k])        # slot k's spectra read back
+                ipfb.ipfb_wiener_upchannelize(d_codes[k], scale, w, phi2, UPFACTOR, out=d_out[k], workspace=wsp)
+                ev_cmp[k].record(s_cmp)
+            with torch.cuda.stream(s_down):
+                s_down.wait_event(ev_cmp[k])
+                h_out.copy_(d_out[k], non_blocking=True)
+                ev_down[k].record(s_down)
+
+    torch.cuda.synchronize()
+    e2e_steps(2)
     torch.cuda.synchronize()
     barrier(dist, torch)
-    e0.record(stream)
-    for _ in range(args.steps):
-        d_codes.copy_(h_codes, non_blocking=True)
-        ipfb.ipfb_wiener_upchannelize(d_codes, scale, w, phi2, UPFACTOR, out=out, workspace=wsp)
-        h_out.copy_(out, non_blocking=True)
-    e1.record(stream)
+    e0.record(s_up)
+    e2e_steps(args.steps)
+    s_down.wait_stream(s_up)
+    s_down.wait_stream(s_cmp)
+    e1.record(s_down)
+    torch.cuda.synchronize()
     barrier(dist, torch)
     ms_e2e = max_over_ranks(dist, torch, e0.elapsed_time(e1) / args.steps)
+    del d_out[1]
 
     # ---- forward PFB (the simulation step), reported as a stage
     fcodes = torch.empty_like(codes)
@@ -497,7 +571,9 @@ def run_ours(args):
         "pipeline_alg_fraction": {"bytes_per_step": pipe_bytes,
                                   "frac": pipe_bytes / (ms * 1e-3) / 1e9 / peak},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(codes.numel()),
-                "d2h_bytes_per_step": int(out.numel() * 8), "ms_per_step": ms_e2e},
+                "d2h_bytes_per_step": int(out.numel() * 8), "ms_per_step": ms_e2e,
+                "pipeline": "pinned host codes -> device, ipfb_wiener_upchannelize, spectra -> pinned host; "
+                            "three streams, two device slots, step i's read-back overlapping step i+1"},
         "gpu_launches": int(launches),
         "kernels": per_kernel,
         "stages": {"pfb_forward_ms": ms_fwd, "pfb_forward_gsas": NSAMP / (ms_fwd * 1e-3) / 1e9,
