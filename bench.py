@@ -80,9 +80,9 @@ def ncu_traffic(name: str):
 
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """SM clock and clock-event reasons during the timed region: NVML polled every
-    5 ms from a background thread (read-only queries), with an nvidia-smi -lms 200
-    sampler beside it as a fallback for when NVML is not importable."""
+    """SM clock and clock-event reasons during the timed region: the driver's NVML
+    polled every 5 ms from a background thread (read-only queries), with an
+    nvidia-smi -lms 200 sampler beside it as a fallback."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -95,30 +95,44 @@ class ClockSampler:
         self.proc = None
         self.path = os.path.join("/tmp", f"ipfb_clocks_{os.getpid()}.csv")
         self.nv = []          # (sm_mhz, max_mhz, reasons bitmask)
+        self.nv_err = None
         self._stop = None
         self._thr = None
 
+    @staticmethod
+    def _nvml():
+        """The driver's NVML library through ctypes (read-only queries only)."""
+        import ctypes
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                return ctypes.CDLL(name)
+            except OSError:
+                pass
+        raise OSError("libnvidia-ml not found")
+
     def _nvml_loop(self):
+        import ctypes
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            h = None
-            if self.pci:
-                try:
-                    h = pynvml.nvmlDeviceGetHandleByPciBusId(self.pci)
-                except Exception:
-                    h = None
-            if h is None:
-                h = pynvml.nvmlDeviceGetHandleByIndex(self.idx)
-            mx = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
+            nv = self._nvml()
+            if nv.nvmlInit_v2() != 0:
+                raise RuntimeError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            ok = self.pci is not None and nv.nvmlDeviceGetHandleByPciBusId_v2(self.pci.encode(), ctypes.byref(h)) == 0
+            if not ok and nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.idx), ctypes.byref(h)) != 0:
+                raise RuntimeError("no NVML handle")
+            NVML_CLOCK_SM = 1
+            mx, sm, rs = ctypes.c_uint(0), ctypes.c_uint(0), ctypes.c_ulonglong(0)
+            nv.nvmlDeviceGetMaxClockInfo(h, NVML_CLOCK_SM, ctypes.byref(mx))
+            get_rs = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
             while not self._stop.is_set():
-                sm = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
-                rs = pynvml.nvmlDeviceGetCurrentClocksEventReasons(h)
-                self.nv.append((sm, mx, rs))
+                if nv.nvmlDeviceGetClockInfo(h, NVML_CLOCK_SM, ctypes.byref(sm)) == 0 and \
+                        get_rs(h, ctypes.byref(rs)) == 0:
+                    self.nv.append((sm.value, mx.value, rs.value))
                 self._stop.wait(0.005)
-            pynvml.nvmlShutdown()
-        except Exception:
-            pass
+            nv.nvmlShutdown()
+        except Exception as e:  # reported in the summary; the nvidia-smi samples remain
+            self.nv_err = f"{type(e).__name__}: {e}"[:160]
 
     def __enter__(self):
         import threading
@@ -153,7 +167,7 @@ class ClockSampler:
             return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(x[1] for x in self.nv), "reasons": reasons,
                     "samples": len(sm), "source": "nvml, 5 ms"}
         if self.proc is None or not os.path.exists(self.path):
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "nvml_error": self.nv_err}
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
@@ -171,7 +185,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm), "source": "nvidia-smi, 200 ms"}
+                "samples": len(sm), "source": "nvidia-smi, 200 ms", "nvml_error": self.nv_err}
 
 
 # --------------------------------------------------------------------------- distributed
