@@ -135,7 +135,8 @@ void column_split(int J, int* C, int* S) {
 }
 
 int run_inverse_core(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
-                     double noise_level, int normalize, float2* d2, int C, int S, cudaStream_t st) {
+                     double noise_level, int normalize, float2* d2, int C, int S, cudaStream_t st,
+                     int out_block_major = 0) {
   const int N = g->lblock, J = g->nframes, H = N / 2;
   {
     Stage t("k2_unpack_irfft", st);
@@ -148,6 +149,7 @@ int run_inverse_core(const ipfb_geom* g, const uint8_t* codes, const float* scal
   gp.invJ = 1.0f / (float)J;
   gp.J = J;
   gp.ntap = g->ntap;
+  gp.out_block_major = out_block_major;
   Stage t("k3_column_wiener", st);
   CK(launch_k3(C, S, d2, window, N, gp, st), "k3_column_wiener");
   t.done();
@@ -376,17 +378,18 @@ int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const flo
   int C, S;
   column_split(g->nframes, &C, &S);
   if (upfactor % C) return IPFB_ERR_UNSUPPORTED;
-  rc = run_inverse_core(g, codes, scale, window, noise_level, normalize, d2, C, S, st);
-  if (rc) return rc;
   const long long nb = (long long)g->nframes / upfactor;
+  const bool two_pass = nb > 0 && upchan2_supported(g->lblock, C, upfactor);
+  rc = run_inverse_core(g, codes, scale, window, noise_level, normalize, d2, C, S, st, two_pass ? 1 : 0);
+  if (rc) return rc;
   if (nb == 0) return IPFB_OK;
-  if (upchan2_supported(g->lblock, C, upfactor)) {
+  if (two_pass) {
     // two passes: frames DFT + pa DFT into the second half of the workspace, then
     // the pb DFTs with the real-input split and contiguous stores
     float2* W = d2 + (size_t)g->nframes * (size_t)(g->lblock / 2);
     {
       Stage ta("k4a_upchan_frames", st);
-      CK(launch_k4a(d2, g->lblock, C, S, nb, W, x_out, st), "k4a_upchan_frames");
+      CK(launch_k4a(d2, g->lblock, g->nframes, nb, W, x_out, st), "k4a_upchan_frames");
       ta.done();
     }
     Stage tb("k4b_upchan_pairs", st);

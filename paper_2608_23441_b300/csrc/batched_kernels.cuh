@@ -177,6 +177,7 @@ __device__ __forceinline__ void column_item(const BStream& st, int p, float2* sm
   gp.gnorm = st.gnorm;
   gp.invJ = st.invJ;
   gp.J = J;
+  gp.out_block_major = 0;
   gp.ntap = 4;
   for (int m = threadIdx.x; m < S; m += T) {
     const int k = C * m + r;

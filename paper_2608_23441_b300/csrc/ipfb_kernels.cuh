@@ -302,8 +302,21 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
   } else {
     __syncthreads();
   }
-  // 4. inverse local FFT: smem -> global (in place over this CTA's input run)
-  block_fft<S, T, true>(sm, tid, SPad{sm}, GMem{base});
+  // 4. inverse local FFT: smem -> global, in place over this CTA's input run, or (for
+  // the up-channelizer) in place over the pair's J frames in block-major order: frame
+  // j at 64 (j >> 6) + 8 (j & 7) + ((j >> 3) & 7), i.e. each 64-frame block contiguous
+  // with its 8 residues as runs of 8.  Every CTA of the cluster has read its input
+  // before the cluster barrier above, so the reordering cannot overwrite unread data.
+  const bool bm = gp.out_block_major != 0;
+  float2* pbase = d2 + (size_t)p * J;
+  block_fft<S, T, true>(sm, tid, SPad{sm}, fn_st([=](int m, float2 v) {
+    if (bm) {
+      const int j = C * m + r;
+      pbase[64 * (j >> 6) + 8 * (j & 7) + ((j >> 3) & 7)] = v;
+    } else {
+      base[m] = v;
+    }
+  }));
 }
 
 // ----------------------------------------------------------------------------

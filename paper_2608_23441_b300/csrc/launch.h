@@ -14,6 +14,7 @@ struct GainParams {
   float invJ;
   int J;
   int ntap;
+  int out_block_major;  // k3 output layout: 0 = the d2 residue runs, 1 = block-major (k4a input)
 };
 
 struct UpchanSrc {
@@ -57,8 +58,10 @@ cudaError_t launch_upchan(const UpchanSrc& src, int L, long long nblocks, float2
                           cudaStream_t st);
 // Two-pass up-channelizer of the column-pair scratch (k4a: d2 -> W, then k4b: W ->
 // spectra), upfactor 64, lblock 1024/2048/4096; W holds nblocks * 32 N complex values.
+// k4a reads d2 in the block-major layout that k3 writes with out_block_major = 1:
+// frame j of pair p at d2[p J + 64 (j >> 6) + 8 (j & 7) + ((j >> 3) & 7)].
 bool upchan2_supported(int N, int C, int U);
-cudaError_t launch_k4a(const float2* d2, int N, int C, int S, long long nblocks, float2* W, float* x_out,
+cudaError_t launch_k4a(const float2* d2, int N, int J, long long nblocks, float2* W, float* x_out,
                        cudaStream_t st);
 cudaError_t launch_k4b(const float2* W, int N, long long nblocks, float2* out, cudaStream_t st);
 

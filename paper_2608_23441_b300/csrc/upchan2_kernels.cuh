@@ -14,7 +14,10 @@
 //
 // k4a: per tile (block b, NPB = 128 / PA consecutive pb, all pa: 128 pairs) the
 //   64-point frames DFT, the w_Q twiddle, the PA-point DFT over pa and the w_P
-//   twiddle; writes W[b][k2a][k1][pb] (NPB-element runs).
+//   twiddle; writes W[b][k2a][k1][pb] (NPB-element runs).  Its input is the scratch
+//   in the block-major order the column kernel writes for it (frame j of pair p at
+//   p J + 64 (j >> 6) + 8 (j & 7) + ((j >> 3) & 7)), so a tile is 128 contiguous
+//   512-byte runs.
 // k4b: per CTA (block b, a < PA/2) the 64-point DFTs over pb of the 128 rows
 //   (k2a, k1) with k2a in {a, PA-1-a} (both contiguous 32 KB slabs of W), which
 //   holds the partner Z[Q-k] of every output it writes (k1 != 0: row (PA-1-k2a,
@@ -56,14 +59,14 @@ __device__ __forceinline__ int k4a_slot(int row, int q) {
 
 template <int P>
 __global__ void __launch_bounds__(kK4aThreads)
-k4a_frames(const float2* __restrict__ d2, int C, int S, long long nblocks, float2* __restrict__ W,
+k4a_frames(const float2* __restrict__ d2, int J, long long nblocks, float2* __restrict__ W,
            float2* __restrict__ x2_out) {
   using K = K4Shape<P>;
   constexpr int T = kK4aThreads;
   constexpr int Q = K::Q, PA = K::PA, NPB = K::NPB;
   extern __shared__ float2 smk4a[];
-  float2* buf = smk4a;                // 8192
-  float2* tw_hi = buf + 64 * 128;     // Q >> 9
+  float2* buf = smk4a;                // max(64 x 128, 128 x 66): frames-DFT state / raw staging
+  float2* tw_hi = buf + 128 * 66;     // Q >> 9
   float2* tw_lo = tw_hi + (Q >> 9);   // 512
   const int tid = threadIdx.x;
   twid2_fill<9, false>(tw_hi, tw_lo, Q, tid, T);
@@ -73,29 +76,35 @@ k4a_frames(const float2* __restrict__ d2, int C, int S, long long nblocks, float
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long b = tile % nblocks;
     const int pb0 = (int)(tile / nblocks) * NPB;
-    // ---- (a) load 8 frames t = 8 m' + rt of one pair (all of a thread's loads in
-    // flight together), DFT over m', twiddle w_64^(rt k1a)
+    // ---- (a) load: the tile is 128 contiguous 512-byte blocks (one per pair, k3's
+    // block-major output: 8 residues rt x 8 consecutive m'); warp instruction i of
+    // warp w reads block q = w + 8 i whole, into raw staging [q][66] (float4-aligned
+    // rows, conflict-free 16-byte accesses); then thread (q, rt) takes its 8 frames.
+    {
+      const int lane = tid & 31, warp = tid >> 5;
+      float4 u[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int q = warp + 8 * i;
+        const int p = K::PB * (q / NPB) + pb0 + (q % NPB);
+        u[i] = reinterpret_cast<const float4*>(d2 + (long long)p * J + b * 64)[lane];
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) reinterpret_cast<float4*>(buf)[(warp + 8 * i) * 33 + lane] = u[i];
+    }
+    __syncthreads();
     float2 v4[4][8];
 #pragma unroll
     for (int it = 0; it < 4; ++it) {
       const int q = tid & 127, rt = (tid >> 7) + 2 * it;
-      const int p = K::PB * (q / NPB) + pb0 + (q % NPB);
-      if (C == 8) {
-        const float4* src = reinterpret_cast<const float4*>(d2 + ((long long)p * 8 + rt) * S + b * 8);
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const float4 u = src[h];
-          v4[it][2 * h] = make_float2(u.x, u.y);
-          v4[it][2 * h + 1] = make_float2(u.z, u.w);
-        }
-      } else {
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const long long j = b * 64 + 8 * m + rt;
-          v4[it][m] = d2[((long long)p * C + (int)(j % C)) * S + j / C];
-        }
+      for (int h = 0; h < 4; ++h) {
+        const float4 w4 = reinterpret_cast<const float4*>(buf)[q * 33 + rt * 4 + h];
+        v4[it][2 * h] = make_float2(w4.x, w4.y);
+        v4[it][2 * h + 1] = make_float2(w4.z, w4.w);
       }
     }
+    __syncthreads();  // the frames-DFT state below overwrites the staging area
 #pragma unroll
     for (int it = 0; it < 4; ++it) {
       const int q = tid & 127, rt = (tid >> 7) + 2 * it;
