@@ -16,10 +16,10 @@ size_t k1_smem() {
   const size_t b = (size_t)F * 4 * (H / 2 + 1) * sizeof(float);
   return a > b ? a : b;
 }
-template <int H>
-cudaError_t power(const float* x, const float* w, int ntap, int J, double* sums, cudaStream_t st) {
+template <int H, int NT>
+cudaError_t power_nt(const float* x, const float* w, int ntap, int J, double* sums, cudaStream_t st) {
   constexpr int TPF = tpf_for(H), F = fpc_for(H);
-  auto kern = k1_pfb_power<H, TPF, F>;
+  auto kern = k1_pfb_power<H, TPF, F, NT>;
   const size_t smem = k1_smem<H>();
   cudaError_t e = smem_attr(kern, smem);
   if (e != cudaSuccess) return e;
@@ -28,17 +28,28 @@ cudaError_t power(const float* x, const float* w, int ntap, int J, double* sums,
   kern<<<grid, TPF * F, smem, st>>>(x, w, ntap, J, sums);
   return cudaGetLastError();
 }
-template <int H>
-cudaError_t quant(const float* x, const float* w, int ntap, int J, const float* scale, uint8_t* codes,
-                  float2* spectra, cudaStream_t st) {
+template <int H, int NT>
+cudaError_t quant_nt(const float* x, const float* w, int ntap, int J, const float* scale, uint8_t* codes,
+                     float2* spectra, cudaStream_t st) {
   constexpr int TPF = tpf_for(H), F = fpc_for(H);
-  auto kern = k1_pfb_quant<H, TPF, F>;
+  auto kern = k1_pfb_quant<H, TPF, F, NT>;
   const size_t smem = k1_smem<H>();
   cudaError_t e = smem_attr(kern, smem);
   if (e != cudaSuccess) return e;
   const int nblk = (J + F - 1) / F;
   kern<<<nblk, TPF * F, smem, st>>>(x, w, ntap, J, scale, codes, spectra);
   return cudaGetLastError();
+}
+// 4 taps (the paper's and every benchmark's) get the unrolled loader
+template <int H>
+cudaError_t power(const float* x, const float* w, int ntap, int J, double* sums, cudaStream_t st) {
+  return (ntap == 4 && J >= 4) ? power_nt<H, 4>(x, w, ntap, J, sums, st) : power_nt<H, 0>(x, w, ntap, J, sums, st);
+}
+template <int H>
+cudaError_t quant(const float* x, const float* w, int ntap, int J, const float* scale, uint8_t* codes,
+                  float2* spectra, cudaStream_t st) {
+  return (ntap == 4 && J >= 4) ? quant_nt<H, 4>(x, w, ntap, J, scale, codes, spectra, st)
+                               : quant_nt<H, 0>(x, w, ntap, J, scale, codes, spectra, st);
 }
 }  // namespace
 

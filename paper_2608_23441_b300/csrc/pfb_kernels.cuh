@@ -10,18 +10,36 @@ namespace ipfb {
 // FFT of z[m] = d[2m] + i d[2m+1]; the polyphase sum is formed while loading:
 //   z[m] = sum_r (w[r][2m], w[r][2m+1]) * (x[(j+r) mod J][2m], x[(j+r) mod J][2m+1]).
 // Result: Z[k] in sm (natural order, padded).
-template <int H, int TPF>
+// NT > 0: the tap count is a compile-time constant (NT == ntap), so the 2 NT loads
+// of each element are independent and issued together; NT == 0: any ntap.
+template <int H, int TPF, int NT>
 __device__ __forceinline__ void frame_rfft_core(const float2* __restrict__ x2, const float2* __restrict__ w2,
                                                 int ntap, int J, int j, float2* sm, int tid) {
   auto ldp = [=](int m) {
     float2 acc = make_float2(0.0f, 0.0f);
-    int jj = j;
-    for (int r = 0; r < ntap; ++r) {
-      const float2 xv = x2[(size_t)jj * H + m];
-      const float2 wv = __ldg(w2 + (size_t)r * H + m);
-      acc.x = fmaf(wv.x, xv.x, acc.x);
-      acc.y = fmaf(wv.y, xv.y, acc.y);
-      jj = (jj + 1 == J) ? 0 : jj + 1;
+    if constexpr (NT > 0) {
+      float2 xv[NT], wv[NT];
+#pragma unroll
+      for (int r = 0; r < NT; ++r) {
+        int jj = j + r;
+        if (jj >= J) jj -= J;  // J >= NT
+        xv[r] = x2[(size_t)jj * H + m];
+        wv[r] = __ldg(w2 + (size_t)r * H + m);
+      }
+#pragma unroll
+      for (int r = 0; r < NT; ++r) {
+        acc.x = fmaf(wv[r].x, xv[r].x, acc.x);
+        acc.y = fmaf(wv[r].y, xv[r].y, acc.y);
+      }
+    } else {
+      int jj = j;
+      for (int r = 0; r < ntap; ++r) {
+        const float2 xv = x2[(size_t)jj * H + m];
+        const float2 wv = __ldg(w2 + (size_t)r * H + m);
+        acc.x = fmaf(wv.x, xv.x, acc.x);
+        acc.y = fmaf(wv.y, xv.y, acc.y);
+        jj = (jj + 1 == J) ? 0 : jj + 1;
+      }
     }
     return acc;
   };
@@ -48,7 +66,7 @@ __device__ __forceinline__ void rfft_post(const float2* sm, int H, int k, const 
 
 // Pass A: per-channel sums of Re^2 and Im^2 over all spectra (FP64 atomics at the
 // end of each CTA).  CTA processes frames blockIdx.x*F + f, stepping gridDim.x*F.
-template <int H, int TPF, int F>
+template <int H, int TPF, int F, int NT>
 __global__ void __launch_bounds__(TPF* F)
 k1_pfb_power(const float* __restrict__ x, const float* __restrict__ window, int ntap, int J,
              double* __restrict__ sums /* [2][H+1] */) {
@@ -67,7 +85,7 @@ k1_pfb_power(const float* __restrict__ x, const float* __restrict__ window, int 
   for (int jb = blockIdx.x * F; jb < J; jb += gridDim.x * F) {
     const int j = jb + f;
     const bool live = j < J;
-    frame_rfft_core<H, TPF>(x2, w2, ntap, J, live ? j : 0, sm, tid);
+    frame_rfft_core<H, TPF, NT>(x2, w2, ntap, J, live ? j : 0, sm, tid);
     __syncthreads();
     if (live) {
 #pragma unroll
@@ -135,7 +153,7 @@ __device__ __forceinline__ uint8_t pack2(int lo, int hi) {
 }
 
 // Pass B: recompute spectra, quantize, pack (and optionally write spectra).
-template <int H, int TPF, int F>
+template <int H, int TPF, int F, int NT>
 __global__ void __launch_bounds__(TPF* F)
 k1_pfb_quant(const float* __restrict__ x, const float* __restrict__ window, int ntap, int J,
              const float* __restrict__ scale, uint8_t* __restrict__ codes, float2* __restrict__ spectra) {
@@ -150,7 +168,7 @@ k1_pfb_quant(const float* __restrict__ x, const float* __restrict__ window, int 
   for (int jb = blockIdx.x * F; jb < J; jb += gridDim.x * F) {
     const int j = jb + f;
     const bool live = j < J;
-    frame_rfft_core<H, TPF>(x2, w2, ntap, J, live ? j : 0, sm, tid);
+    frame_rfft_core<H, TPF, NT>(x2, w2, ntap, J, live ? j : 0, sm, tid);
     __syncthreads();
     if (live) {
       uint8_t* row = codes + (size_t)j * H;
