@@ -37,7 +37,8 @@ cudaError_t quant_nt(const float* x, const float* w, int ntap, int J, const floa
   cudaError_t e = smem_attr(kern, smem);
   if (e != cudaSuccess) return e;
   const int nblk = (J + F - 1) / F;
-  kern<<<nblk, TPF * F, smem, st>>>(x, w, ntap, J, scale, codes, spectra);
+  const int grid = nblk < 148 * 4 ? nblk : 148 * 4;  // persistent: the twiddle table is built once per CTA
+  kern<<<grid, TPF * F, smem, st>>>(x, w, ntap, J, scale, codes, spectra);
   return cudaGetLastError();
 }
 // 4 taps (the paper's and every benchmark's) get the unrolled loader

@@ -46,6 +46,54 @@ __device__ __forceinline__ void frame_rfft_core(const float2* __restrict__ x2, c
   block_fft<H, TPF, false>(sm, tid, fn_ld(ldp), SPad{sm});
 }
 
+// The polyphase sums of the F consecutive frames jb .. jb+F-1 of a CTA, for a
+// compile-time tap count NT: each element m loads the F + NT - 1 rows it needs once
+// (instead of NT rows per frame) and the NT window values once, then writes the F
+// sums z_f[m] into the frames' padded buffers (frame f at smem + f * stride).
+template <int H, int F, int NT, int NTH>
+__device__ __forceinline__ void polyphase_group(const float2* __restrict__ x2, const float2* __restrict__ w2,
+                                                int J, int jb, float2* smem, int stride) {
+  constexpr int NR = F + NT - 1;
+  for (int m = threadIdx.x; m < H; m += NTH) {
+    float2 xr[NR], wv[NT];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      int jj = jb + r;
+      while (jj >= J) jj -= J;
+      xr[r] = x2[(size_t)jj * H + m];
+    }
+#pragma unroll
+    for (int t = 0; t < NT; ++t) wv[t] = __ldg(w2 + (size_t)t * H + m);
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+      float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        acc.x = fmaf(wv[t].x, xr[f + t].x, acc.x);
+        acc.y = fmaf(wv[t].y, xr[f + t].y, acc.y);
+      }
+      smem[f * stride + pidx(m)] = acc;
+    }
+  }
+}
+
+// Polyphase sum + H-point complex FFT of the CTA's frames: with a compile-time tap
+// count the sums of all F frames are formed together first; otherwise each frame's
+// first FFT pass forms its own sums while loading.
+template <int H, int TPF, int F, int NT>
+__device__ __forceinline__ void frames_rfft(const float2* __restrict__ x2, const float2* __restrict__ w2, int ntap,
+                                            int J, int jb, float2* smem, int tid, int f) {
+  float2* sm = smem + f * padded_len(H);
+  if constexpr (NT > 0) {
+    polyphase_group<H, F, NT, TPF * F>(x2, w2, J, jb, smem, padded_len(H));
+    __syncthreads();
+    block_fft<H, TPF, false>(sm, tid, SPad{sm}, SPad{sm});
+  } else {
+    const int j = jb + f;
+    frame_rfft_core<H, TPF, 0>(x2, w2, ntap, J, j < J ? j : 0, sm, tid);
+  }
+}
+
 // Post-processing of the half-length FFT into the real-input spectrum:
 //   E = (Z[k] + conj Z[H-k])/2, O = (Z[k] - conj Z[H-k])/(2i),
 //   Y[k] = E + e^{-2 pi i k/N} O,   Y[H-k] = conj(E) - e^{+2 pi i k/N} conj(O)... (see below)
@@ -85,7 +133,7 @@ k1_pfb_power(const float* __restrict__ x, const float* __restrict__ window, int 
   for (int jb = blockIdx.x * F; jb < J; jb += gridDim.x * F) {
     const int j = jb + f;
     const bool live = j < J;
-    frame_rfft_core<H, TPF, NT>(x2, w2, ntap, J, live ? j : 0, sm, tid);
+    frames_rfft<H, TPF, F, NT>(x2, w2, ntap, J, jb, smem, tid, f);
     __syncthreads();
     if (live) {
 #pragma unroll
@@ -168,7 +216,7 @@ k1_pfb_quant(const float* __restrict__ x, const float* __restrict__ window, int 
   for (int jb = blockIdx.x * F; jb < J; jb += gridDim.x * F) {
     const int j = jb + f;
     const bool live = j < J;
-    frame_rfft_core<H, TPF, NT>(x2, w2, ntap, J, live ? j : 0, sm, tid);
+    frames_rfft<H, TPF, F, NT>(x2, w2, ntap, J, jb, smem, tid, f);
     __syncthreads();
     if (live) {
       uint8_t* row = codes + (size_t)j * H;
