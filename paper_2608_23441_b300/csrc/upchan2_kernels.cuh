@@ -203,45 +203,32 @@ k4b_pairs(const float2* __restrict__ W, float2* __restrict__ out) {
     const int k2a = ka(i < 128 ? (i >> 6) : (i - 126));
     rb[i] = twiddle<false>(k1 + 64 * k2a, L);
   }
-  // ---- load: two 4096-element slabs (rows 0..127) and two 64-element rows, eight
-  // 16-byte loads in flight per thread
+  // ---- load: two 4096-element slabs (rows 0..127) and two 64-element rows.  With
+  // 256 threads, thread tid always handles the element pair pb = 2 (tid & 31) of rows
+  // k1 = (tid >> 5) + 8 i: the column and the swizzle are fixed per thread.
+  static_assert(T == 256, "index plan assumes 256 threads");
   {
-    constexpr int NV = 2 * 2048 + 2 * 32;  // float4 (two elements each)
-    auto src_of = [&](int f, int& rho, int& pb) -> const float4* {
-      int k2a, k1;
-      if (f < 4096) {
-        const int s = f >> 11, e = f & 2047;
-        k1 = e >> 5;
-        pb = (e & 31) * 2;
-        rho = s * 64 + k1;
-        k2a = ka(s);
-      } else {
-        const int x = (f - 4096) >> 5;
-        k1 = 0;
-        pb = ((f - 4096) & 31) * 2;
-        rho = 128 + x;
-        k2a = ka(2 + x);
-      }
-      return reinterpret_cast<const float4*>(W + ((b * PA + k2a) * 64 + k1) * 64 + pb);
-    };
-    for (int f0 = tid; f0 < NV; f0 += 8 * T) {
+    const int pb = (tid & 31) * 2, k1b = tid >> 5;
+    const int c0 = k4b_col(pb), c1 = k4b_col(pb + 1);
+    const float4* s0 = reinterpret_cast<const float4*>(W + ((b * PA + ka(0)) * 64) * 64 + pb);
+    const float4* s1 = reinterpret_cast<const float4*>(W + ((b * PA + ka(1)) * 64) * 64 + pb);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
       float4 u[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int f = f0 + i * T;
-        int rho, pb;
-        if (f < NV) u[i] = *src_of(f, rho, pb);
-      }
+      for (int i = 0; i < 8; ++i) u[i] = (half ? s1 : s0)[(k1b + 8 * i) * 32];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int f = f0 + i * T;
-        int rho, pb;
-        if (f < NV) {
-          (void)src_of(f, rho, pb);
-          rows[rho * RS + k4b_col(pb)] = make_float2(u[i].x, u[i].y);
-          rows[rho * RS + k4b_col(pb + 1)] = make_float2(u[i].z, u[i].w);
-        }
+        const int rho = half * 64 + k1b + 8 * i;
+        rows[rho * RS + c0] = make_float2(u[i].x, u[i].y);
+        rows[rho * RS + c1] = make_float2(u[i].z, u[i].w);
       }
+    }
+    if (tid < 64) {
+      const int x = tid >> 5;
+      const float4 u = *reinterpret_cast<const float4*>(W + ((b * PA + ka(2 + x)) * 64) * 64 + pb);
+      rows[(128 + x) * RS + c0] = make_float2(u.x, u.y);
+      rows[(128 + x) * RS + c1] = make_float2(u.z, u.w);
     }
   }
   __syncthreads();
@@ -277,30 +264,46 @@ k4b_pairs(const float2* __restrict__ W, float2* __restrict__ out) {
     }
   }
   __syncthreads();
-  // ---- post-processing and contiguous stores: w = (half, k2b, k1), k1 fastest
+  // ---- post-processing and contiguous stores: w = (half, k2b, k1), k1 fastest.  With
+  // 256 threads k1 = tid & 63 is fixed per thread, so the partner row and the per-row
+  // twiddle are too; only k2b and the half change across the unrolled iterations.
   float2* ob = out + b * (long long)(Q + 1);
-#pragma unroll 4
-  for (int w = tid; w < 2 * 64 * 64; w += T) {
-    const int k1 = w & 63, k2b = (w >> 6) & 63, hf = w >> 12;
-    const int rho = hf * 64 + k1;
-    const int k2a = ka(hf);
-    int rp, k2bp;
-    if (k1 != 0) {
-      rp = (1 - hf) * 64 + (64 - k1);
-      k2bp = 63 - k2b;
-    } else {
-      const int kp = (PA - k2a) % PA;
-      k2bp = k2a == 0 ? ((64 - k2b) & 63) : 63 - k2b;
-      rp = kp == ka(0) ? 0 : (kp == ka(1) ? 64 : (kp == ka(2) ? 128 : 129));
+  {
+    const int k1 = tid & 63, k2b0 = tid >> 6;
+    int rho_h[2], rp_h[2], k2a_h[2];
+    bool dc_wrap[2];
+    float2 rb_h[2];
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      const int k2a = ka(hf);
+      k2a_h[hf] = k2a;
+      rho_h[hf] = hf * 64 + k1;
+      rb_h[hf] = rb[hf * 64 + k1];
+      dc_wrap[hf] = (k1 == 0 && k2a == 0);
+      if (k1 != 0) {
+        rp_h[hf] = (1 - hf) * 64 + (64 - k1);
+      } else {
+        const int kp = (PA - k2a) % PA;
+        rp_h[hf] = kp == ka(0) ? 0 : (kp == ka(1) ? 64 : (kp == ka(2) ? 128 : 129));
+      }
     }
-    const float2 zk = rows[rho * RS + k4b_col(k2b)];
-    const float2 zm = rows[rp * RS + k4b_col(k2bp)];
-    const float2 E = cscale(cadd(zk, cconj(zm)), 0.5f);
-    const float2 dd = csub(zk, cconj(zm));
-    const float2 O = make_float2(0.5f * dd.y, -0.5f * dd.x);
-    const long long k = k1 + 64 * k2a + 64LL * PA * k2b;
-    ob[k] = cadd(E, cmul(cmul(rb[rho], t128[k2b]), O));
-    if (k == 0) ob[Q] = make_float2(zk.x - zk.y, 0.0f);
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+#pragma unroll 4
+    for (int i = 0; i < 16; ++i) {
+      const int k2b = k2b0 + 4 * i;
+      // partner mode: k2b' = 63 - k2b, except the DC row (k1 = 0, k2a = 0): (64 - k2b) mod 64
+      const int k2bp = dc_wrap[hf] ? ((64 - k2b) & 63) : 63 - k2b;
+      const float2 zk = rows[rho_h[hf] * RS + k4b_col(k2b)];
+      const float2 zm = rows[rp_h[hf] * RS + k4b_col(k2bp)];
+      const float2 E = cscale(cadd(zk, cconj(zm)), 0.5f);
+      const float2 dd = csub(zk, cconj(zm));
+      const float2 O = make_float2(0.5f * dd.y, -0.5f * dd.x);
+      const long long k = k1 + 64 * k2a_h[hf] + 64LL * PA * k2b;
+      ob[k] = cadd(E, cmul(cmul(rb_h[hf], t128[k2b]), O));
+      if (k == 0) ob[Q] = make_float2(zk.x - zk.y, 0.0f);
+    }
+    }
   }
 }
 
