@@ -73,9 +73,11 @@ k4a_frames(const float2* __restrict__ d2, int J, long long nblocks, float2* __re
   __syncthreads();
   const Twid2<9> tw{tw_hi, tw_lo};
   const long long ntiles = nblocks * (K::PB / NPB);
+  // pair group fastest: the PB / NPB tiles of one block, which together fill whole
+  // 512-byte rows of W, run at the same time, so those rows leave L2 complete
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long b = tile % nblocks;
-    const int pb0 = (int)(tile / nblocks) * NPB;
+    const long long b = tile / (K::PB / NPB);
+    const int pb0 = (int)(tile % (K::PB / NPB)) * NPB;
     // ---- (a) load: the tile is 128 contiguous 512-byte blocks (one per pair, k3's
     // block-major output: 8 residues rt x 8 consecutive m'); warp instruction i of
     // warp w reads block q = w + 8 i whole, into raw staging [q][66] (float4-aligned
