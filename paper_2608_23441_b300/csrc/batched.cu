@@ -101,9 +101,9 @@ void layout(Plan& P) {
 }  // namespace
 
 namespace ipfb {
-cudaError_t kb3_launch_v0(const BStream*, const BItem*, int, int*, cudaStream_t, int*);
-cudaError_t kb3_launch_v1(const BStream*, const BItem*, int, int*, cudaStream_t, int*);
-cudaError_t kb3_launch_v2(const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb3_launch_v0(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb3_launch_v1(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb3_launch_v2(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 }  // namespace ipfb
 
 namespace {
@@ -117,9 +117,9 @@ int launch_kb3(const Plan& P, char* ws, int cls, int v, cudaStream_t stream) {
   int nclusters = 0;
   cudaError_t e = cudaErrorInvalidValue;
   switch (v) {
-    case 0: e = kb3_launch_v0(s, it, (int)n, ctr, stream, &nclusters); break;
-    case 1: e = kb3_launch_v1(s, it, (int)n, ctr, stream, &nclusters); break;
-    case 2: e = kb3_launch_v2(s, it, (int)n, ctr, stream, &nclusters); break;
+    case 0: e = kb3_launch_v0(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
+    case 1: e = kb3_launch_v1(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
+    case 2: e = kb3_launch_v2(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
   }
   if (e != cudaSuccess) return fail(e, "kb3_columns");
   return IPFB_OK;

@@ -147,6 +147,7 @@ __device__ __forceinline__ void column_item(const BStream& st, int p, float2* sm
   const float2* w = st.chirp;
   const float invM = 1.0f / (float)M;
   // 1. a[n] = z[n] w[n], zero padded
+#pragma unroll 1
   for (int m = threadIdx.x; m < S; m += T) {
     const int n = C * m + r;
     sm[pidx(m)] = (n < J) ? cmul(col[n], __ldg(w + n)) : make_float2(0.0f, 0.0f);
@@ -154,6 +155,7 @@ __device__ __forceinline__ void column_item(const BStream& st, int p, float2* sm
   __syncthreads();
   conv_engine<C, S, T, MAXR, false>(sm, st.bhat, nullptr, r);
   // 2. X[k] = w[k] conv[k] / M for own k
+#pragma unroll 1
   for (int m = threadIdx.x; m < S; m += T) {
     const int k = C * m + r;
     if (k < J) sm[pidx(m)] = cscale(cmul(__ldg(w + k), sm[pidx(m)]), invM);
@@ -179,6 +181,7 @@ __device__ __forceinline__ void column_item(const BStream& st, int p, float2* sm
   gp.J = J;
   gp.out_block_major = 0;
   gp.ntap = 4;
+#pragma unroll 1
   for (int m = threadIdx.x; m < S; m += T) {
     const int k = C * m + r;
     float2 xk = make_float2(0.0f, 0.0f);
@@ -201,10 +204,12 @@ __device__ __forceinline__ void column_item(const BStream& st, int p, float2* sm
   } else {
     __syncthreads();
   }
+#pragma unroll 1
   for (int m = threadIdx.x; m < S; m += T) sm[pidx(m)] = sm2[pidx(m)];
   __syncthreads();
   conv_engine<C, S, T, MAXR, false>(sm, st.bhat, nullptr, r);
   // 5. x[j] = conj(w[j] conv'[j] / M)
+#pragma unroll 1
   for (int m = threadIdx.x; m < S; m += T) {
     const int j = C * m + r;
     if (j < J) col[j] = cconj(cscale(cmul(__ldg(w + j), sm[pidx(m)]), invM));
@@ -268,8 +273,12 @@ kb2_unpack(const BStream* __restrict__ streams, const BItem* __restrict__ items,
 
 // kb3: columns (4-tap windows); a cluster of C CTAs per item, M = C * S with S
 // picked per item.  Dynamic smem: two padded S = 8192 buffers.
-template <int C, int T, int MAXR>
-__global__ void __launch_bounds__(T, 1)
+// One launch per M class: every item of the class has M = C * S, so each kernel is
+// specialised to its S (one kernel switching over all S was register-allocated for
+// the largest and spilled ~3.7 KB per thread), and limited to 128 registers so two
+// CTAs share an SM (measured faster than one CTA with 255 registers).
+template <int C, int S, int T, int MAXR>
+__global__ void __launch_bounds__(T, 2)
 kb3_columns(const BStream* __restrict__ streams, const BItem* __restrict__ items, int nitems, int* counter) {
   extern __shared__ float2 smem[];
   __shared__ int slot;
@@ -280,14 +289,7 @@ kb3_columns(const BStream* __restrict__ streams, const BItem* __restrict__ items
     if (it >= nitems) break;
     const BItem item = items[it];
     const BStream& st = streams[item.s];
-    switch (st.M / C) {
-      case 512: column_item<C, 512, T, MAXR>(st, item.a, smem, r); break;
-      case 1024: column_item<C, 1024, T, MAXR>(st, item.a, smem, r); break;
-      case 2048: column_item<C, 2048, T, MAXR>(st, item.a, smem, r); break;
-      case 4096: column_item<C, 4096, T, MAXR>(st, item.a, smem, r); break;
-      case 8192: column_item<C, 8192, T, MAXR>(st, item.a, smem, r); break;
-      default: break;
-    }
+    if (st.M == C * S) column_item<C, S, T, MAXR>(st, item.a, smem, r);  // always true within a class
     if constexpr (C > 1) {
       cg::this_cluster().sync();
     } else {
@@ -296,7 +298,52 @@ kb3_columns(const BStream* __restrict__ streams, const BItem* __restrict__ items
   }
 }
 
-// B-hat tables: one cluster per distinct J (blockIdx.x / C)
+// Launch of the class-M kernel of one variant: a persistent grid of as many clusters
+// as fit, each CTA with 2 S padded elements of shared memory (data + partner buffer).
+template <int C, int T, int MAXR>
+struct Kb3Launch {
+  template <int S>
+  static cudaError_t go(const BStream* s, const BItem* it, int n, int* ctr, cudaStream_t stream, int* nclusters) {
+    auto kern = kb3_columns<C, S, T, MAXR>;
+    const size_t smem = 2 * (size_t)padded_len(S) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(T);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(C);
+    int nc = 0;
+    e = cudaOccupancyMaxActiveClusters(&nc, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (nc < 1) nc = 1;
+    if (nc > n) nc = n;
+    *nclusters = nc;
+    cfg.gridDim = dim3(nc * C);
+    e = cudaLaunchKernelEx(&cfg, kern, s, it, n, ctr);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
+  static cudaError_t launch(int M, const BStream* s, const BItem* it, int n, int* ctr, cudaStream_t stream,
+                            int* nclusters) {
+    switch (M / C) {
+      case 512: return go<512>(s, it, n, ctr, stream, nclusters);
+      case 1024: return go<1024>(s, it, n, ctr, stream, nclusters);
+      case 2048: return go<2048>(s, it, n, ctr, stream, nclusters);
+      case 4096: return go<4096>(s, it, n, ctr, stream, nclusters);
+      case 8192: return go<8192>(s, it, n, ctr, stream, nclusters);
+    }
+    return cudaErrorNotSupported;
+  }
+};
+
 template <int C, int T, int MAXR>
 __global__ void __launch_bounds__(T, 1)
 kb_bhat(const int* __restrict__ Js, const int* __restrict__ Ms, const float2* const* __restrict__ chirps,
