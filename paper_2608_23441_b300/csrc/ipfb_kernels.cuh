@@ -173,6 +173,45 @@ __device__ __forceinline__ void split_gain(float2& zk, float2& zm, float2 ga, fl
   zm = cadd(cconj(ya), cmul_i(cconj(yb)));
 }
 
+// The same for a compile-time tap count NT > 0, in one step: W_a and W_b share the
+// powers of e1, and the split, the gains and the recombination fold into
+//   s = Z_k + conj Z_-k,  d = Z_k - conj Z_-k,  P = (Ga/2) s,  Q = (Gb/2) d,
+//   Z'_k = P + Q,  Z'_-k = conj(P - Q).
+// Where either |W|^2 falls below kFp64Below both gains come from gain_at.
+template <int NT>
+__device__ __forceinline__ void pair_gain(float2& zk, float2& zm, const float* ta, const float* tb, int k,
+                                          float2 e1, const GainParams& gp) {
+  static_assert(NT > 0, "compile-time tap count");
+  float2 ep[NT];
+  ep[0] = make_float2(1.0f, 0.0f);
+  if constexpr (NT > 1) ep[1] = e1;
+#pragma unroll
+  for (int q = 2; q < NT; ++q) ep[q] = cmul(ep[q / 2], ep[q - q / 2]);
+  float2 Wa = make_float2(ta[0], 0.0f), Wb = make_float2(tb[0], 0.0f);
+#pragma unroll
+  for (int q = 1; q < NT; ++q) {
+    Wa.x = fmaf(ta[q], ep[q].x, Wa.x);
+    Wa.y = fmaf(ta[q], ep[q].y, Wa.y);
+    Wb.x = fmaf(tb[q], ep[q].x, Wb.x);
+    Wb.y = fmaf(tb[q], ep[q].y, Wb.y);
+  }
+  const float a2a = fmaf(Wa.x, Wa.x, Wa.y * Wa.y), a2b = fmaf(Wb.x, Wb.x, Wb.y * Wb.y);
+  float2 Ga, Gb;
+  if (fminf(a2a, a2b) < kFp64Below) {
+    Ga = cscale(gain_at<NT>(ta, k, e1, gp), 0.5f);
+    Gb = cscale(gain_at<NT>(tb, k, e1, gp), 0.5f);
+  } else {
+    const float half = 0.5f * gp.gnorm * gp.invJ;
+    Ga = cscale(Wa, __fdividef(half, a2a + gp.phi2));
+    Gb = cscale(Wb, __fdividef(half, a2b + gp.phi2));
+  }
+  const float2 sv = make_float2(zk.x + zm.x, zk.y - zm.y);
+  const float2 dv = make_float2(zk.x - zm.x, zk.y + zm.y);
+  const float2 P = cmul(Ga, sv), Q = cmul(Gb, dv);
+  zk = cadd(P, Q);
+  zm = make_float2(P.x - Q.x, Q.y - P.y);
+}
+
 // ----------------------------------------------------------------------------
 // K3: per column pair: FFT_J along frames -> gain -> inverse FFT_J, in place on d2.
 // A cluster of C CTAs handles one pair; CTA r owns z[C m + r], m < S.
@@ -251,8 +290,12 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
       for (int ka = 0; ka < C; ++ka) {
         const int k = kb0 + S * ka;
         const float2 e1 = rotq<C, false>(e0, ka);
-        const float2 ga = gain_at<NT>(ta, k, e1, gp), gb = gain_at<NT>(tb, k, e1, gp);
-        split_gain(z0[ka], z1[C - 1 - ka], ga, gb);
+        if constexpr (NT > 0) {
+          pair_gain<NT>(z0[ka], z1[C - 1 - ka], ta, tb, k, e1, gp);
+        } else {
+          const float2 ga = gain_at<NT>(ta, k, e1, gp), gb = gain_at<NT>(tb, k, e1, gp);
+          split_gain(z0[ka], z1[C - 1 - ka], ga, gb);
+        }
       }
     } else if (t == 0) {
       // modes S*ka; -k is S*((C-ka) mod C)
