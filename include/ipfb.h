@@ -178,7 +178,9 @@ int upchannelize(const float* x, int64_t nsamples, int64_t block, float* out, vo
  * a round trip of the reconstructed stream through time order.  x_out (time
  * order) is optional (NULL = not written).  out: float2 [J/upfactor][L/2 + 1].
  * Workspace: ipfb_workspace_size(g, IPFB_OP_WIENER_UPCHAN) (2 J N floats: the
- * column-pair scratch and the up-channelizer's intermediate).
+ * column-pair scratch and the up-channelizer's intermediate); it must start on a
+ * 16-byte boundary (the up-channelizer moves it with 16-byte copies), else
+ * IPFB_ERR_INVALID.
  */
 int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const float* scale,
                              const float* window, double noise_level, int normalize,

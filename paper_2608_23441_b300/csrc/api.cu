@@ -373,6 +373,7 @@ int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const flo
   size_t need = 0;
   ipfb_workspace_size(g, IPFB_OP_WIENER_UPCHAN, &need);
   if (!ws || ws_bytes < need) return IPFB_ERR_WORKSPACE;
+  if (misaligned16(ws)) return IPFB_ERR_INVALID;
   cudaStream_t st = as_stream(stream);
   float2* d2 = reinterpret_cast<float2*>(ws);
   int C, S;

@@ -231,6 +231,15 @@ __device__ __forceinline__ void apply_twiddles(float2* v, float2 w) {
   }
 }
 
+// asynchronous 16-byte global -> shared copies (both addresses 16-byte aligned):
+// issue, close the group, wait for all of this thread's groups
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // padded shared-memory index: one spare float2 after every 16, so that radix-16
 // scatters (stride 16 elements) land in distinct banks.
 __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }

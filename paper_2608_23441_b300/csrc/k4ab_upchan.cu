@@ -7,7 +7,7 @@ namespace {
 template <int P>
 cudaError_t k4a(const float2* d2, int J, long long nblocks, float2* W, float* x_out, cudaStream_t st) {
   constexpr int Q = K4Shape<P>::Q;
-  const size_t smem = (size_t)(128 * 66 + (Q >> 9) + 512) * sizeof(float2);
+  const size_t smem = (size_t)(64 * 128 + 128 * 66 + (Q >> 9) + 512) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(k4a_frames<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per = 0;

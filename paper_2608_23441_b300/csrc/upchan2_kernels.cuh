@@ -64,36 +64,40 @@ k4a_frames(const float2* __restrict__ d2, int J, long long nblocks, float2* __re
   using K = K4Shape<P>;
   constexpr int T = kK4aThreads;
   constexpr int Q = K::Q, PA = K::PA, NPB = K::NPB;
-  extern __shared__ float2 smk4a[];
-  float2* buf = smk4a;                // max(64 x 128, 128 x 66): frames-DFT state / raw staging
-  float2* tw_hi = buf + 128 * 66;     // Q >> 9
+  extern __shared__ __align__(16) float2 smk4a[];
+  float2* buf = smk4a;                // 64 x 128 frames-DFT state
+  float2* stage = buf + 64 * 128;     // 128 x 66 raw staging (asynchronous copies)
+  float2* tw_hi = stage + 128 * 66;   // Q >> 9
   float2* tw_lo = tw_hi + (Q >> 9);   // 512
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   twid2_fill<9, false>(tw_hi, tw_lo, Q, tid, T);
-  __syncthreads();
   const Twid2<9> tw{tw_hi, tw_lo};
   const long long ntiles = nblocks * (K::PB / NPB);
   // pair group fastest: the PB / NPB tiles of one block, which together fill whole
-  // 512-byte rows of W, run at the same time, so those rows leave L2 complete
+  // 512-byte rows of W, run at the same time, so those rows leave L2 complete.
+  // A tile's input is 128 contiguous 512-byte blocks (one per pair, the column
+  // kernel's block-major output: 8 residues rt x 8 consecutive m'); warp w copies
+  // blocks q = w + 8 i whole into the staging rows [q][66] (float4-aligned rows,
+  // conflict-free 16-byte accesses) with asynchronous 16-byte copies, the next
+  // tile's while this one is computed.
+  auto prefetch = [&](long long tile) {
+    const long long b = tile / (K::PB / NPB);
+    const int pb0 = (int)(tile % (K::PB / NPB)) * NPB;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int q = warp + 8 * i;
+      const int p = K::PB * (q / NPB) + pb0 + (q % NPB);
+      cp_async16(reinterpret_cast<float4*>(stage) + q * 33 + lane,
+                 reinterpret_cast<const float4*>(d2 + (long long)p * J + b * 64) + lane);
+    }
+    cp_async_commit();
+  };
+  if ((long long)blockIdx.x < ntiles) prefetch(blockIdx.x);
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long b = tile / (K::PB / NPB);
     const int pb0 = (int)(tile % (K::PB / NPB)) * NPB;
-    // ---- (a) load: the tile is 128 contiguous 512-byte blocks (one per pair, k3's
-    // block-major output: 8 residues rt x 8 consecutive m'); warp instruction i of
-    // warp w reads block q = w + 8 i whole, into raw staging [q][66] (float4-aligned
-    // rows, conflict-free 16-byte accesses); then thread (q, rt) takes its 8 frames.
-    {
-      const int lane = tid & 31, warp = tid >> 5;
-      float4 u[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int q = warp + 8 * i;
-        const int p = K::PB * (q / NPB) + pb0 + (q % NPB);
-        u[i] = reinterpret_cast<const float4*>(d2 + (long long)p * J + b * 64)[lane];
-      }
-#pragma unroll
-      for (int i = 0; i < 16; ++i) reinterpret_cast<float4*>(buf)[(warp + 8 * i) * 33 + lane] = u[i];
-    }
+    // ---- (a) the tile's copies have landed; thread (q, rt) takes its 8 frames
+    cp_async_wait_all();
     __syncthreads();
     float2 v4[4][8];
 #pragma unroll
@@ -101,12 +105,13 @@ k4a_frames(const float2* __restrict__ d2, int J, long long nblocks, float2* __re
       const int q = tid & 127, rt = (tid >> 7) + 2 * it;
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
-        const float4 w4 = reinterpret_cast<const float4*>(buf)[q * 33 + rt * 4 + h];
+        const float4 w4 = reinterpret_cast<const float4*>(stage)[q * 33 + rt * 4 + h];
         v4[it][2 * h] = make_float2(w4.x, w4.y);
         v4[it][2 * h + 1] = make_float2(w4.z, w4.w);
       }
     }
-    __syncthreads();  // the frames-DFT state below overwrites the staging area
+    __syncthreads();  // every read of the staging area is done: prefetch the next tile
+    if (tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);
 #pragma unroll
     for (int it = 0; it < 4; ++it) {
       const int q = tid & 127, rt = (tid >> 7) + 2 * it;

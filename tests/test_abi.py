@@ -115,6 +115,9 @@ def test_host_validation_rejects_before_launch():
     # code arrays are read with 16-byte loads: an unaligned start is refused
     odd = ctypes.c_void_p(0x1008)
     assert L.ipfb_wiener(G, odd, fake, fake, 0.01, 1, fake, fake, 1 << 30, None) == ipfb.ERR_INVALID
+    # the up-channelizer's workspace is moved with 16-byte copies: 16-byte aligned
+    assert L.ipfb_wiener_upchannelize(ctypes.byref(g_up), fake, fake, fake, 0.01, 1, 64, fake, None, odd,
+                                      1 << 30, None) == ipfb.ERR_INVALID
 
 
 def test_binding_refuses_cpu_tensors():
