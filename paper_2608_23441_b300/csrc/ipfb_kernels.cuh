@@ -57,40 +57,61 @@ __device__ __forceinline__ void k2_group(const uint8_t* __restrict__ codes, cons
         reinterpret_cast<uint4*>(crow + ff * H)[c] = reinterpret_cast<const uint4*>(codes + jj * H)[c];
       }
     }
-    for (int i = threadIdx.x; i <= H; i += TPF * F) sscale[i] = scale[i];
+    for (int i = threadIdx.x; i <= H; i += TPF * F) sscale[i] = scale[i] * pre;  // 1/(2H) folded in
   }
   __syncthreads();
   const Twid2<7> tw{tw_hi, tw_lo};
   const uint8_t* row = crow + f * H;
 
-  // pre-processing: each thread forms Z[k] and Z[H-k] for k in [0, H/2]
-  for (int k = tid; live && k <= H / 2; k += TPF) {
-    const int km = H - k;  // == H for k == 0 (Nyquist lives in byte 0's high nibble)
-    const uint8_t bk = row[k];
-    const uint8_t bm = row[km == H ? 0 : km];
-    auto nib = [](uint8_t v, int hi) -> float {
-      int q = hi ? (v >> 4) : (v & 0xF);
-      return (float)((q ^ 8) - 8);
-    };
-    float2 yk, ym;
-    if (k == 0) {
-      yk = make_float2(nib(bk, 0) * sscale[0], 0.0f);
-      ym = make_float2(nib(bk, 1) * sscale[H], 0.0f);
-    } else {
-      yk = make_float2(nib(bk, 0) * sscale[k], nib(bk, 1) * sscale[k]);
-      ym = make_float2(nib(bm, 0) * sscale[km], nib(bm, 1) * sscale[km]);
-    }
-    // E, O at k:   E = (yk + conj ym)/2, O = (yk - conj ym) w/2, w = e^{+2 pi i k/N}
-    const float2 w = tw(k);
+  // pre-processing: Z[k] and Z[H-k] for k in [0, H/2], four consecutive k per step
+  // (one 4-byte load of codes k..k+3, two of the mirror bytes H-k-3..H-k, float4
+  // loads of the steps and the twiddles).  With d = Y[k] - conj Y[H-k]:
+  //   E = Y[k] + conj Y[H-k],  O = d w,  Z[k] = E + i O,  Z[H-k] = conj E + i conj O
+  // (w = e^{+2 pi i k/N}; the 1/2 and 1/H are in the staged steps).  A nibble q
+  // (two's complement) becomes a float exactly as (2^23 + (q ^ 8)) - (2^23 + 8).
+  auto nib = [](uint32_t v, int hi) -> float {
+    return __uint_as_float(((hi ? v >> 4 : v) & 0xFu) ^ 0x4B000008u) - 8388616.0f;
+  };
+  auto emit = [&](int k, float2 yk, float2 ym, float2 w) {
     const float2 e = cadd(yk, cconj(ym));
     const float2 o = cmul(csub(yk, cconj(ym)), w);
-    const float2 zk = cscale(cadd(e, cmul_i(o)), pre);
-    // at H-k: E' = conj(E), O' = (ym - conj yk) w', w' = e^{+2 pi i (H-k)/N} = -conj(w)
-    const float2 e2 = cconj(e);
-    const float2 o2 = cmul(csub(ym, cconj(yk)), make_float2(-w.x, w.y));
-    const float2 zm = cscale(cadd(e2, cmul_i(o2)), pre);
-    sm[pidx(k)] = zk;
-    if (k != 0 && km != k) sm[pidx(km)] = zm;
+    sm[pidx(k)] = make_float2(e.x - o.y, e.y + o.x);
+    if (k != 0 && 2 * k != H) sm[pidx(H - k)] = make_float2(e.x + o.y, o.x - e.y);
+  };
+  for (int g = tid; live && g < H / 8; g += TPF) {
+    const int k0 = 4 * g;
+    const uint32_t cw = *reinterpret_cast<const uint32_t*>(row + k0);
+    const uint32_t mlo = *reinterpret_cast<const uint32_t*>(row + (H - k0 - 4));  // bytes H-k0-4 .. H-k0-1
+    const uint32_t mhi = g ? row[H - k0] : 0u;                                     // byte H-k0
+    const float4 sk = *reinterpret_cast<const float4*>(sscale + k0);
+    const float4 smv = *reinterpret_cast<const float4*>(sscale + (H - k0 - 4));
+    const float sm0 = sscale[H - k0];  // g = 0: the Nyquist step
+    const float2 th = tw_hi[k0 >> 7];
+    const float4 tl01 = *reinterpret_cast<const float4*>(tw_lo + (k0 & 127));
+    const float4 tl23 = *reinterpret_cast<const float4*>(tw_lo + (k0 & 127) + 2);
+    const float skj[4] = {sk.x, sk.y, sk.z, sk.w};
+    const float smj[4] = {sm0, smv.w, smv.z, smv.y};
+    const uint32_t bmj[4] = {mhi, mlo >> 24, mlo >> 16, mlo >> 8};
+    const float2 tlj[4] = {make_float2(tl01.x, tl01.y), make_float2(tl01.z, tl01.w), make_float2(tl23.x, tl23.y),
+                           make_float2(tl23.z, tl23.w)};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t bk = cw >> (8 * j);
+      float2 yk, ym;
+      if (j == 0 && g == 0) {  // DC and Nyquist share byte 0
+        yk = make_float2(nib(bk, 0) * skj[0], 0.0f);
+        ym = make_float2(nib(bk, 1) * smj[0], 0.0f);
+      } else {
+        yk = make_float2(nib(bk, 0) * skj[j], nib(bk, 1) * skj[j]);
+        ym = make_float2(nib(bmj[j], 0) * smj[j], nib(bmj[j], 1) * smj[j]);
+      }
+      emit(k0 + j, yk, ym, cmul(th, tlj[j]));
+    }
+  }
+  if (live && tid == 0) {  // k = H/2, its own mirror
+    const uint32_t bk = row[H / 2];
+    const float2 y = make_float2(nib(bk, 0) * sscale[H / 2], nib(bk, 1) * sscale[H / 2]);
+    emit(H / 2, y, y, tw(H / 2));
   }
   __syncthreads();
   block_fft<H, TPF, true>(sm, tid, SPad{sm}, SPad{sm});
