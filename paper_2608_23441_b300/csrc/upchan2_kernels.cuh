@@ -172,16 +172,22 @@ k4a_frames(const float2* __restrict__ d2, int J, long long nblocks, float2* __re
 }
 
 // ---------------------------------------------------------------------------
-// k4b.  Rows rho (stride RS = 65, odd, so that consecutive rows at one column hit
-// distinct banks in the post-processing): 0..63 = (a, k1), 64..127 = (PA-1-a, k1), 128 = (PA-a mod PA,
+// k4b.  Rows rho of 64 elements, element c of row rho at rho 64 + (k4b_col(c) ^
+// k4b_rowx(rho)): the column swizzle k4b_col puts the radix-8 accesses of one row
+// (columns 8 bf + r and bf + 8 r, lanes bf) into distinct banks, and the row XOR
+// puts the two rows of a half-warp into opposite halves of the banks (FFT passes)
+// and any 16 consecutive rows at one column into distinct banks (post-processing).
+// Rows: 0..63 = (a, k1), 64..127 = (PA-1-a, k1), 128 = (PA-a mod PA,
 // 0), 129 = (a+1 mod PA, 0).  Tables: w_128^n (the 64-point FFT twiddles and the
 // k2b part of exp(-2 pi i k / L)) and w_L^(k1 + 64 k2a) per row.
 // ---------------------------------------------------------------------------
-constexpr int kK4bRS = 65;
+constexpr int kK4bRS = 64;
 constexpr int kK4bRows = 130;
 // column swizzle inside a row: the radix-8 passes access columns 8 bf + r and bf + 8 r
 // (lanes bf); c ^ ((c >> 3) & 7) maps both onto distinct banks
 __device__ __forceinline__ int k4b_col(int c) { return c ^ ((c >> 3) & 7); }
+__device__ __forceinline__ int k4b_rowx(int rho) { return ((rho & 1) << 3) | ((rho >> 1) & 7); }
+__device__ __forceinline__ int k4b_at(int rho, int c) { return rho * kK4bRS + (k4b_col(c) ^ k4b_rowx(rho)); }
 
 template <int P>
 constexpr size_t k4b_smem_bytes() {
@@ -216,7 +222,14 @@ k4b_pairs(const float2* __restrict__ W, float2* __restrict__ out) {
   static_assert(T == 256, "index plan assumes 256 threads");
   {
     const int pb = (tid & 31) * 2, k1b = tid >> 5;
-    const int c0 = k4b_col(pb), c1 = k4b_col(pb + 1);
+    // odd lanes store their second element first: each store instruction then puts
+    // the 16 lanes of a half-warp into 16 distinct bank pairs
+    const bool sw = tid & 1;
+    const int ca = sw ? pb + 1 : pb, cb = sw ? pb : pb + 1;
+    auto put = [&](int rho, float4 u) {
+      rows[k4b_at(rho, ca)] = sw ? make_float2(u.z, u.w) : make_float2(u.x, u.y);
+      rows[k4b_at(rho, cb)] = sw ? make_float2(u.x, u.y) : make_float2(u.z, u.w);
+    };
     const float4* s0 = reinterpret_cast<const float4*>(W + ((b * PA + ka(0)) * 64) * 64 + pb);
     const float4* s1 = reinterpret_cast<const float4*>(W + ((b * PA + ka(1)) * 64) * 64 + pb);
 #pragma unroll
@@ -225,17 +238,11 @@ k4b_pairs(const float2* __restrict__ W, float2* __restrict__ out) {
 #pragma unroll
       for (int i = 0; i < 8; ++i) u[i] = (half ? s1 : s0)[(k1b + 8 * i) * 32];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int rho = half * 64 + k1b + 8 * i;
-        rows[rho * RS + c0] = make_float2(u[i].x, u[i].y);
-        rows[rho * RS + c1] = make_float2(u[i].z, u[i].w);
-      }
+      for (int i = 0; i < 8; ++i) put(half * 64 + k1b + 8 * i, u[i]);
     }
     if (tid < 64) {
       const int x = tid >> 5;
-      const float4 u = *reinterpret_cast<const float4*>(W + ((b * PA + ka(2 + x)) * 64) * 64 + pb);
-      rows[(128 + x) * RS + c0] = make_float2(u.x, u.y);
-      rows[(128 + x) * RS + c1] = make_float2(u.z, u.w);
+      put(128 + x, *reinterpret_cast<const float4*>(W + ((b * PA + ka(2 + x)) * 64) * 64 + pb));
     }
   }
   __syncthreads();
@@ -247,25 +254,26 @@ k4b_pairs(const float2* __restrict__ W, float2* __restrict__ out) {
       const int rho = rg * 4 + (lane >> 3), bf = lane & 7;
       const bool ok = rho < kK4bRows;
       float2* row = rows + (ok ? rho : 0) * RS;
+      const int rx = k4b_rowx(ok ? rho : 0);
       float2 v[8];
       if (ok) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) v[r] = row[k4b_col(bf + 8 * r)];
+        for (int r = 0; r < 8; ++r) v[r] = row[k4b_col(bf + 8 * r) ^ rx];
         DFT<8, false>::run(v);
       }
       __syncwarp();
       if (ok) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) row[k4b_col(8 * bf + r)] = v[r];  // Ns = 1: output 8 bf + r
+        for (int r = 0; r < 8; ++r) row[k4b_col(8 * bf + r) ^ rx] = v[r];  // Ns = 1: output 8 bf + r
       }
       __syncwarp();
       if (ok) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) v[r] = row[k4b_col(bf + 8 * r)];
+        for (int r = 0; r < 8; ++r) v[r] = row[k4b_col(bf + 8 * r) ^ rx];
         if (bf) apply_twiddles<8>(v, t128[2 * bf]);  // w_64^bf
         DFT<8, false>::run(v);
 #pragma unroll
-        for (int r = 0; r < 8; ++r) row[k4b_col(bf + 8 * r)] = v[r];  // Ns = 8: output bf + 8 r
+        for (int r = 0; r < 8; ++r) row[k4b_col(bf + 8 * r) ^ rx] = v[r];  // Ns = 8: output bf + 8 r
       }
       __syncwarp();
     }
@@ -301,8 +309,8 @@ k4b_pairs(const float2* __restrict__ W, float2* __restrict__ out) {
       const int k2b = k2b0 + 4 * i;
       // partner mode: k2b' = 63 - k2b, except the DC row (k1 = 0, k2a = 0): (64 - k2b) mod 64
       const int k2bp = dc_wrap[hf] ? ((64 - k2b) & 63) : 63 - k2b;
-      const float2 zk = rows[rho_h[hf] * RS + k4b_col(k2b)];
-      const float2 zm = rows[rp_h[hf] * RS + k4b_col(k2bp)];
+      const float2 zk = rows[k4b_at(rho_h[hf], k2b)];
+      const float2 zm = rows[k4b_at(rp_h[hf], k2bp)];
       const float2 E = cscale(cadd(zk, cconj(zm)), 0.5f);
       const float2 dd = csub(zk, cconj(zm));
       const float2 O = make_float2(0.5f * dd.y, -0.5f * dd.x);
