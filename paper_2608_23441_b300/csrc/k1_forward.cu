@@ -33,7 +33,8 @@ cudaError_t quant_nt(const float* x, const float* w, int ntap, int J, const floa
                      float2* spectra, cudaStream_t st) {
   constexpr int TPF = tpf_for(H), F = fpc_for(H);
   auto kern = k1_pfb_quant<H, TPF, F, NT>;
-  const size_t smem = k1_smem<H>();
+  // frames + twiddles, then the H + 1 reciprocal steps
+  const size_t smem = ((size_t)F * padded_len(H) + 256) * sizeof(float2) + (size_t)(H + 4) * sizeof(float);
   cudaError_t e = smem_attr(kern, smem);
   if (e != cudaSuccess) return e;
   const int nblk = (J + F - 1) / F;

@@ -196,6 +196,18 @@ __device__ __forceinline__ int quant4(float v, float s) {
   q = fminf(fmaxf(q, -7.0f), 7.0f);
   return (int)q;
 }
+// The same decision from a precomputed reciprocal r = 1/s (correctly rounded): d =
+// v r lies within 1.5 2^-23 |v/s| of the rounded quotient fl(v/s), so for |d| < 8
+// the two round to the same integer unless d is within 3e-6 of a half-integer
+// (then the exact quotient is formed); |d| >= 8 clamps to +-7 either way.
+__device__ __forceinline__ int quant4r(float v, float s, float r) {
+  if (s == 0.0f) return 0;
+  const float d = v * r;
+  float q = rintf(d);
+  if (fabsf(d) < 8.0f && 0.5f - fabsf(d - q) < 3.0e-6f) q = rintf(__fdiv_rn(v, s));
+  q = fminf(fmaxf(q, -7.0f), 7.0f);
+  return (int)q;
+}
 __device__ __forceinline__ uint8_t pack2(int lo, int hi) {
   return (uint8_t)((lo & 0xF) | ((hi & 0xF) << 4));
 }
@@ -213,6 +225,9 @@ k1_pfb_quant(const float* __restrict__ x, const float* __restrict__ window, int 
   float2* tw_hi = smem + F * padded_len(H);
   twid2_fill<7, false>(tw_hi, tw_hi + 128, 2 * H, threadIdx.x, TPF * F);
   const Twid2<7> tw{tw_hi, tw_hi + 128};
+  // reciprocal steps 1/scale[c], c <= H (0 where the step is 0), once per CTA
+  float* rstep = reinterpret_cast<float*>(tw_hi + 256);
+  for (int c = threadIdx.x; c <= H; c += TPF * F) rstep[c] = scale[c] == 0.0f ? 0.0f : __frcp_rn(scale[c]);
   for (int jb = blockIdx.x * F; jb < J; jb += gridDim.x * F) {
     const int j = jb + f;
     const bool live = j < J;
@@ -226,14 +241,18 @@ k1_pfb_quant(const float* __restrict__ x, const float* __restrict__ window, int 
         rfft_post(sm, H, k, tw, yk, ym);
         const int km = H - k;
         if (k == 0) {
-          row[0] = pack2(quant4(yk.x, scale[0]), quant4(ym.x, scale[H]));
+          row[0] = pack2(quant4r(yk.x, scale[0], rstep[0]), quant4r(ym.x, scale[H], rstep[H]));
           if (srow) {
             srow[0] = make_float2(yk.x, 0.0f);
             srow[H] = make_float2(ym.x, 0.0f);
           }
         } else {
-          row[k] = pack2(quant4(yk.x, scale[k]), quant4(yk.y, scale[k]));
-          if (km != k) row[km] = pack2(quant4(ym.x, scale[km]), quant4(ym.y, scale[km]));
+          const float sk = scale[k], rk = rstep[k];
+          row[k] = pack2(quant4r(yk.x, sk, rk), quant4r(yk.y, sk, rk));
+          if (km != k) {
+            const float sm_ = scale[km], rm = rstep[km];
+            row[km] = pack2(quant4r(ym.x, sm_, rm), quant4r(ym.y, sm_, rm));
+          }
           if (srow) {
             srow[k] = yk;
             if (km != k) srow[km] = ym;
