@@ -24,8 +24,9 @@ struct Variant {
   int C, T, MAXR;
   const char* name;
 };
-constexpr Variant kVariants[] = {{4, 256, 32, "c4_t256_r32"}, {4, 256, 16, "c4_t256_r16"}, {2, 256, 32, "c2_t256_r32"}};
-constexpr int kNumVariants = 3;
+constexpr Variant kVariants[] = {{4, 256, 32, "c4_t256_r32"}, {4, 256, 16, "c4_t256_r16"}, {2, 256, 32, "c2_t256_r32"},
+                                 {8, 256, 32, "c8_t256_r32"}};
+constexpr int kNumVariants = 4;
 constexpr int kNumMClass = 5;  // M = 2048 .. 32768
 
 int mclass(int M) {
@@ -48,7 +49,8 @@ struct Plan {
   size_t off_Js = 0, off_Ms = 0, off_chirp_ptr = 0, off_bhat_ptr = 0;
   std::vector<size_t> off_chirp, off_bhat, off_d2;
   size_t total = 0;
-  int variant[kNumMClass] = {0, 0, 0, 0, 0};
+  // defaults = the autotuner's choice on the 256-stream batch (M = 2048 .. 32768)
+  int variant[kNumMClass] = {0, 2, 2, 0, 3};
   const void* prepared_ws = nullptr;
   int normalize = 1;
 };
@@ -104,6 +106,7 @@ namespace ipfb {
 cudaError_t kb3_launch_v0(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb3_launch_v1(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb3_launch_v2(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb3_launch_v3(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 }  // namespace ipfb
 
 namespace {
@@ -120,6 +123,7 @@ int launch_kb3(const Plan& P, char* ws, int cls, int v, cudaStream_t stream) {
     case 0: e = kb3_launch_v0(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
     case 1: e = kb3_launch_v1(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
     case 2: e = kb3_launch_v2(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
+    case 3: e = kb3_launch_v3(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
   }
   if (e != cudaSuccess) return fail(e, "kb3_columns");
   return IPFB_OK;

@@ -22,6 +22,10 @@ SHAPES = [(1024, 1031), (2048, 1500), (4096, 1024), (1024, 2310), (2048, 4099), 
           (2048, 3000), (1024, 8191)]
 
 
+# column-kernel variants (cluster size, threads, largest radix) and their cluster sizes
+VARIANTS = {"c4_t256_r32": 4, "c4_t256_r16": 4, "c2_t256_r32": 2, "c8_t256_r32": 8}
+
+
 def relrms(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
@@ -63,7 +67,7 @@ def test_batched_autotune_cache_and_graph_replay():
         lines = open(cache).read().split()
         assert len(lines) == 10
         names = {plan.variant(2048 << c) for c in range(5)}
-        assert names <= {"c4_t256_r32", "c4_t256_r16", "c2_t256_r32"}
+        assert names <= set(VARIANTS)
         # a plan that loads the cache picks the same variants
         plan2 = ipfb.BatchedPlan(streams, tune_cache=cache)
         for c in range(5):
@@ -89,6 +93,32 @@ def test_batched_autotune_cache_and_graph_replay():
     torch.cuda.synchronize()
     for (N, J), x, ref in zip(shapes, plan.x, refs):
         assert relrms(x.cpu().numpy(), ref) < 1e-4, (N, J)
+    plan.close()
+
+
+@pytest.mark.parametrize("name", sorted(VARIANTS))
+def test_batched_each_variant_matches_oracle(name):
+    # one stream per Bluestein length class M = 4096 .. 32768, every class forced to
+    # `name` through a tune cache (classes outside the variant's range M / C in
+    # [512, 8192] keep the default variant)
+    shapes = [(1024, 1031), (2048, 1500), (1024, 2310), (2048, 4099), (1024, 9000)]
+    streams, host = _streams(shapes, 700)
+    C = VARIANTS[name]
+    with tempfile.TemporaryDirectory() as d:
+        cache = os.path.join(d, "tune.txt")
+        with open(cache, "w") as f:
+            for c in range(5):
+                f.write(f"{2048 << c} {name}\n")
+        plan = ipfb.BatchedPlan(streams, tune_cache=cache)
+        for c in range(5):
+            M = 2048 << c
+            if 512 <= M // C <= 8192:
+                assert plan.variant(M) == name, M
+    xs = plan.run()
+    torch.cuda.synchronize()
+    refs = obatched.ipfb_batched(host)
+    for (N, J), x, ref in zip(shapes, xs, refs):
+        assert relrms(x.cpu().numpy(), ref) < 1e-4, (name, N, J)
     plan.close()
 
 
