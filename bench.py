@@ -631,6 +631,30 @@ def run_profile_case(lblock: int, nframes: int, reps: int):
     return 0
 
 
+def run_profile_batched(nstreams: int):
+    """The batched-streams configuration (first `nstreams` streams of the seeded
+    256-stream recipe) planned with the default variants and run once, for ncu
+    captures of the batched kernels."""
+    import torch
+    from paper_2608_23441_b300 import ipfb, synth
+    dev = torch.device("cuda", 0)
+    geoms = synth.batched_geometries(256, 3)[:nstreams]
+    streams = []
+    for i, (N, J) in enumerate(geoms):
+        x = synth.gaussian_stream_torch(N * J, 3 * 100003 + i, dev)
+        w = torch.from_numpy(ipfb.sinc_hamming_window(N, NTAP)).to(dev)
+        codes, scale, _ = ipfb.pfb_forward(x, w)
+        del x
+        streams.append({"codes": codes, "scale": scale, "window": w, "noise_level": 0.0141})
+    plan = ipfb.BatchedPlan(streams)
+    plan.prepare()
+    plan.run()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_batched": {"streams": nstreams, "samples": int(sum(N * J for N, J in geoms))}}))
+    plan.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -644,9 +668,13 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-streams timing")
     ap.add_argument("--profile-case", nargs=3, type=int, metavar=("LBLOCK", "NFRAMES", "REPS"),
                     help="run a smaller case of the pipeline (for ncu captures) and exit")
+    ap.add_argument("--profile-batched", type=int, metavar="NSTREAMS",
+                    help="plan and run the first NSTREAMS streams of the batched configuration once (for ncu)")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(*args.profile_case)
+    if args.profile_batched:
+        return run_profile_batched(args.profile_batched)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -281,20 +281,21 @@ template <int C, int S, int T, int MAXR>
 __global__ void __launch_bounds__(T, 2)
 kb3_columns(const BStream* __restrict__ streams, const BItem* __restrict__ items, int nitems, int* counter) {
   extern __shared__ float2 smem[];
-  __shared__ int slot;
+  (void)counter;
   int r = 0;
   if constexpr (C > 1) r = (int)cg::this_cluster().block_rank();
-  for (int guard = 0; guard < nitems + 1; ++guard) {
-    const int it = fetch_item_cluster<C>(counter, &slot, r);
-    if (it >= nitems) break;
+  // Static round-robin over the class's items (all of one M, so of nearly one cost;
+  // the host sorts them longest first): every CTA of a cluster walks the same item
+  // sequence, so no cluster barrier is spent on fetching work.  No barrier is needed
+  // between items either: an item's last remote shared-memory access precedes its
+  // last cluster barrier, and the next item's first one follows the next item's
+  // first cluster barrier.
+  const int ncl = (int)gridDim.x / C, cl = (int)blockIdx.x / C;
+  for (int it = cl; it < nitems; it += ncl) {
     const BItem item = items[it];
     const BStream& st = streams[item.s];
     if (st.M == C * S) column_item<C, S, T, MAXR>(st, item.a, smem, r);  // always true within a class
-    if constexpr (C > 1) {
-      cg::this_cluster().sync();
-    } else {
-      __syncthreads();
-    }
+    if constexpr (C == 1) __syncthreads();
   }
 }
 
