@@ -15,6 +15,25 @@ int resident_ctas(const void* kern, int threads, size_t smem) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess) return 0;
   return sms * per;
 }
+// resident CTAs over the GPU of a kernel that holds `tmem_cols` TMEM columns per CTA
+int resident_ctas_tmem(const void* kern, int threads, size_t smem, uint32_t tmem_cols) {
+  int dev = 0, sms = 0, regs_sm = 0, smem_sm = 0, rsv = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
+    return 0;
+  const int by_regs = regs_sm / (((fa.numRegs + 7) / 8 * 8) * threads);
+  const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + (size_t)rsv);
+  const int by_tmem = 512 / (int)tmem_cols;
+  const int by_threads = 2048 / threads;
+  int per = by_regs < by_smem ? by_regs : by_smem;
+  per = per < by_tmem ? per : by_tmem;
+  per = per < by_threads ? per : by_threads;
+  return sms * (per > 0 ? per : 1);
+}
 }  // namespace
 
 size_t net_pack_bytes() { return PACK_BYTES; }
@@ -33,7 +52,9 @@ cudaError_t launch_net_forward(const uint8_t* packed, const float* in, float* y,
   cudaError_t e = cudaFuncSetAttribute(k6_net_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long items = net_fwd_items(count ? max_slots : nslots_host, J);
-  const int res = resident_ctas((const void*)k6_net_forward, 256, smem);
+  // The occupancy query answers one CTA per SM for this kernel (it allocates tensor
+  // memory), but three fit: count them from its registers, shared memory and TMEM.
+  const int res = resident_ctas_tmem((const void*)k6_net_forward, 256, smem, kNetTmemCols);
   if (res <= 0) return cudaErrorInvalidConfiguration;
   const long long grid = items < res ? (items < 1 ? 1 : items) : res;
   k6_net_forward<<<(unsigned)grid, 256, smem, st>>>(packed, in, y, J, nslots_host, count, zero_other);

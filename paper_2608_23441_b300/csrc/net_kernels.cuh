@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace ipfb {
 namespace netk {
@@ -219,39 +220,77 @@ __device__ __forceinline__ void conv_out_warp(const __nv_bfloat16* A, const __nv
 // Work item = (slot, tile of FT outputs); persistent CTAs of 256 threads.
 // Rows: x0 i <-> p0 - 12 + i (264), a1 i <-> p0 - 8 + i (256, +8 zero rows),
 //       a2 i <-> p0 - 4 + i (256, first 248 used), y i <-> p0 + i (240).
+// Layers 1 and 3 run on mma.sync; layer 2 (90 % of the flops) on the fifth-generation
+// tensor cores: two M = 128 row blocks x N = 32 channels x K = 288 (9 taps x 32 input
+// channels) in 2 x 18 tcgen05.mma of K = 16, issued by one thread, accumulators in
+// 64 TMEM columns, read back by all eight warps (warp w: lane quarter w % 4, block
+// w / 4) for the bias + GELU epilogue.  Operands in shared memory as no-swizzle
+// K-major core matrices: a1 as [4 channel chunks][264 rows][8] (a tap is a 16-byte
+// row offset of the descriptor's start address), W2 as [36 k-chunks][32 co][8].
 // ---------------------------------------------------------------------------
 constexpr int FT = 240;
 constexpr int F_X0 = FT + 24;   // 264
 constexpr int F_A1 = FT + 16;   // 256 computed rows of a1
 constexpr int F_A2 = FT + 16;   // 256 computed rows of a2 (248 valid)
-constexpr size_t fwd_smem_bytes() {
-  return (size_t)NFWD_BF * 2 + 68 * 4 + (size_t)F_X0 * 4 + (size_t)(F_A1 + 8) * S32 * 2 + (size_t)F_A2 * S32 * 2;
-}
+constexpr int A1R = F_A1 + 8;   // a1 rows held (8 zero rows past the computed ones)
+// shared-memory map of the forward (bytes)
+constexpr size_t FO_W2C = 0;                                    // [36][32][8] bf16
+constexpr size_t FO_A1C = FO_W2C + 36 * 32 * 16;                // [4][A1R][8] bf16
+constexpr size_t FO_A2 = FO_A1C + 4 * (size_t)A1R * 16;         // [256][S32] bf16 (also layer-1 im2col)
+constexpr size_t FO_W1 = FO_A2 + (size_t)F_A2 * S32 * 2;        // [32][S32] bf16
+constexpr size_t FO_W3 = FO_W1 + 32 * S32 * 2;                  // [8][S288] bf16
+constexpr size_t FO_B = FO_W3 + 8 * S288 * 2;                   // 68 floats
+constexpr size_t FO_X0 = FO_B + 68 * 4;                         // F_X0 packed bf16 pairs
+constexpr size_t fwd_smem_bytes() { return FO_X0 + (size_t)F_X0 * 4; }
+static_assert(FO_A1C % 1024 == 0 && FO_A2 % 16 == 0 && FO_W1 % 16 == 0 && FO_W3 % 16 == 0, "alignment");
+constexpr uint32_t kNetTmemCols = 64;
+constexpr long long kNetMmaWait = 2000000000LL;  // SM clocks (~1 s)
 
 __global__ void __launch_bounds__(256)
 k6_net_forward(const uint8_t* __restrict__ packed, const float* __restrict__ in, float* __restrict__ y, int J,
                int nslots_host, const int* __restrict__ count, int* __restrict__ zero_other) {
-  extern __shared__ __align__(16) uint8_t smraw[];
-  __nv_bfloat16* wsm = reinterpret_cast<__nv_bfloat16*>(smraw);
-  float* bsm = reinterpret_cast<float*>(smraw + (size_t)NFWD_BF * 2);
-  uint32_t* x0s = reinterpret_cast<uint32_t*>(bsm + 68);
-  __nv_bfloat16* a1s = reinterpret_cast<__nv_bfloat16*>(x0s + F_X0);
-  __nv_bfloat16* a2s = a1s + (F_A1 + 8) * S32;  // also the layer-1 im2col
-  const __nv_bfloat16* W1 = wsm + PW1;
-  const __nv_bfloat16* W2 = wsm + PW2;
-  const __nv_bfloat16* W3 = wsm + PW3;
+  extern __shared__ __align__(1024) uint8_t smfwd[];
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ uint32_t tmem_slot;
+  __nv_bfloat16* w2c = reinterpret_cast<__nv_bfloat16*>(smfwd + FO_W2C);
+  __nv_bfloat16* a1c = reinterpret_cast<__nv_bfloat16*>(smfwd + FO_A1C);
+  __nv_bfloat16* a2s = reinterpret_cast<__nv_bfloat16*>(smfwd + FO_A2);
+  __nv_bfloat16* W1 = reinterpret_cast<__nv_bfloat16*>(smfwd + FO_W1);
+  __nv_bfloat16* W3 = reinterpret_cast<__nv_bfloat16*>(smfwd + FO_W3);
+  float* bsm = reinterpret_cast<float*>(smfwd + FO_B);
+  uint32_t* x0s = reinterpret_cast<uint32_t*>(smfwd + FO_X0);
 
   if (zero_other && blockIdx.x == 0 && threadIdx.x == 0) *zero_other = 0;
   const int nslots = count ? *count : nslots_host;
   const int ntile = (J + FT - 1) / FT;
   const long long nitems = (long long)nslots * ntile;
   if ((long long)blockIdx.x >= nitems) return;
-
-  load_pack(packed, wsm, bsm, NFWD_BF);
-  // the 8 rows past a1 (read by the unused a2 rows 248..255) stay zero
-  for (int i = threadIdx.x; i < 8 * S32 / 2; i += blockDim.x)
-    reinterpret_cast<uint32_t*>(a1s + F_A1 * S32)[i] = 0u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // weights: W1, W3 and the biases as packed; W2 regrouped into k-chunk core matrices
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(packed);
+    for (int i = threadIdx.x; i < 32 * S32 / 8; i += blockDim.x)
+      reinterpret_cast<uint4*>(W1)[i] = src[PW1 / 8 + i];
+    for (int i = threadIdx.x; i < 8 * S288 / 8; i += blockDim.x)
+      reinterpret_cast<uint4*>(W3)[i] = src[PW3 / 8 + i];
+    for (int i = threadIdx.x; i < 36 * 32; i += blockDim.x) {
+      const int kc = i >> 5, co = i & 31;
+      reinterpret_cast<uint4*>(w2c)[i] = src[(PW2 + co * S288) / 8 + kc];
+    }
+    const float* pb = reinterpret_cast<const float*>(packed + PACK_BIAS_OFF);
+    for (int i = threadIdx.x; i < 68; i += blockDim.x) bsm[i] = pb[i];
+    // the 8 rows past a1 in every channel chunk (read by the unused a2 rows) stay zero
+    for (int i = threadIdx.x; i < 4 * 8; i += blockDim.x)
+      reinterpret_cast<uint4*>(a1c)[(i >> 3) * A1R + F_A1 + (i & 7)] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (warp == 0) tc::alloc(smem_u32(&tmem_slot), kNetTmemCols);
+  if (threadIdx.x == 0) tc::mbar_init(smem_u32(&mma_bar));
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = tmem_slot;
+  uint32_t phase = 0;
 
   for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int slot = (int)(item / ntile), tile = (int)(item % ntile);
@@ -261,23 +300,56 @@ k6_net_forward(const uint8_t* __restrict__ packed, const float* __restrict__ in,
     __syncthreads();
     build_a1col(x0s, F_A1, a2s);
     __syncthreads();
-    // layer 1: m-tiles warp, warp + 8
+    // layer 1 (mma.sync): m-tiles warp, warp + 8, into the chunked a1
 #pragma unroll 1
     for (int mt = warp; mt < F_A1 / 16; mt += 8)
       conv_layer_warp<2, false>(a2s, S32, W1, S32, mt * 16, lane, [&](int r, int cc, float v0, float v1) {
         v0 = gelu_f(v0 + bsm[cc]);
         v1 = gelu_f(v1 + bsm[cc + 1]);
-        *reinterpret_cast<uint32_t*>(a1s + r * S32 + cc) = pack_bf2(v0, v1);
+        *reinterpret_cast<uint32_t*>(a1c + ((cc >> 3) * A1R + r) * 8 + (cc & 7)) = pack_bf2(v0, v1);
       });
+    tc::fence_smem_operands();
+    tc::fence_before();
     __syncthreads();
-    // layer 2
+    // layer 2 (tcgen05): one thread issues the 36 MMAs and commits them to mma_bar
+    if (threadIdx.x == 0) {
+      tc::fence_after();
+      const uint32_t a0 = smem_u32(a1c), b0 = smem_u32(w2c);
+      constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
 #pragma unroll 1
-    for (int mt = warp; mt < F_A2 / 16; mt += 8)
-      conv_layer_warp<18, true>(a1s, S32, W2, S288, mt * 16, lane, [&](int r, int cc, float v0, float v1) {
-        v0 = gelu_f(v0 + bsm[32 + cc]);
-        v1 = gelu_f(v1 + bsm[32 + cc + 1]);
-        *reinterpret_cast<uint32_t*>(a2s + r * S32 + cc) = pack_bf2(v0, v1);
-      });
+      for (int mb = 0; mb < 2; ++mb)
+#pragma unroll 1
+        for (int ks = 0; ks < 2 * KW; ++ks) {
+          const int t = ks >> 1, h = ks & 1;
+          const uint64_t ad = tc::desc(a0 + (uint32_t)((2 * h) * A1R + 128 * mb + t) * 16, A1R * 16, 128);
+          const uint64_t bd = tc::desc(b0 + (uint32_t)(2 * ks) * 32 * 16, 32 * 16, 128);
+          tc::mma(tbase + 32 * mb, ad, bd, idesc, ks > 0 ? 1u : 0u);
+        }
+      tc::commit(smem_u32(&mma_bar));
+    }
+    // one thread waits on the barrier; the others sleep in the block barrier below
+    bool late = false;
+    if (threadIdx.x == 0) late = !tc::mbar_wait(smem_u32(&mma_bar), phase, kNetMmaWait);
+    phase ^= 1;
+    if (__syncthreads_or(late)) {  // the accumulators never arrived: mark the slot's output, stop
+      if (threadIdx.x == 0) y[(size_t)slot * J + p0] = __int_as_float(0x7fc00000);
+      break;
+    }
+    tc::fence_after();
+    {
+      const int qd = warp & 3, mb = warp >> 2;
+      const int r = 128 * mb + 32 * qd + lane;
+      float v[32];
+      tc::ld32(tbase + ((uint32_t)(32 * qd) << 16) + 32 * mb, v);
+      uint32_t pk[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        pk[c] = pack_bf2(gelu_f(v[2 * c] + bsm[32 + 2 * c]), gelu_f(v[2 * c + 1] + bsm[33 + 2 * c]));
+      uint4* dst = reinterpret_cast<uint4*>(a2s + r * S32);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dst[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+    }
+    tc::fence_before();
     __syncthreads();
     // layer 3
     float* yo = y + (size_t)slot * J;
@@ -288,6 +360,9 @@ k6_net_forward(const uint8_t* __restrict__ packed, const float* __restrict__ in,
         if (p0 + r < J) yo[p0 + r] = v + b3;
       });
   }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::dealloc(tbase, kNetTmemCols);
 }
 
 // ---------------------------------------------------------------------------
