@@ -655,6 +655,23 @@ def run_profile_batched(nstreams: int):
     return 0
 
 
+def run_profile_net(nslots: int):
+    """One learned-preconditioner net forward over `nslots` columns of 8192 frames
+    (the ML workload's column length), seeded inputs and He-initialised weights, for
+    ncu captures of the net kernels."""
+    import torch
+    from paper_2608_23441_b300 import ipfb, precond_train
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device="cpu").manual_seed(5)
+    xin = torch.randn((nslots, 2, ML_NFRAMES), generator=g).to(dev)
+    xin[:, 1] = (xin[:, 1] > 1.0).float()
+    theta = torch.from_numpy(precond_train.init_theta(5, scale3=1.0)).to(dev)
+    y = ipfb.net_forward(theta, xin)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_net": {"slots": nslots, "frames": ML_NFRAMES, "y_rms": float(y.pow(2).mean().sqrt())}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -670,7 +687,11 @@ def main():
                     help="run a smaller case of the pipeline (for ncu captures) and exit")
     ap.add_argument("--profile-batched", type=int, metavar="NSTREAMS",
                     help="plan and run the first NSTREAMS streams of the batched configuration once (for ncu)")
+    ap.add_argument("--profile-net", type=int, metavar="NSLOTS",
+                    help="run one net forward over NSLOTS columns of 8192 frames (for ncu)")
     args = ap.parse_args()
+    if args.profile_net:
+        return run_profile_net(args.profile_net)
     if args.profile_case:
         return run_profile_case(*args.profile_case)
     if args.profile_batched:
