@@ -80,6 +80,45 @@ def decorrelate(d: np.ndarray, window: np.ndarray, noise_level: float,
     return np.real(np.fft.ifft(G * D, axis=0))
 
 
+def pinv_gain(W: np.ndarray, threshold: float) -> np.ndarray:
+    """Thresholded pseudo-inverse, one of the eigenvalue filters Sec. 3.2 allows on the
+    circulant eigenmodes: G = 1 / conj(W) where |W| >= threshold, 0 elsewhere."""
+    G = np.zeros(W.shape, dtype=np.complex128)
+    keep = np.abs(W) >= threshold
+    G[keep] = 1.0 / np.conj(W[keep])
+    return G
+
+
+def full_gain_from_half(gains_half: np.ndarray, nframes: int) -> np.ndarray:
+    """Caller-supplied gains [N, J/2 + 1] (modes k <= J/2 of every column) extended to
+    all J modes by G(J - k) = conj G(k), the symmetry that keeps the columns real.
+    Returns [J, N]."""
+    N, K = gains_half.shape
+    J = nframes
+    assert K == J // 2 + 1
+    G = np.zeros((J, N), dtype=np.complex128)
+    G[:K] = gains_half.T
+    k = np.arange(K, J)
+    G[k] = np.conj(gains_half.T[J - k])
+    return G
+
+
+def ipfb_filter(codes: np.ndarray, scale: np.ndarray, window: np.ndarray, threshold: float | None = None,
+                gains_half: np.ndarray | None = None) -> np.ndarray:
+    """Circulant inverse PFB with a general eigenvalue filter (Sec. 3.2): per column,
+    F d_n times G_n, then F^dagger (1/J); G is the thresholded pseudo-inverse
+    (pinv_gain) or caller-supplied gains (full_gain_from_half).  Returns x_hat [J*N]."""
+    p, N = window.shape
+    d = frames_from_spectra(dequantize(codes, scale), N)
+    J = d.shape[0]
+    if threshold is not None:
+        G = pinv_gain(eigenvalues(window, J), threshold)
+    else:
+        G = full_gain_from_half(np.asarray(gains_half, dtype=np.complex128), J)
+    D = np.fft.fft(d, axis=0)
+    return np.real(np.fft.ifft(G * D, axis=0)).reshape(-1)
+
+
 def ipfb_from_spectra(spectra: np.ndarray, window: np.ndarray, noise_level: float,
                       normalize: bool = True) -> np.ndarray:
     """Circulant (Wiener) inverse PFB of complex spectra [J, N/2+1]; returns x_hat [J*N]."""

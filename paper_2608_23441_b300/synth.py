@@ -107,6 +107,24 @@ def mask_from_chunks(nsamples: int, starts, length: int) -> np.ndarray:
     return m
 
 
+def saved_paths(lblock: int, fraction: float, every: int = 4) -> int:
+    """Number L of sub-filter paths to save every `every`-th sample of for a saved
+    fraction beta = L / (every * lblock) of the stream (Sec. 4.3), rounded to an even
+    count so that the paths sit symmetrically around lblock / 2."""
+    L = int(round(fraction * every * lblock / 2.0)) * 2
+    return max(2, min(L, lblock))
+
+
+def path_sample_mask(lblock: int, nframes: int, npaths: int, every: int = 4, phase: int = 0) -> np.ndarray:
+    """Byte mask (1 = saved sample) in time order [nframes * lblock]: every `every`-th
+    frame (frames j with j % every == phase) of the `npaths` sub-filter paths
+    n in [lblock/2 - npaths/2, lblock/2 + npaths/2), the saving scheme of Sec. 4.3."""
+    m = np.zeros((nframes, lblock), dtype=np.uint8)
+    n0 = lblock // 2 - npaths // 2
+    m[phase::every, n0:n0 + npaths] = 1
+    return m.reshape(-1)
+
+
 def batched_geometries(nstreams: int, seed: int, lblocks=(1024, 2048, 4096),
                        jmin: int = 1024, jmax: int = 16384):
     """Uneven stream shapes: lblock uniform over `lblocks`, nframes = round(exp(U(ln jmin,

@@ -194,3 +194,54 @@ def test_delta_at_channel_centre():
     wn = w / w.sum(axis=0, keepdims=True)
     d0 = ipfb.analytic_delta_wiener(wn, J, 1.0 / snr)[0]
     assert abs(d0 - 1.0 / (1.0 + snr)) < 1e-12
+
+
+# ----------------------------------------------------------------------------- general eigenvalue filters
+def test_pinv_threshold_zero_recovers_periodic_input():
+    # Sec. 3.2: with no mode dropped the thresholded pseudo-inverse is the exact inverse,
+    # which recovers unquantized circulant data to round-off.
+    N, J, p = 64, 128, 4
+    x = synth.gaussian_stream(N * J, 23)
+    w = pfb.sinc_hamming_window(N, p)
+    d = pfb.polyphase_sum(x, w)
+    D = np.fft.fft(d, axis=0)
+    G = ipfb.pinv_gain(ipfb.eigenvalues(w, J), 0.0)
+    xh = np.real(np.fft.ifft(G * D, axis=0)).reshape(-1)
+    assert np.linalg.norm(xh - x) / np.linalg.norm(x) < 1e-10
+
+
+def test_pinv_keeps_or_drops_a_pure_eigenmode():
+    # one real mode k of sub-stream n: kept exactly when |W_n(k)| >= threshold, removed otherwise
+    N, p, J = 16, 4, 64
+    w = pfb.sinc_hamming_window(N, p)
+    n, k = 8, 29
+    xcol = np.cos(2 * np.pi * k * np.arange(J) / J + 0.3)
+    X = np.zeros((J, N))
+    X[:, n] = xcol
+    d = pfb.polyphase_sum(X.reshape(-1), w)
+    D = np.fft.fft(d, axis=0)
+    Wk = abs(ipfb.eigenvalues(w, J)[k, n])
+    for thr, expect in ((0.5 * Wk, xcol), (2.0 * Wk, 0.0 * xcol)):
+        out = np.real(np.fft.ifft(ipfb.pinv_gain(ipfb.eigenvalues(w, J), thr) * D, axis=0))
+        assert np.allclose(out[:, n], expect, atol=1e-12)
+        assert np.abs(np.delete(out, n, axis=1)).max() < 1e-12
+
+
+def test_caller_gains_identity_and_scaled_inverse():
+    # G = 1 leaves the polyphase data d as it is; G = c / conj(W) on a pure mode returns c x
+    N, p, J = 32, 4, 64
+    codes = synth.random_code_bytes(J, N // 2, 31)
+    scale = synth.random_scale(N // 2 + 1, 32)
+    w = pfb.sinc_hamming_window(N, p)
+    ones = np.ones((N, J // 2 + 1), dtype=np.complex128)
+    d = ipfb.frames_from_spectra(pfb.dequantize(codes, scale), N)
+    assert np.allclose(ipfb.ipfb_filter(codes, scale, w, gains_half=ones), d.reshape(-1), atol=1e-12)
+    n, k, c = 5, 13, 0.7
+    xcol = np.cos(2 * np.pi * k * np.arange(J) / J - 1.1)
+    X = np.zeros((J, N))
+    X[:, n] = xcol
+    dm = pfb.polyphase_sum(X.reshape(-1), w)
+    W = ipfb.eigenvalues(w, J)
+    Gh = (c / np.conj(W[: J // 2 + 1])).T                       # [N, J/2+1]
+    out = np.real(np.fft.ifft(ipfb.full_gain_from_half(Gh, J) * np.fft.fft(dm, axis=0), axis=0))
+    assert np.allclose(out[:, n], c * xcol, atol=1e-12)

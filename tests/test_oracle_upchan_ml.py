@@ -119,3 +119,16 @@ def test_paper_protocol_wiener_start_improves_chi2():
 
     X25 = ml.ml_solve_d(d, w, sig2, mask, x, 1.0, "none", 0.0, 25, x0=x0)[0]
     assert chi2(X25) < chi2(x0)
+
+
+def test_path_sample_mask_fraction_and_layout():
+    # Sec. 4.3: saving every R-th sample of L of N sub-filter paths keeps beta = L / (R N)
+    N, J, R = 2048, 64, 4
+    for beta, L_expect in ((0.01, 82), (0.10, 820)):     # the paper's 82 ... 820 paths
+        L = synth.saved_paths(N, beta, R)
+        assert L == L_expect
+        m = synth.path_sample_mask(N, J, L, R).reshape(J, N)
+        assert abs(m.mean() - L / (R * N)) < 1e-15
+        cols = np.nonzero(m.any(axis=0))[0]
+        assert cols.size == L and cols[0] == N // 2 - L // 2 and cols[-1] == N // 2 + L // 2 - 1
+        assert np.array_equal(np.nonzero(m.any(axis=1))[0], np.arange(0, J, R))
