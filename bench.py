@@ -383,7 +383,44 @@ def run_ml(torch, ipfb, dev, reps=3, theta=None):
         del ws
     if theta is not None:
         out["learned_vs_plain_time"] = out["learned"]["ms"] / out["none"]["ms"]
+    out["paper_protocol"] = run_ml_paper_protocol(torch, ipfb, dev, codes, scale, w, prior, sig2, reps=reps)
     return out
+
+
+def run_ml_paper_protocol(torch, ipfb, dev, codes, scale, w, truth, sig2, reps=3, phi2=0.0141):
+    """Sec. 4.3 sample-saving protocol on the config-4 instance: every 4th sample of the
+    L central sub-filter paths saved (beta = L / (4 N) = 1 %, 3 %, 10 %), the Wiener
+    inverse as the initial guess, then 25 plain-CG iterations; timed as one step
+    (ipfb_wiener + ml_solve)."""
+    from paper_2608_23441_b300 import synth
+    N, J = ML_LBLOCK, ML_NFRAMES
+    g = ipfb.geom(N, NTAP, J)
+    ws = torch.empty(ipfb.workspace_size(g, ipfb.OP_ML), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    res = {"recipe": "every 4th frame of the L central sub-filter paths, Wiener start (phi^2 0.0141), "
+                     "25 plain-CG iterations"}
+    tn = float(torch.linalg.norm(truth))
+    for beta in (0.01, 0.03, 0.10):
+        L = synth.saved_paths(N, beta)
+        mask = torch.from_numpy(synth.path_sample_mask(N, J, L)).to(dev)
+
+        def step():
+            x0 = ipfb.ipfb_wiener(codes, scale, w, phi2)
+            x, _, _ = ipfb.ml_solve(codes, scale, w, sig2, mask, truth, tol=0.0, max_iter=25, x0=x0, workspace=ws)
+            return x0, x
+        step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            x0, x = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[f"beta_{beta:.2f}"] = {"paths": L, "ms": e0.elapsed_time(e1) / reps,
+                                   "rel_error_wiener_start": float(torch.linalg.norm(x0 - truth)) / tn,
+                                   "rel_error_after_25": float(torch.linalg.norm(x - truth)) / tn}
+    del ws
+    return res
 
 
 def run_batched(torch, ipfb, dev, reps=5, seed=3, nstreams=256):

@@ -163,6 +163,28 @@ int ipfb_wiener(const ipfb_geom* g, const uint8_t* codes, const float* scale, co
                 void* stream);
 
 /*
+ * ipfb_filter: the circulant inverse PFB of ipfb_wiener with another eigenvalue filter
+ * on the frame-axis modes (Sec. 3.2: the circulant form exposes every eigenmode, so
+ * any per-mode filter costs the same as the Wiener one).  Per column n and mode k
+ * the reconstruction multiplies the column spectrum by G_n(k):
+ *   mode IPFB_FILTER_THRESHOLD: thresholded pseudo-inverse, G = 1 / conj W_n(k) where
+ *     |W_n(k)| >= threshold (threshold >= 0), G = 0 elsewhere; threshold 0 is the
+ *     exact inverse.  |W|^2 below 1e-4 is evaluated in FP64, the keep-or-drop decision
+ *     included; above that it is decided in FP32.
+ *   mode IPFB_FILTER_GAINS: caller gains, a DEVICE array of complex float pairs
+ *     (re, im) laid out [N][J/2 + 1]: gains[n (J/2 + 1) + k] = G_n(k) for k <= J/2;
+ *     G_n(J - k) = conj G_n(k) (real output), 8-byte aligned.  The 1/J of the inverse
+ *     transform is applied by the library.
+ * codes, scale, window, x_out as for ipfb_wiener (same sizes, same workspace:
+ * ipfb_workspace_size(g, IPFB_OP_WIENER)).  Errors: IPFB_ERR_INVALID for an unknown
+ * mode, a negative or non-finite threshold, or a null / unaligned gains array.
+ */
+#define IPFB_FILTER_THRESHOLD 1
+#define IPFB_FILTER_GAINS 2
+int ipfb_filter(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window, int mode,
+                double threshold, const float* gains, float* x_out, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * Up-channelization (Sec. 4.3, re-channelization with frames `block` samples
  * long; read here as a plain real DFT of consecutive blocks, no window):
  *   X_b[c] = sum_{t<L} x[b L + t] exp(-2 pi i t c / L),  c <= L/2,

@@ -136,7 +136,8 @@ void column_split(int J, int* C, int* S) {
 
 int run_inverse_core(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
                      double noise_level, int normalize, float2* d2, int C, int S, cudaStream_t st,
-                     int out_block_major = 0) {
+                     int out_block_major = 0, int filter_mode = 0, double threshold = 0.0,
+                     const float2* gains = nullptr) {
   const int N = g->lblock, J = g->nframes, H = N / 2;
   {
     Stage t("k2_unpack_irfft", st);
@@ -150,6 +151,9 @@ int run_inverse_core(const ipfb_geom* g, const uint8_t* codes, const float* scal
   gp.J = J;
   gp.ntap = g->ntap;
   gp.out_block_major = out_block_major;
+  gp.mode = filter_mode;
+  gp.thresh2 = (float)(threshold * threshold);
+  gp.gains = gains;
   Stage t("k3_column_wiener", st);
   CK(launch_k3(C, S, d2, window, N, gp, st), "k3_column_wiener");
   t.done();
@@ -338,6 +342,34 @@ int ipfb_wiener(const ipfb_geom* g, const uint8_t* codes, const float* scale, co
   int C, S;
   column_split(g->nframes, &C, &S);
   rc = run_inverse_core(g, codes, scale, window, noise_level, normalize, d2, C, S, st);
+  if (rc) return rc;
+  Stage t("k_pairs_to_time", st);
+  CK(launch_pairs_to_time(d2, x_out, g->lblock, C, S, st), "k_pairs_to_time");
+  t.done();
+  return IPFB_OK;
+}
+
+int ipfb_filter(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window, int mode,
+                double threshold, const float* gains, float* x_out, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_geom(g, true);
+  if (rc) return rc;
+  if (!codes || !scale || !window || !x_out || misaligned16(codes)) return IPFB_ERR_INVALID;
+  if (mode == IPFB_FILTER_THRESHOLD) {
+    if (!(threshold >= 0.0) || !std::isfinite(threshold)) return IPFB_ERR_INVALID;
+  } else if (mode == IPFB_FILTER_GAINS) {
+    if (!gains || (reinterpret_cast<uintptr_t>(gains) & 7) != 0) return IPFB_ERR_INVALID;
+  } else {
+    return IPFB_ERR_INVALID;
+  }
+  size_t need = 0;
+  ipfb_workspace_size(g, IPFB_OP_WIENER, &need);
+  if (!ws || ws_bytes < need) return IPFB_ERR_WORKSPACE;
+  cudaStream_t st = as_stream(stream);
+  float2* d2 = reinterpret_cast<float2*>(ws);
+  int C, S;
+  column_split(g->nframes, &C, &S);
+  rc = run_inverse_core(g, codes, scale, window, 0.0, 0, d2, C, S, st, 0, mode, threshold,
+                        reinterpret_cast<const float2*>(gains));
   if (rc) return rc;
   Stage t("k_pairs_to_time", st);
   CK(launch_pairs_to_time(d2, x_out, g->lblock, C, S, st), "k_pairs_to_time");

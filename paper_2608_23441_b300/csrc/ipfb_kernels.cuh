@@ -182,6 +182,53 @@ __device__ __forceinline__ float2 gain_at(const float* taps, int k, float2 e1, c
   return make_float2(W.x * g, W.y * g);
 }
 
+// Filters other than Wiener (GainParams::mode 1, 2), for the generic-tap kernels:
+//   1: thresholded pseudo-inverse G = W / |W|^2 / J where |W|^2 >= thresh2, else 0
+//      (|W|^2 below kFp64Below is formed in FP64, decision included);
+//   2: caller gains G = gains[col][k] / J for k <= J/2, conj(gains[col][J - k]) / J above.
+static __device__ __noinline__ float2 pinv_gain_fp64(const float* taps, int ntap, int k, const GainParams& gp) {
+  double s, c;
+  sincospi(2.0 * (double)k / (double)gp.J, &s, &c);
+  double wx = 0.0, wy = 0.0;
+  for (int t = ntap - 1; t >= 0; --t) {
+    const double nx = wx * c + wy * s;
+    const double ny = wy * c - wx * s;
+    wx = nx + (double)taps[t];
+    wy = ny;
+  }
+  const double a2 = wx * wx + wy * wy;
+  if (!(a2 >= (double)gp.thresh2) || a2 == 0.0) return make_float2(0.0f, 0.0f);
+  const double g = (double)gp.invJ / a2;
+  return make_float2((float)(wx * g), (float)(wy * g));
+}
+
+template <int NT>
+__device__ __forceinline__ float2 filter_gain(const float* taps, int k, float2 e1, const GainParams& gp, int col) {
+  if constexpr (NT == 0) {
+    if (gp.mode == 1) {
+      float2 W = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int t = kMaxTaps - 1; t >= 0; --t) {
+        if (t < gp.ntap) {
+          W = cmul(W, e1);
+          W.x += taps[t];
+        }
+      }
+      const float a2 = fmaf(W.x, W.x, W.y * W.y);
+      if (a2 < kFp64Below) return pinv_gain_fp64(taps, gp.ntap, k, gp);
+      if (a2 < gp.thresh2) return make_float2(0.0f, 0.0f);
+      const float g = __fdividef(gp.invJ, a2);
+      return make_float2(W.x * g, W.y * g);
+    }
+    if (gp.mode == 2) {
+      const int half = gp.J / 2;
+      const float2 G = __ldg(gp.gains + (size_t)col * (half + 1) + (k <= half ? k : gp.J - k));
+      return make_float2(G.x * gp.invJ, (k <= half ? G.y : -G.y) * gp.invJ);
+    }
+  }
+  return gain_at<NT>(taps, k, e1, gp);
+}
+
 // Column-pair split, per-column gain, recombination for modes k and -k:
 //   A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i)      (spectra of columns a, b)
 //   Z'_k = Ga A + i Gb B,   Z'_-k = conj(Ga A) + i conj(Gb B)
@@ -314,7 +361,7 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
         if constexpr (NT > 0) {
           pair_gain<NT>(z0[ka], z1[C - 1 - ka], ta, tb, k, e1, gp);
         } else {
-          const float2 ga = gain_at<NT>(ta, k, e1, gp), gb = gain_at<NT>(tb, k, e1, gp);
+          const float2 ga = filter_gain<NT>(ta, k, e1, gp, 2 * p), gb = filter_gain<NT>(tb, k, e1, gp, 2 * p + 1);
           split_gain(z0[ka], z1[C - 1 - ka], ga, gb);
         }
       }
@@ -325,7 +372,7 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
         const int km = (C - ka) % C;
         const int k = S * ka;
         const float2 e1 = rotq<C, false>(make_float2(1.0f, 0.0f), ka);
-        const float2 ga = gain_at<NT>(ta, k, e1, gp), gb = gain_at<NT>(tb, k, e1, gp);
+        const float2 ga = filter_gain<NT>(ta, k, e1, gp, 2 * p), gb = filter_gain<NT>(tb, k, e1, gp, 2 * p + 1);
         float2 a = z0[ka], b = z0[km];
         split_gain(a, b, ga, gb);
         z0[ka] = a;
@@ -338,7 +385,7 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
         const int km = C - 1 - ka;
         const int k = kb0 + S * ka;
         const float2 e1 = rotq<C, false>(e0, ka);
-        const float2 ga = gain_at<NT>(ta, k, e1, gp), gb = gain_at<NT>(tb, k, e1, gp);
+        const float2 ga = filter_gain<NT>(ta, k, e1, gp, 2 * p), gb = filter_gain<NT>(tb, k, e1, gp, 2 * p + 1);
         float2 a = z0[ka], b = z0[km];
         split_gain(a, b, ga, gb);
         z0[ka] = a;

@@ -15,6 +15,11 @@ struct GainParams {
   int J;
   int ntap;
   int out_block_major;  // k3 output layout: 0 = the d2 residue runs, 1 = block-major (k4a input)
+  // eigenvalue filter: 0 = Wiener (phi2, gnorm); 1 = thresholded pseudo-inverse
+  // (|W|^2 >= thresh2 kept as 1 / conj W, else 0); 2 = caller gains [N][J/2 + 1]
+  int mode = 0;
+  float thresh2 = 0.0f;
+  const float2* gains = nullptr;
 };
 
 struct UpchanSrc {

@@ -36,6 +36,7 @@ class MLParams(ctypes.Structure):
 
 
 PRECOND = {"none": 0, "wiener": 1, "learned": 2}
+FILTER_THRESHOLD, FILTER_GAINS = 1, 2
 
 
 class StreamDesc(ctypes.Structure):
@@ -72,6 +73,7 @@ _SIGS = {
     "pfb_forward": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "pfb_quantize": (_I, [_I, _I, _P, _P, _P, _P]),
     "ipfb_wiener": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _D, _I, _P, _P, _SZ, _P]),
+    "ipfb_filter": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _I, _D, _P, _P, _P, _SZ, _P]),
     "upchannelize": (_I, [_P, _I64, _I64, _P, _P, _SZ, _P]),
     "ipfb_wiener_upchannelize": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _D, _I, _I, _P, _P, _P, _SZ, _P]),
     "ipfb_batched_plan": (_I, [ctypes.POINTER(StreamDesc), _I, _I, ctypes.c_char_p, ctypes.POINTER(_P),
@@ -254,6 +256,32 @@ def ipfb_wiener(codes, scale, window, noise_level: float, normalize: bool = True
     ws, wsb = _workspace(workspace_size(g, OP_WIENER), codes.device, workspace)
     _check("ipfb_wiener", lib().ipfb_wiener(ctypes.byref(g), _ptr(codes), _ptr(scale), _ptr(window),
                                             float(noise_level), int(bool(normalize)), _ptr(x), _ptr(ws), wsb,
+                                            _stream()))
+    return x
+
+
+def ipfb_filter(codes, scale, window, threshold: float | None = None, gains=None, out=None, workspace=None):
+    """Circulant inverse PFB with another eigenvalue filter (ipfb_filter): the
+    thresholded pseudo-inverse (threshold >= 0) or caller gains (complex64 [N, J/2+1],
+    G_n(k) for k <= J/2).  Exactly one of threshold / gains.  Returns x float32 [J*N]."""
+    torch = _torch()
+    if (threshold is None) == (gains is None):
+        raise ValueError("give exactly one of threshold, gains")
+    codes = _dev(codes, torch.uint8, "codes")
+    scale = _dev(scale, torch.float32, "scale")
+    window = _dev(window, torch.float32, "window")
+    p, N = window.shape
+    J = codes.shape[0]
+    g = geom(N, p, J)
+    if gains is not None:
+        gains = _dev(gains, torch.complex64, "gains")
+        if tuple(gains.shape) != (N, J // 2 + 1):
+            raise ValueError("gains must be [N, J/2 + 1]")
+    x = out if out is not None else torch.empty(J * N, dtype=torch.float32, device=codes.device)
+    ws, wsb = _workspace(workspace_size(g, OP_WIENER), codes.device, workspace)
+    mode = FILTER_THRESHOLD if threshold is not None else FILTER_GAINS
+    _check("ipfb_filter", lib().ipfb_filter(ctypes.byref(g), _ptr(codes), _ptr(scale), _ptr(window), mode,
+                                            float(threshold or 0.0), _ptr(gains), _ptr(x), _ptr(ws), wsb,
                                             _stream()))
     return x
 

@@ -115,6 +115,14 @@ def test_host_validation_rejects_before_launch():
     # code arrays are read with 16-byte loads: an unaligned start is refused
     odd = ctypes.c_void_p(0x1008)
     assert L.ipfb_wiener(G, odd, fake, fake, 0.01, 1, fake, fake, 1 << 30, None) == ipfb.ERR_INVALID
+    # general eigenvalue filters: mode, threshold and gains are checked on the host
+    assert L.ipfb_filter(G, fake, fake, fake, 7, 0.1, None, fake, fake, 1 << 30, None) == ipfb.ERR_INVALID
+    assert L.ipfb_filter(G, fake, fake, fake, ipfb.FILTER_THRESHOLD, -1.0, None, fake, fake, 1 << 30, None) \
+        == ipfb.ERR_INVALID
+    assert L.ipfb_filter(G, fake, fake, fake, ipfb.FILTER_GAINS, 0.0, None, fake, fake, 1 << 30, None) \
+        == ipfb.ERR_INVALID
+    assert L.ipfb_filter(G, fake, fake, fake, ipfb.FILTER_THRESHOLD, 0.1, None, fake, fake, 16, None) \
+        == ipfb.ERR_WORKSPACE
     # the up-channelizer's workspace is moved with 16-byte copies: 16-byte aligned
     assert L.ipfb_wiener_upchannelize(ctypes.byref(g_up), fake, fake, fake, 0.01, 1, 64, fake, None, odd,
                                       1 << 30, None) == ipfb.ERR_INVALID

@@ -237,3 +237,60 @@ def test_config1_small_wiener():
     # GPU forward on the same stream gives the same codes except at boundaries
     gc, gs, _ = ipfb.pfb_forward(cuda(x.astype(np.float32)), cuda(w.astype(np.float32)))
     assert np.mean(gc.cpu().numpy() != opfb.pfb_forward(x.astype(np.float32).astype(np.float64), w)[0]) < 2e-3
+
+
+# ----------------------------------------------------------------------------- general eigenvalue filters
+def _threshold_in_gap(absW, q):
+    """A threshold between two consecutive |W| values near quantile q, at least 2e-5
+    relative away from both: FP32 |W| is within ~1e-6 relative of FP64, so both sides
+    keep the same modes."""
+    v = np.unique(np.sort(absW.reshape(-1)))
+    i0 = int(q * (v.size - 1))
+    for i in range(i0, v.size - 1):
+        lo, hi = v[i], v[i + 1]
+        if hi - lo > 4e-5 * hi:
+            return 0.5 * (lo + hi)
+    raise AssertionError("no gap")
+
+
+@pytest.mark.parametrize("N,J,run", [(256, 512, 8192), (64, 2048, 512)])
+def test_filter_threshold_pinv_matches_oracle(N, J, run):
+    ipfb.set_max_column_run(run)
+    x = synth.stream_config(N, J, 61, ntones=3)
+    w = opfb.sinc_hamming_window(N, 4).astype(np.float32).astype(np.float64)
+    codes, scale, _ = opfb.pfb_forward(x, w)
+    absW = np.abs(oipfb.eigenvalues(w, J))
+    for q in (0.02, 0.2):
+        thr = _threshold_in_gap(absW, q)
+        got = ipfb.ipfb_filter(cuda(codes), cuda(scale), cuda(w.astype(np.float32)), threshold=thr)
+        ref = oipfb.ipfb_filter(codes, scale, w, threshold=thr)
+        assert relrms(got.cpu().numpy(), ref) < 1e-4, (q, thr)
+    # threshold 0 is the exact inverse
+    g0 = ipfb.ipfb_filter(cuda(codes), cuda(scale), cuda(w.astype(np.float32)), threshold=0.0)
+    e0 = ipfb.ipfb_wiener(cuda(codes), cuda(scale), cuda(w.astype(np.float32)), 0.0)
+    assert relrms(g0.cpu().numpy(), e0.cpu().numpy().astype(np.float64)) < 1e-6
+    ipfb.set_max_column_run(8192)
+
+
+@pytest.mark.parametrize("N,J,run", [(256, 512, 8192), (64, 2048, 512)])
+def test_filter_caller_gains_matches_oracle(N, J, run):
+    ipfb.set_max_column_run(run)
+    x = synth.stream_config(N, J, 62, ntones=3)
+    w = opfb.sinc_hamming_window(N, 4).astype(np.float32).astype(np.float64)
+    codes, scale, _ = opfb.pfb_forward(x, w)
+    rng = np.random.default_rng(63)
+    G = (rng.uniform(0.2, 1.5, size=(N, J // 2 + 1)) * np.exp(1j * rng.uniform(-np.pi, np.pi, size=(N, J // 2 + 1))))
+    G[:, 0] = G[:, 0].real                    # DC and Nyquist gains real, as for a real filter
+    G[:, -1] = G[:, -1].real
+    Gd = torch.from_numpy(G.astype(np.complex64)).cuda()
+    got = ipfb.ipfb_filter(cuda(codes), cuda(scale), cuda(w.astype(np.float32)), gains=Gd)
+    ref = oipfb.ipfb_filter(codes, scale, w, gains_half=G.astype(np.complex64).astype(np.complex128))
+    assert relrms(got.cpu().numpy(), ref) < 1e-4
+    # the Wiener gains given as caller gains reproduce ipfb_wiener
+    phi2 = 0.014
+    Gw = oipfb.gain(oipfb.eigenvalues(w, J), phi2, True)[: J // 2 + 1].T
+    gw = ipfb.ipfb_filter(cuda(codes), cuda(scale), cuda(w.astype(np.float32)),
+                          gains=torch.from_numpy(np.ascontiguousarray(Gw).astype(np.complex64)).cuda())
+    ew = ipfb.ipfb_wiener(cuda(codes), cuda(scale), cuda(w.astype(np.float32)), phi2)
+    assert relrms(gw.cpu().numpy(), ew.cpu().numpy().astype(np.float64)) < 1e-5
+    ipfb.set_max_column_run(8192)
