@@ -132,3 +132,20 @@ def test_path_sample_mask_fraction_and_layout():
         cols = np.nonzero(m.any(axis=0))[0]
         assert cols.size == L and cols[0] == N // 2 - L // 2 and cols[-1] == N // 2 + L // 2 - 1
         assert np.array_equal(np.nonzero(m.any(axis=1))[0], np.arange(0, J, R))
+
+
+def test_pfb_upchannelize_reduces_to_block_dft_and_matches_pfb():
+    # one tap of unit weight is the plain block DFT; p taps are the forward PFB of
+    # Eq. pfb with the frame length N replaced by L
+    L, nb = 256, 12
+    x = synth.gaussian_stream(L * nb + 37, 71)
+    assert np.allclose(upchan.pfb_upchannelize(x, np.ones((1, L))), upchan.upchannelize(x, L), atol=1e-10)
+    w = pfb.sinc_hamming_window(L, 4)
+    ref = pfb.pfb_spectra(x[:L * nb], w, periodic=True)
+    assert np.allclose(upchan.pfb_upchannelize(x, w), ref, atol=1e-9)
+    # a tone at the centre of fine channel c0 stays in c0 (the flat PFB passband)
+    c0 = 40
+    t = np.arange(L * nb)
+    X = upchan.pfb_upchannelize(np.cos(2 * np.pi * c0 * t / L), w)
+    pw = np.mean(np.abs(X) ** 2, axis=0)
+    assert pw[c0] > 1e3 * np.delete(pw, c0).max()
