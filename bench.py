@@ -390,15 +390,15 @@ def run_ml(torch, ipfb, dev, reps=3, theta=None):
 def run_ml_paper_protocol(torch, ipfb, dev, codes, scale, w, truth, sig2, reps=3, phi2=0.0141):
     """Sec. 4.3 sample-saving protocol on the config-4 instance: every 4th sample of the
     L central sub-filter paths saved (beta = L / (4 N) = 1 %, 3 %, 10 %), the Wiener
-    inverse as the initial guess, then 25 plain-CG iterations; timed as one step
-    (ipfb_wiener + ml_solve)."""
+    inverse as the initial guess, then 25 plain-CG iterations of Eq. chi squared with
+    unit weights on both terms; timed as one step (ipfb_wiener + ml_solve)."""
     from paper_2608_23441_b300 import synth
     N, J = ML_LBLOCK, ML_NFRAMES
     g = ipfb.geom(N, NTAP, J)
     ws = torch.empty(ipfb.workspace_size(g, ipfb.OP_ML), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     res = {"recipe": "every 4th frame of the L central sub-filter paths, Wiener start (phi^2 0.0141), "
-                     "25 plain-CG iterations"}
+                     "25 plain-CG iterations, unit weights on the data and prior terms (prior weight 1/sigma^2)"}
     tn = float(torch.linalg.norm(truth))
     for beta in (0.01, 0.03, 0.10):
         L = synth.saved_paths(N, beta)
@@ -406,7 +406,8 @@ def run_ml_paper_protocol(torch, ipfb, dev, codes, scale, w, truth, sig2, reps=3
 
         def step():
             x0 = ipfb.ipfb_wiener(codes, scale, w, phi2)
-            x, _, _ = ipfb.ml_solve(codes, scale, w, sig2, mask, truth, tol=0.0, max_iter=25, x0=x0, workspace=ws)
+            x, _, _ = ipfb.ml_solve(codes, scale, w, sig2, mask, truth, prior_weight=1.0 / sig2, tol=0.0,
+                                    max_iter=25, x0=x0, workspace=ws)
             return x0, x
         step()
         torch.cuda.synchronize()

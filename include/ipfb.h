@@ -196,6 +196,19 @@ int upchannelize(const float* x, int64_t nsamples, int64_t block, float* out, vo
                  size_t ws_bytes, void* stream);
 
 /*
+ * Windowed re-channelization (Sec. 4.3: the inverted stream "channelized again using
+ * a PFB with 64-times longer frame size"): a PFB with frames L = block samples long
+ * and p = ntap taps, periodic over the nb = floor(nsamples / L) blocks:
+ *   s_b[t] = sum_{r<p} window[r L + t] x[((b + r) mod nb) L + t],   X_b = rfft_L(s_b).
+ * x: float [nsamples] time order; window: float [p][L] (e.g. ipfb_sinc_hamming_window
+ * with lblock = L); out: float2 [nb][L/2 + 1].  L: power of two, 1024 <= L <= 262144;
+ * 1 <= ntap <= 64.  Workspace: nb * L floats (the summed blocks).  x, window and ws
+ * must start on a 16-byte boundary.
+ */
+int upchannelize_pfb(const float* x, int64_t nsamples, int64_t block, int ntap, const float* window, float* out,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/*
  * ipfb_wiener followed by upchannelize with block = upfactor * lblock, without
  * a round trip of the reconstructed stream through time order.  x_out (time
  * order) is optional (NULL = not written).  out: float2 [J/upfactor][L/2 + 1].

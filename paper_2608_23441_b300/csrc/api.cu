@@ -392,6 +392,30 @@ int upchannelize(const float* x, int64_t nsamples, int64_t block, float* out, vo
   return IPFB_OK;
 }
 
+int upchannelize_pfb(const float* x, int64_t nsamples, int64_t block, int ntap, const float* window, float* out,
+                     void* ws, size_t ws_bytes, void* stream) {
+  if (!x || !window || !out || nsamples < 0 || block < 2 || ntap < 1 || ntap > 64) return IPFB_ERR_INVALID;
+  if (misaligned16(x) || misaligned16(window)) return IPFB_ERR_INVALID;
+  if (!is_pow2(block) || block < 1024 || block > 262144) return IPFB_ERR_UNSUPPORTED;
+  const long long nb = nsamples / block;
+  if (nb == 0) return IPFB_OK;
+  const size_t need = (size_t)nb * (size_t)block * sizeof(float);
+  if (!ws || ws_bytes < need) return IPFB_ERR_WORKSPACE;
+  if (misaligned16(ws)) return IPFB_ERR_INVALID;
+  cudaStream_t st = as_stream(stream);
+  float* xs = reinterpret_cast<float*>(ws);
+  {
+    Stage t("k_block_polyphase", st);
+    CK(launch_block_polyphase(x, window, (int)block, ntap, nb, xs, st), "k_block_polyphase");
+    t.done();
+  }
+  UpchanSrc src{xs, nullptr, 0, 0, 0};
+  Stage t("k4_upchan", st);
+  CK(launch_upchan(src, (int)block, nb, reinterpret_cast<float2*>(out), nullptr, st), "k4_upchan");
+  t.done();
+  return IPFB_OK;
+}
+
 int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
                              double noise_level, int normalize, int upfactor, float* out, float* x_out, void* ws,
                              size_t ws_bytes, void* stream) {

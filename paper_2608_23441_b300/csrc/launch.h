@@ -59,6 +59,8 @@ struct MLParams {
 cudaError_t launch_k5(int J, const float2* d2, float2* x2, const uint8_t* mask, const float* prior,
                       const float* window, int N, const MLParams& mp, int* iters, float* resid, cudaStream_t st);
 cudaError_t launch_time_to_pairs(const float* x, float2* x2, int N, int J, cudaStream_t st);
+cudaError_t launch_block_polyphase(const float* x, const float* w, int L, int ntap, long long nb, float* xs,
+                                   cudaStream_t st);
 cudaError_t launch_upchan(const UpchanSrc& src, int L, long long nblocks, float2* out, float* x_out,
                           cudaStream_t st);
 // Two-pass up-channelizer of the column-pair scratch (k4a: d2 -> W, then k4b: W ->

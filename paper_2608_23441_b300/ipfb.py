@@ -75,6 +75,7 @@ _SIGS = {
     "ipfb_wiener": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _D, _I, _P, _P, _SZ, _P]),
     "ipfb_filter": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _I, _D, _P, _P, _P, _SZ, _P]),
     "upchannelize": (_I, [_P, _I64, _I64, _P, _P, _SZ, _P]),
+    "upchannelize_pfb": (_I, [_P, _I64, _I64, _I, _P, _P, _P, _SZ, _P]),
     "ipfb_wiener_upchannelize": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _D, _I, _I, _P, _P, _P, _SZ, _P]),
     "ipfb_batched_plan": (_I, [ctypes.POINTER(StreamDesc), _I, _I, ctypes.c_char_p, ctypes.POINTER(_P),
                                ctypes.POINTER(_SZ)]),
@@ -295,6 +296,23 @@ def upchannelize(x, block: int, out=None):
     if out is None:
         out = torch.empty((nb, L // 2 + 1), dtype=torch.complex64, device=x.device)
     _check("upchannelize", lib().upchannelize(_ptr(x), x.numel(), L, _ptr(out), None, 0, _stream()))
+    return out
+
+
+def upchannelize_pfb(x, window, out=None, workspace=None):
+    """Windowed re-channelization (upchannelize_pfb): a PFB with frames L =
+    window.shape[1] long and window.shape[0] taps over x float32 [T] (CUDA).
+    Returns complex64 [T // L, L/2 + 1]."""
+    torch = _torch()
+    x = _dev(x, torch.float32, "x")
+    window = _dev(window, torch.float32, "window")
+    p, L = window.shape
+    nb = x.numel() // L
+    if out is None:
+        out = torch.empty((nb, L // 2 + 1), dtype=torch.complex64, device=x.device)
+    ws, wsb = _workspace(max(1, nb * L * 4), x.device, workspace)
+    _check("upchannelize_pfb", lib().upchannelize_pfb(_ptr(x), x.numel(), L, p, _ptr(window), _ptr(out), _ptr(ws),
+                                                      wsb, _stream()))
     return out
 
 

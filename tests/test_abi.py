@@ -115,6 +115,10 @@ def test_host_validation_rejects_before_launch():
     # code arrays are read with 16-byte loads: an unaligned start is refused
     odd = ctypes.c_void_p(0x1008)
     assert L.ipfb_wiener(G, odd, fake, fake, 0.01, 1, fake, fake, 1 << 30, None) == ipfb.ERR_INVALID
+    # the windowed re-channelizer: taps, block size and workspace are checked on the host
+    assert L.upchannelize_pfb(fake, 1 << 20, 4096, 0, fake, fake, fake, 1 << 30, None) == ipfb.ERR_INVALID
+    assert L.upchannelize_pfb(fake, 1 << 20, 3000, 4, fake, fake, fake, 1 << 30, None) == ipfb.ERR_UNSUPPORTED
+    assert L.upchannelize_pfb(fake, 1 << 20, 4096, 4, fake, fake, fake, 16, None) == ipfb.ERR_WORKSPACE
     # general eigenvalue filters: mode, threshold and gains are checked on the host
     assert L.ipfb_filter(G, fake, fake, fake, 7, 0.1, None, fake, fake, 1 << 30, None) == ipfb.ERR_INVALID
     assert L.ipfb_filter(G, fake, fake, fake, ipfb.FILTER_THRESHOLD, -1.0, None, fake, fake, 1 << 30, None) \

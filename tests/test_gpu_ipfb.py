@@ -294,3 +294,14 @@ def test_filter_caller_gains_matches_oracle(N, J, run):
     ew = ipfb.ipfb_wiener(cuda(codes), cuda(scale), cuda(w.astype(np.float32)), phi2)
     assert relrms(gw.cpu().numpy(), ew.cpu().numpy().astype(np.float64)) < 1e-5
     ipfb.set_max_column_run(8192)
+
+
+@pytest.mark.parametrize("L,nb,p", [(4096, 9, 4), (1024, 5, 1), (131072, 3, 4)])
+def test_upchannelize_pfb_matches_oracle(L, nb, p):
+    # the windowed re-channelizer (a PFB with frames L long, p taps, periodic over blocks)
+    x = synth.gaussian_stream(L * nb + 123, 81).astype(np.float32)
+    w = opfb.sinc_hamming_window(L, p).astype(np.float32) if p > 1 else np.ones((1, L), np.float32)
+    got = ipfb.upchannelize_pfb(cuda(x), cuda(w))
+    ref = oup.pfb_upchannelize(x.astype(np.float64), w.astype(np.float64))
+    assert got.shape == ref.shape
+    assert relrms(got.cpu().numpy(), ref) < 1e-5
