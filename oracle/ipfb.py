@@ -119,6 +119,35 @@ def ipfb_filter(codes: np.ndarray, scale: np.ndarray, window: np.ndarray, thresh
     return np.real(np.fft.ifft(G * D, axis=0)).reshape(-1)
 
 
+def stream_chunks(nspec: int, chunk: int, margin: int):
+    """Chunk starts of the overlap-save inverse: chunks of `chunk` spectra stepping by
+    S = chunk - 2 margin, the last one aligned to the end of the run; the chunk at
+    `start` contributes frames [start + margin, start + margin + S) (the last one its
+    frames up to nspec - margin)."""
+    S = chunk - 2 * margin
+    assert S > 0 and nspec >= chunk
+    starts = list(range(0, nspec - chunk + 1, S))
+    if starts[-1] + chunk < nspec:
+        starts.append(nspec - chunk)
+    return starts
+
+
+def ipfb_wiener_stream(codes: np.ndarray, scale: np.ndarray, window: np.ndarray, noise_level: float,
+                       chunk: int, margin: int, normalize: bool = True) -> np.ndarray:
+    """Overlap-save circulant inverse of a long run of spectra (App. C: the Wiener
+    decorrelation kernels are short, so a chunk inverted as if periodic is exact up to
+    the kernel's tail beyond `margin` frames from its edges): every chunk of `chunk`
+    spectra is inverted with ipfb_wiener and its frames margin .. chunk - margin kept.
+    Returns frames [margin, nspec - margin) in time order, [(nspec - 2 margin) * N]."""
+    p, N = window.shape
+    nspec = codes.shape[0]
+    out = np.zeros((nspec - 2 * margin, N))
+    for st in stream_chunks(nspec, chunk, margin):
+        xc = ipfb_wiener(codes[st:st + chunk], scale, window, noise_level, normalize).reshape(chunk, N)
+        out[st:st + chunk - 2 * margin] = xc[margin:chunk - margin]
+    return out.reshape(-1)
+
+
 def ipfb_from_spectra(spectra: np.ndarray, window: np.ndarray, noise_level: float,
                       normalize: bool = True) -> np.ndarray:
     """Circulant (Wiener) inverse PFB of complex spectra [J, N/2+1]; returns x_hat [J*N]."""

@@ -245,3 +245,35 @@ def test_caller_gains_identity_and_scaled_inverse():
     Gh = (c / np.conj(W[: J // 2 + 1])).T                       # [N, J/2+1]
     out = np.real(np.fft.ifft(ipfb.full_gain_from_half(Gh, J) * np.fft.fft(dm, axis=0), axis=0))
     assert np.allclose(out[:, n], c * xcol, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- overlap-save inverse
+def test_stream_chunks_cover_the_interior_once():
+    for nspec, chunk, margin in ((1000, 256, 32), (256, 256, 0), (300, 128, 16)):
+        starts = ipfb.stream_chunks(nspec, chunk, margin)
+        covered = np.zeros(nspec, dtype=int)
+        S = chunk - 2 * margin
+        for k, st in enumerate(starts):
+            covered[st + margin:st + chunk - margin] += 1
+        assert np.all(covered[margin:nspec - margin] >= 1)
+        assert starts[0] == 0 and starts[-1] + chunk == nspec
+
+
+def test_stream_inverse_converges_to_the_global_inverse():
+    # App. C: the Wiener kernels decay within tens of frames, so the overlap-save inverse
+    # of a periodic run approaches the run's global circulant inverse as the margin grows;
+    # one chunk over the whole run with no margin is the global inverse itself
+    N, p, J = 64, 4, 1024
+    x = synth.gaussian_stream(N * J, 91)
+    w = pfb.sinc_hamming_window(N, p)
+    codes, scale, _ = pfb.pfb_forward(x, w)
+    phi2 = 0.0141
+    ref = ipfb.ipfb_wiener(codes, scale, w, phi2).reshape(J, N)
+    assert np.allclose(ipfb.ipfb_wiener_stream(codes, scale, w, phi2, J, 0), ref.reshape(-1))
+    errs = []
+    for margin in (4, 16, 64, 112):
+        got = ipfb.ipfb_wiener_stream(codes, scale, w, phi2, 256, margin).reshape(-1, N)
+        want = ref[margin:J - margin]
+        errs.append(np.sqrt(np.mean((got - want) ** 2) / np.mean(want ** 2)))
+    assert all(b < a for a, b in zip(errs[:-1], errs[1:])), errs
+    assert errs[-1] < 1e-6, errs
