@@ -387,6 +387,30 @@ def run_ml(torch, ipfb, dev, reps=3, theta=None):
     return out
 
 
+def run_stream(torch, ipfb, dev, codes, scale, w, phi2, chunk=8192, margin=128, reps=3):
+    """Overlap-save Wiener inverse of the 65536-spectrum run in chunks of 8192 with a
+    128-frame margin (ipfb_wiener_stream), against the one-block inverse of the run."""
+    N = LBLOCK
+    out = torch.empty((NFRAMES - 2 * margin) * N, dtype=torch.float32, device=dev)
+    g = ipfb.geom(N, NTAP, chunk)
+    ws = torch.empty(ipfb.workspace_size(g, ipfb.OP_WIENER_STREAM), dtype=torch.uint8, device=dev)
+    ipfb.ipfb_wiener_stream(codes, scale, w, phi2, chunk, margin, out=out, workspace=ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        ipfb.ipfb_wiener_stream(codes, scale, w, phi2, chunk, margin, out=out, workspace=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    full = ipfb.ipfb_wiener(codes, scale, w, phi2)
+    ref = full[margin * N:(NFRAMES - margin) * N]
+    rel = float(torch.linalg.norm(out - ref) / torch.linalg.norm(ref))
+    del ws, full
+    return {"chunk": chunk, "margin": margin, "ms": ms, "gsas": out.numel() / (ms * 1e-3) / 1e9,
+            "rel_diff_to_one_block_inverse": rel}
+
+
 def run_ml_paper_protocol(torch, ipfb, dev, codes, scale, w, truth, sig2, reps=3, phi2=0.0141):
     """Sec. 4.3 sample-saving protocol on the config-4 instance: every 4th sample of the
     L central sub-filter paths saved (beta = L / (4 N) = 1 %, 3 %, 10 %), the Wiener
@@ -633,6 +657,7 @@ def run_ours(args):
                                            for k, (t, c) in fstages.items()}},
         "clocks": clk.summary(),
     }
+    result["stages"]["stream_overlap_save"] = run_stream(torch, ipfb, dev, codes, scale, w, phi2)
     if not args.no_ml:
         theta, tinfo = (None, None) if args.no_learned else train_learned(torch, dev)
         result["ml"] = run_ml(torch, ipfb, dev, theta=theta)

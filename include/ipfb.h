@@ -54,6 +54,7 @@ extern "C" {
 #define IPFB_OP_ML 4
 #define IPFB_OP_ML_LEARNED 5 /* ipfb_ml_solve with precond = 2        */
 #define IPFB_OP_ML_PAIRS 6   /* ipfb_ml_training_pairs                 */
+#define IPFB_OP_WIENER_STREAM 7 /* ipfb_wiener_stream (nframes = chunk) */
 
 typedef struct {
   int lblock;   /* N: power of two, 32 <= N <= 16384                              */
@@ -194,6 +195,24 @@ int ipfb_filter(const ipfb_geom* g, const uint8_t* codes, const float* scale, co
  */
 int upchannelize(const float* x, int64_t nsamples, int64_t block, float* out, void* ws,
                  size_t ws_bytes, void* stream);
+
+/*
+ * ipfb_wiener_stream: overlap-save inverse of a run of nspec spectra longer than one
+ * circulant block (App. C: the Wiener decorrelation kernels are tens of frames long,
+ * so a chunk inverted as if periodic is exact up to the kernel's tail beyond the
+ * margin).  g->nframes is the chunk length J (power of two); chunks of J spectra step
+ * by S = J - 2 margin, the last one aligned to the end of the run; each is inverted
+ * as ipfb_wiener does and its frames margin .. J - margin are kept.
+ * codes: uint8 [nspec][N/2] (16-byte aligned; N/2 a multiple of 16), scale: float
+ * [N/2 + 1] of the whole run, window: float [p][N]; x_out: float
+ * [(nspec - 2 margin) N], frames margin .. nspec - margin - 1 in time order.
+ * 0 <= margin, J - 2 margin >= 1, nspec >= J.  The first and last `margin` frames
+ * of the run have no context on one side and are not produced.
+ * Workspace: ipfb_workspace_size(g, IPFB_OP_WIENER_STREAM), 16-byte aligned.
+ */
+int ipfb_wiener_stream(const ipfb_geom* g, int64_t nspec, const uint8_t* codes, const float* scale,
+                       const float* window, double noise_level, int normalize, int margin, float* x_out, void* ws,
+                       size_t ws_bytes, void* stream);
 
 /*
  * Windowed re-channelization (Sec. 4.3: the inverted stream "channelized again using

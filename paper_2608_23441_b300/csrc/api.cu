@@ -254,6 +254,12 @@ int ipfb_workspace_size(const ipfb_geom* g, int op, size_t* bytes) {
       // the up-channelizer's two passes keep their intermediate in a second buffer
       *bytes = (size_t)g->nframes * (size_t)g->lblock * sizeof(float) * (op == IPFB_OP_WIENER_UPCHAN ? 2 : 1);
       return IPFB_OK;
+    case IPFB_OP_WIENER_STREAM:
+      rc = check_geom(g, true);
+      if (rc) return rc;
+      // the chunk's column-pair scratch, then the chunk's time-order output
+      *bytes = 2 * al256((size_t)g->nframes * (size_t)g->lblock * sizeof(float));
+      return IPFB_OK;
     case IPFB_OP_ML:
       rc = check_geom(g, true);
       if (rc) return rc;
@@ -389,6 +395,46 @@ int upchannelize(const float* x, int64_t nsamples, int64_t block, float* out, vo
   Stage t("k4_upchan", as_stream(stream));
   CK(launch_upchan(src, (int)block, nb, reinterpret_cast<float2*>(out), nullptr, as_stream(stream)), "k4_upchan");
   t.done();
+  return IPFB_OK;
+}
+
+int ipfb_wiener_stream(const ipfb_geom* g, int64_t nspec, const uint8_t* codes, const float* scale,
+                       const float* window, double noise_level, int normalize, int margin, float* x_out, void* ws,
+                       size_t ws_bytes, void* stream) {
+  int rc = check_geom(g, true);
+  if (rc) return rc;
+  if (!codes || !scale || !window || !x_out || misaligned16(codes)) return IPFB_ERR_INVALID;
+  if ((rc = check_noise(noise_level))) return rc;
+  const int N = g->lblock, J = g->nframes;
+  if (margin < 0 || J - 2 * margin < 1 || nspec < J) return IPFB_ERR_INVALID;
+  if (((size_t)N / 2) % 16 != 0) return IPFB_ERR_UNSUPPORTED;  // chunk starts must stay 16-byte aligned
+  size_t need = 0;
+  ipfb_workspace_size(g, IPFB_OP_WIENER_STREAM, &need);
+  if (!ws || ws_bytes < need) return IPFB_ERR_WORKSPACE;
+  if (misaligned16(ws)) return IPFB_ERR_INVALID;
+  cudaStream_t st = as_stream(stream);
+  size_t wiener_bytes = 0;
+  ipfb_workspace_size(g, IPFB_OP_WIENER, &wiener_bytes);
+  float2* d2 = reinterpret_cast<float2*>(ws);
+  float* xc = reinterpret_cast<float*>(static_cast<char*>(ws) + al256(wiener_bytes));
+  int C, S;
+  column_split(J, &C, &S);
+  const long long step = J - 2 * margin;
+  long long start = 0;
+  while (true) {
+    const bool last = start + J >= nspec;
+    if (last) start = nspec - J;
+    rc = run_inverse_core(g, codes + (size_t)start * (N / 2), scale, window, noise_level, normalize, d2, C, S, st);
+    if (rc) return rc;
+    CK(launch_pairs_to_time(d2, xc, N, C, S, st), "k_pairs_to_time");
+    // frames margin .. J - margin of this chunk are frames start + margin .. of the run,
+    // stored from x_out[(start) N] (x_out begins at frame `margin`)
+    CK(cudaMemcpyAsync(x_out + (size_t)start * N, xc + (size_t)margin * N, (size_t)step * N * sizeof(float),
+                       cudaMemcpyDeviceToDevice, st),
+       "cudaMemcpyAsync");
+    if (last) break;
+    start += step;
+  }
   return IPFB_OK;
 }
 

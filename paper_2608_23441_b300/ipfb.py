@@ -21,6 +21,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "ipfb.h")
 OK = 0
 ERR_INVALID, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA = -1, -2, -3, -4, -5, -6
 OP_FORWARD, OP_WIENER, OP_WIENER_UPCHAN, OP_ML, OP_ML_LEARNED, OP_ML_PAIRS = 1, 2, 3, 4, 5, 6
+OP_WIENER_STREAM = 7
 NET_FORWARD, NET_GRAD = 1, 2
 NET_NPARAMS = 10145
 
@@ -74,6 +75,7 @@ _SIGS = {
     "pfb_quantize": (_I, [_I, _I, _P, _P, _P, _P]),
     "ipfb_wiener": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _D, _I, _P, _P, _SZ, _P]),
     "ipfb_filter": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _I, _D, _P, _P, _P, _SZ, _P]),
+    "ipfb_wiener_stream": (_I, [ctypes.POINTER(Geom), _I64, _P, _P, _P, _D, _I, _I, _P, _P, _SZ, _P]),
     "upchannelize": (_I, [_P, _I64, _I64, _P, _P, _SZ, _P]),
     "upchannelize_pfb": (_I, [_P, _I64, _I64, _I, _P, _P, _P, _SZ, _P]),
     "ipfb_wiener_upchannelize": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _D, _I, _I, _P, _P, _P, _SZ, _P]),
@@ -297,6 +299,27 @@ def upchannelize(x, block: int, out=None):
         out = torch.empty((nb, L // 2 + 1), dtype=torch.complex64, device=x.device)
     _check("upchannelize", lib().upchannelize(_ptr(x), x.numel(), L, _ptr(out), None, 0, _stream()))
     return out
+
+
+def ipfb_wiener_stream(codes, scale, window, noise_level: float, chunk: int, margin: int, normalize: bool = True,
+                       out=None, workspace=None):
+    """Overlap-save Wiener inverse of a long run of spectra (ipfb_wiener_stream):
+    chunks of `chunk` spectra, `margin` frames dropped at each chunk edge.  codes uint8
+    [nspec, N/2]; returns x float32 [(nspec - 2 margin) * N], frames margin ..
+    nspec - margin - 1."""
+    torch = _torch()
+    codes = _dev(codes, torch.uint8, "codes")
+    scale = _dev(scale, torch.float32, "scale")
+    window = _dev(window, torch.float32, "window")
+    p, N = window.shape
+    nspec = codes.shape[0]
+    g = geom(N, p, int(chunk))
+    x = out if out is not None else torch.empty((nspec - 2 * margin) * N, dtype=torch.float32, device=codes.device)
+    ws, wsb = _workspace(workspace_size(g, OP_WIENER_STREAM), codes.device, workspace)
+    _check("ipfb_wiener_stream", lib().ipfb_wiener_stream(ctypes.byref(g), int(nspec), _ptr(codes), _ptr(scale),
+                                                          _ptr(window), float(noise_level), int(bool(normalize)),
+                                                          int(margin), _ptr(x), _ptr(ws), wsb, _stream()))
+    return x
 
 
 def upchannelize_pfb(x, window, out=None, workspace=None):

@@ -30,6 +30,7 @@ def test_workspace_sizes():
     assert ipfb.workspace_size(g, ipfb.OP_WIENER) == 65536 * 4096 * 4
     assert ipfb.workspace_size(g, ipfb.OP_WIENER_UPCHAN) == 2 * 65536 * 4096 * 4
     assert ipfb.workspace_size(g, ipfb.OP_FORWARD) == 2 * 2049 * 8
+    assert ipfb.workspace_size(ipfb.geom(2048, 4, 8192), ipfb.OP_WIENER_STREAM) == 2 * 8192 * 2048 * 4
     with pytest.raises(ipfb.IpfbError) as e:
         ipfb.workspace_size(ipfb.geom(4096, 4, 65537), ipfb.OP_WIENER)
     assert e.value.rc == ipfb.ERR_UNSUPPORTED
@@ -115,6 +116,14 @@ def test_host_validation_rejects_before_launch():
     # code arrays are read with 16-byte loads: an unaligned start is refused
     odd = ctypes.c_void_p(0x1008)
     assert L.ipfb_wiener(G, odd, fake, fake, 0.01, 1, fake, fake, 1 << 30, None) == ipfb.ERR_INVALID
+    # the overlap-save inverse: margin, run length and workspace are checked on the host
+    g_s = ipfb.geom(256, 4, 64)
+    assert L.ipfb_wiener_stream(ctypes.byref(g_s), 1000, fake, fake, fake, 0.01, 1, 32, fake, fake, 1 << 30,
+                                None) == ipfb.ERR_INVALID          # 64 - 2 * 32 < 1
+    assert L.ipfb_wiener_stream(ctypes.byref(g_s), 32, fake, fake, fake, 0.01, 1, 8, fake, fake, 1 << 30,
+                                None) == ipfb.ERR_INVALID          # run shorter than one chunk
+    assert L.ipfb_wiener_stream(ctypes.byref(g_s), 1000, fake, fake, fake, 0.01, 1, 8, fake, fake, 16,
+                                None) == ipfb.ERR_WORKSPACE
     # the windowed re-channelizer: taps, block size and workspace are checked on the host
     assert L.upchannelize_pfb(fake, 1 << 20, 4096, 0, fake, fake, fake, 1 << 30, None) == ipfb.ERR_INVALID
     assert L.upchannelize_pfb(fake, 1 << 20, 3000, 4, fake, fake, fake, 1 << 30, None) == ipfb.ERR_UNSUPPORTED

@@ -305,3 +305,29 @@ def test_upchannelize_pfb_matches_oracle(L, nb, p):
     ref = oup.pfb_upchannelize(x.astype(np.float64), w.astype(np.float64))
     assert got.shape == ref.shape
     assert relrms(got.cpu().numpy(), ref) < 1e-5
+
+
+# ----------------------------------------------------------------------------- overlap-save inverse
+@pytest.mark.parametrize("N,nspec,chunk,margin", [(256, 2000, 512, 64), (64, 4096, 1024, 112), (128, 1024, 1024, 0)])
+def test_wiener_stream_matches_oracle(N, nspec, chunk, margin):
+    x = synth.stream_config(N, nspec, 95, ntones=3)
+    w = opfb.sinc_hamming_window(N, 4).astype(np.float32).astype(np.float64)
+    codes, scale, _ = opfb.pfb_forward(x, w)
+    got = ipfb.ipfb_wiener_stream(cuda(codes), cuda(scale), cuda(w.astype(np.float32)), 0.014, chunk, margin)
+    ref = oipfb.ipfb_wiener_stream(codes, scale, w, 0.014, chunk, margin)
+    assert got.shape[0] == ref.shape[0] == (nspec - 2 * margin) * N
+    assert relrms(got.cpu().numpy(), ref) < 1e-4
+
+
+def test_wiener_stream_approaches_the_global_inverse():
+    # a periodic run of 4096 spectra: chunks of 1024 with a 112-frame margin agree with
+    # the run's global circulant inverse to the round-off of the FP32 path
+    N, J = 64, 4096
+    x = synth.stream_config(N, J, 96)
+    w = opfb.sinc_hamming_window(N, 4).astype(np.float32)
+    codes, scale, _ = opfb.pfb_forward(x, w.astype(np.float64))
+    wg = cuda(w)
+    full = ipfb.ipfb_wiener(cuda(codes), cuda(scale), wg, 0.014).cpu().numpy().reshape(J, N)
+    m = 112
+    got = ipfb.ipfb_wiener_stream(cuda(codes), cuda(scale), wg, 0.014, 1024, m).cpu().numpy().reshape(-1, N)
+    assert relrms(got, full[m:J - m].astype(np.float64)) < 1e-5
