@@ -6,7 +6,7 @@
 //   z2 = conv(a1, w2) + b2   (32 -> 32)                     a2 = GELU(z2)
 //   y  = conv(a2, w3) + b3   (32 -> 1)
 // conv(x, w)[co, j] = sum_{ci, t} w[co, ci, t] x[ci, (j + t - 4) mod J]  (cross-correlation),
-// GELU(x) = x Phi(x) = 0.5 x (1 + erf(x / sqrt 2)).
+// GELU(x) = x Phi(x) = 0.5 x (1 + erf(x / sqrt 2)), Phi the standard normal CDF.
 // Parameters theta (FP32 master copy) are laid out w1[32][2][9], b1[32],
 // w2[32][32][9], b2[32], w3[1][32][9], b3[1]: 10145 values.
 //
@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "gelu_poly.cuh"
 #include "tcgen05.cuh"
 
 namespace ipfb {
@@ -44,10 +45,70 @@ constexpr int NFWD_BF = PW2T;                       // forward needs W1, W2, W3
 constexpr size_t PACK_BIAS_OFF = (size_t)NPACK_BF * 2;  // bytes; FP32 b1[32] b2[32] b3[1] pad[3]
 constexpr size_t PACK_BYTES = PACK_BIAS_OFF + 68 * sizeof(float);
 
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
-// d/dx x Phi(x) = Phi(x) + x phi(x)
-__device__ __forceinline__ float gelu_grad_f(float x) {
-  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+// ---- GELU, two values at a time on the paired FP32 pipe (fma.rn.f32x2 / mul.rn.f32x2).
+// With a = |x| and Q(a) = 1 - Phi(a) the upper normal tail,
+//   GELU(x) = max(x, 0) - a Q(a),   Q(a) = exp(-a^2 / 2) R(a),   R(a) = erfcx(a / sqrt 2) / 2,
+// R a polynomial on [0, kGeluClamp] (gelu_poly.cuh; the FP32 result is within 3e-7
+// absolute of x Phi(x)), the Gaussian factor one hardware exp2; and
+//   GELU'(x) = Phi(x) + x phi(x) = (x >= 0 ? 1 - Q(a) : Q(a)) + x exp(-x^2 / 2) / sqrt(2 pi).
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_splat(float c) { return f2_pack(c, c); }
+__device__ __forceinline__ float ex2_fast(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Q(|x0|), Q(|x1|) and the Gaussian factors exp(-x^2 / 2)
+__device__ __forceinline__ void normal_tail2(float x0, float x1, float& q0, float& q1, float& e0, float& e1) {
+  const float a0 = fabsf(x0), a1 = fabsf(x1);
+  const uint64_t t = f2_pack(fminf(a0, kGeluClamp), fminf(a1, kGeluClamp));
+  uint64_t r = f2_fma(f2_splat(gelu_r(kGeluDeg)), t, f2_splat(gelu_r(kGeluDeg - 1)));
+#pragma unroll
+  for (int k = kGeluDeg - 2; k >= 0; --k) r = f2_fma(r, t, f2_splat(gelu_r(k)));
+  constexpr float kHalfLog2e = 0.72134752044448170f;  // exp(-a^2 / 2) = 2^(-a^2 log2(e) / 2)
+  const uint64_t aa = f2_pack(a0, a1);
+  float s0, s1;
+  f2_unpack(f2_mul(f2_mul(aa, aa), f2_splat(-kHalfLog2e)), s0, s1);
+  e0 = ex2_fast(s0);
+  e1 = ex2_fast(s1);
+  f2_unpack(f2_mul(f2_pack(e0, e1), r), q0, q1);
+}
+
+// x <- GELU(x) for two values
+__device__ __forceinline__ void gelu2(float& x0, float& x1) {
+  float q0, q1, e0, e1;
+  normal_tail2(x0, x1, q0, q1, e0, e1);
+  f2_unpack(f2_fma(f2_pack(-fabsf(x0), -fabsf(x1)), f2_pack(q0, q1), f2_pack(fmaxf(x0, 0.0f), fmaxf(x1, 0.0f))),
+            x0, x1);
+}
+
+// GELU (g) and GELU' (d) of two values
+__device__ __forceinline__ void gelu2_grad(float x0, float x1, float& g0, float& g1, float& d0, float& d1) {
+  float q0, q1, e0, e1;
+  normal_tail2(x0, x1, q0, q1, e0, e1);
+  g0 = fmaf(-fabsf(x0), q0, fmaxf(x0, 0.0f));
+  g1 = fmaf(-fabsf(x1), q1, fmaxf(x1, 0.0f));
+  constexpr float kInvSqrt2Pi = 0.39894228040143268f;
+  d0 = fmaf(x0 * kInvSqrt2Pi, e0, x0 >= 0.0f ? 1.0f - q0 : q0);
+  d1 = fmaf(x1 * kInvSqrt2Pi, e1, x1 >= 0.0f ? 1.0f - q1 : q1);
 }
 
 __device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
@@ -304,8 +365,9 @@ k6_net_forward(const uint8_t* __restrict__ packed, const float* __restrict__ in,
 #pragma unroll 1
     for (int mt = warp; mt < F_A1 / 16; mt += 8)
       conv_layer_warp<2, false>(a2s, S32, W1, S32, mt * 16, lane, [&](int r, int cc, float v0, float v1) {
-        v0 = gelu_f(v0 + bsm[cc]);
-        v1 = gelu_f(v1 + bsm[cc + 1]);
+        v0 += bsm[cc];
+        v1 += bsm[cc + 1];
+        gelu2(v0, v1);
         *reinterpret_cast<uint32_t*>(a1c + ((cc >> 3) * A1R + r) * 8 + (cc & 7)) = pack_bf2(v0, v1);
       });
     tc::fence_smem_operands();
@@ -343,8 +405,11 @@ k6_net_forward(const uint8_t* __restrict__ packed, const float* __restrict__ in,
       tc::ld32(tbase + ((uint32_t)(32 * qd) << 16) + 32 * mb, v);
       uint32_t pk[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c)
-        pk[c] = pack_bf2(gelu_f(v[2 * c] + bsm[32 + 2 * c]), gelu_f(v[2 * c + 1] + bsm[33 + 2 * c]));
+      for (int c = 0; c < 16; ++c) {
+        float g0 = v[2 * c] + bsm[32 + 2 * c], g1 = v[2 * c + 1] + bsm[33 + 2 * c];
+        gelu2(g0, g1);
+        pk[c] = pack_bf2(g0, g1);
+      }
       uint4* dst = reinterpret_cast<uint4*>(a2s + r * S32);
 #pragma unroll
       for (int c = 0; c < 4; ++c) dst[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
@@ -441,11 +506,13 @@ k6_net_backward(const uint8_t* __restrict__ packed, const float* __restrict__ in
         v0 += bsm[cc];
         v1 += bsm[cc + 1];
         // a1 row r <-> dz1 row r - 16
+        float g0, g1, d0, d1;
+        gelu2_grad(v0, v1, g0, g1, d0, d1);
         if (r >= 16 && r < 16 + BT) {
-          gp1[(r - 16) * GP_STRIDE + cc] = gelu_grad_f(v0);
-          gp1[(r - 16) * GP_STRIDE + cc + 1] = gelu_grad_f(v1);
+          gp1[(r - 16) * GP_STRIDE + cc] = d0;
+          gp1[(r - 16) * GP_STRIDE + cc + 1] = d1;
         }
-        *reinterpret_cast<uint32_t*>(a1s + r * S32 + cc) = pack_bf2(gelu_f(v0), gelu_f(v1));
+        *reinterpret_cast<uint32_t*>(a1s + r * S32 + cc) = pack_bf2(g0, g1);
       });
     __syncthreads();
 #pragma unroll 1
@@ -454,11 +521,13 @@ k6_net_backward(const uint8_t* __restrict__ packed, const float* __restrict__ in
         v0 += bsm[32 + cc];
         v1 += bsm[32 + cc + 1];
         // a2 row r <-> dz2 row r - 8
+        float g0, g1, d0, d1;
+        gelu2_grad(v0, v1, g0, g1, d0, d1);
         if (r >= 8 && r < 8 + B_DZ2) {
-          gp2[(r - 8) * GP_STRIDE + cc] = gelu_grad_f(v0);
-          gp2[(r - 8) * GP_STRIDE + cc + 1] = gelu_grad_f(v1);
+          gp2[(r - 8) * GP_STRIDE + cc] = d0;
+          gp2[(r - 8) * GP_STRIDE + cc + 1] = d1;
         }
-        *reinterpret_cast<uint32_t*>(a2s + r * S32 + cc) = pack_bf2(gelu_f(v0), gelu_f(v1));
+        *reinterpret_cast<uint32_t*>(a2s + r * S32 + cc) = pack_bf2(g0, g1);
       });
     __syncthreads();
     float loss_part = 0.0f;
