@@ -17,8 +17,20 @@ namespace ipfb {
 // ----------------------------------------------------------------------------
 // complex float2 arithmetic
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// complex add / subtract on the paired FP32 pipe (add.rn.f32x2: both halves in one
+// instruction, IEEE round-to-nearest as the scalar forms)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  float2 r;
+  asm("{\n .reg .b64 ta, tb, td;\n mov.b64 ta, {%2, %3};\n mov.b64 tb, {%4, %5};\n add.rn.f32x2 td, ta, tb;\n mov.b64 {%0, %1}, td;\n}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  float2 r;
+  asm("{\n .reg .b64 ta, tb, td;\n mov.b64 ta, {%2, %3};\n mov.b64 tb, {%4, %5};\n sub.rn.f32x2 td, ta, tb;\n mov.b64 {%0, %1}, td;\n}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
