@@ -10,7 +10,12 @@
 // net input of the columns still active) and the net forward over the requests.
 // Requests are compacted: a column that is still active takes the next free slot
 // of the request buffer (atomic counter), so the net runs over active columns only.
-// All vectors are FP32 in the column-pair layout [P][J] (column 2p in .x, 2p+1 in .y).
+// All vectors are FP32 column pairs (column 2p in .x, 2p+1 in .y).  Thread t of pair
+// p works on frames t EPT .. t EPT + EPT - 1 (the stencil reads its neighbours in
+// shared memory), so the iteration vectors X, R, P, Z, U are stored lane-interleaved:
+// element e of thread t at p J + e T + t, which makes every warp access one contiguous
+// run.  X enters (initial guess) and leaves (k5_fcg_finish) in frame order [P][J];
+// the net's inputs and outputs stay in frame order [slot][J], moved as float4.
 #pragma once
 
 #include "ml_kernels.cuh"
@@ -98,15 +103,20 @@ __device__ __forceinline__ void fcg_request(const float2 (&r)[J / T], float2 (&u
   slot_a = sflag[0];
   slot_b = sflag[1];
   const float ia = 1.0f / s_a, ib = 1.0f / s_b;
+  static_assert(EPT % 4 == 0, "float4 rows");
+  auto mk = [&](int bit) { return ((mbits >> bit) & 1u) ? 1.0f : 0.0f; };
 #pragma unroll
-  for (int e = 0; e < EPT; ++e) {
+  for (int q = 0; q < EPT / 4; ++q) {
+    const int e = 4 * q;
     if (slot_a >= 0) {
-      netin[((size_t)slot_a * 2) * J + j0 + e] = u[e].x * ia;
-      netin[((size_t)slot_a * 2 + 1) * J + j0 + e] = ((mbits >> e) & 1u) ? 1.0f : 0.0f;
+      float4* row = reinterpret_cast<float4*>(netin + ((size_t)slot_a * 2) * J + j0);
+      row[q] = make_float4(u[e].x * ia, u[e + 1].x * ia, u[e + 2].x * ia, u[e + 3].x * ia);
+      row[J / 4 + q] = make_float4(mk(e), mk(e + 1), mk(e + 2), mk(e + 3));
     }
     if (slot_b >= 0) {
-      netin[((size_t)slot_b * 2) * J + j0 + e] = u[e].y * ib;
-      netin[((size_t)slot_b * 2 + 1) * J + j0 + e] = ((mbits >> (e + 16)) & 1u) ? 1.0f : 0.0f;
+      float4* row = reinterpret_cast<float4*>(netin + ((size_t)slot_b * 2) * J + j0);
+      row[q] = make_float4(u[e].y * ib, u[e + 1].y * ib, u[e + 2].y * ib, u[e + 3].y * ib);
+      row[J / 4 + q] = make_float4(mk(e + 16), mk(e + 17), mk(e + 18), mk(e + 19));
     }
   }
 }
@@ -138,7 +148,7 @@ k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, fl
   int* sflag = reinterpret_cast<int*>(part + (T / 32) * 4);
 
   const int tid = threadIdx.x, p = blockIdx.x, j0 = tid * EPT;
-  const size_t vb = (size_t)p * J + j0;
+  const size_t vb = (size_t)p * J + tid;  // element e of this thread at vb + e T
   FcgCol sa = {}, sb = {};
   if (phase != 0) {
     sa = cs[2 * p];
@@ -164,18 +174,21 @@ k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, fl
     sb.bnorm = res[1] > 0.0 ? sqrtf((float)res[1]) : 1.0f;
     sa.lam_m = mp.lam * (float)(res[2] / (double)J);
     sb.lam_m = mp.lam * (float)(res[3] / (double)J);
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      const float2 x0 = mp.use_x0 ? X[vb + e] : make_float2(0.0f, 0.0f);
-      sm_p[pidx(j0 + e)] = x0;
-      if (!mp.use_x0) X[vb + e] = x0;
-    }
     if (mp.use_x0) {
+      // the initial guess arrives in frame order: coalesced into shared memory, then
+      // stored back lane-interleaved (every read of X precedes the barrier)
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) sm_p[pidx(tid + i * T)] = X[(size_t)p * J + tid + i * T];
       __syncthreads();
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) X[vb + (size_t)e * T] = sm_p[pidx(j0 + e)];
       float2 v[WIN];
       load_window<J, T, RMAX>(sm_p, j0, v);
 #pragma unroll
       for (int e = 0; e < EPT; ++e) r[e] = csub(r[e], apply_A_at<EPT, RMAX>(v, a, mbits, mp.lam, e));
+    } else {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) X[vb + (size_t)e * T] = make_float2(0.0f, 0.0f);
     }
     float q2[2] = {0.0f, 0.0f};
 #pragma unroll
@@ -192,25 +205,32 @@ k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, fl
     sa.rz = sb.rz = 0.0;
     sa.slot = sb.slot = -1;
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) R[vb + e] = r[e];
+    for (int e = 0; e < EPT; ++e) R[vb + (size_t)e * T] = r[e];
   } else {
     mbits = load_mbits<EPT>(mask, N, p, j0);
     const bool aa = sa.active, ab = sb.active;
     float2 z[EPT];
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      r[e] = R[vb + e];
-      const float2 u = U[vb + e];
-      const float ya = aa ? Y[(size_t)sa.slot * J + j0 + e] : 0.0f;
-      const float yb = ab ? Y[(size_t)sb.slot * J + j0 + e] : 0.0f;
-      z[e] = make_float2(aa ? fmaf(sa.s, ya, u.x) : 0.0f, ab ? fmaf(sb.s, yb, u.y) : 0.0f);
+    for (int q = 0; q < EPT / 4; ++q) {
+      const float4 va = aa ? reinterpret_cast<const float4*>(Y + (size_t)sa.slot * J + j0)[q]
+                           : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      const float4 vb4 = ab ? reinterpret_cast<const float4*>(Y + (size_t)sb.slot * J + j0)[q]
+                            : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      const float ya[4] = {va.x, va.y, va.z, va.w}, yb[4] = {vb4.x, vb4.y, vb4.z, vb4.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int e = 4 * q + i;
+        r[e] = R[vb + (size_t)e * T];
+        const float2 u = U[vb + (size_t)e * T];
+        z[e] = make_float2(aa ? fmaf(sa.s, ya[i], u.x) : 0.0f, ab ? fmaf(sb.s, yb[i], u.y) : 0.0f);
+      }
     }
     // r.z_new (and r.z_old for the Polak-Ribiere beta)
     float q[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     float2 zo[EPT];
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
-      zo[e] = phase == 2 ? Z[vb + e] : make_float2(0.0f, 0.0f);
+      zo[e] = phase == 2 ? Z[vb + (size_t)e * T] : make_float2(0.0f, 0.0f);
       q[0] = fmaf(r[e].x, z[e].x, q[0]);
       q[1] = fmaf(r[e].y, z[e].y, q[1]);
       q[2] = fmaf(r[e].x, zo[e].x, q[2]);
@@ -226,14 +246,14 @@ k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, fl
     if (ab) sb.rz = res[1];
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
-      float2 pe = phase == 2 ? Pv[vb + e] : make_float2(0.0f, 0.0f);
+      float2 pe = phase == 2 ? Pv[vb + (size_t)e * T] : make_float2(0.0f, 0.0f);
       if (aa) pe.x = fmaf(be_a, pe.x, z[e].x);
       if (ab) pe.y = fmaf(be_b, pe.y, z[e].y);
       if (!aa) pe.x = 0.0f;
       if (!ab) pe.y = 0.0f;
       sm_p[pidx(j0 + e)] = pe;
-      Pv[vb + e] = pe;
-      Z[vb + e] = z[e];
+      Pv[vb + (size_t)e * T] = pe;
+      Z[vb + (size_t)e * T] = z[e];
     }
     __syncthreads();
     float2 pw[WIN];
@@ -252,13 +272,13 @@ k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, fl
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
       const float2 ape = apply_A_at<EPT, RMAX>(pw, a, mbits, mp.lam, e);
-      float2 xe = X[vb + e];
+      float2 xe = X[vb + (size_t)e * T];
       xe.x = fmaf(al_a, pw[e + RMAX].x, xe.x);
       xe.y = fmaf(al_b, pw[e + RMAX].y, xe.y);
-      X[vb + e] = xe;
+      X[vb + (size_t)e * T] = xe;
       r[e].x = fmaf(-al_a, ape.x, r[e].x);
       r[e].y = fmaf(-al_b, ape.y, r[e].y);
-      R[vb + e] = r[e];
+      R[vb + (size_t)e * T] = r[e];
       q3[0] = fmaf(r[e].x, r[e].x, q3[0]);
       q3[1] = fmaf(r[e].y, r[e].y, q3[1]);
     }
@@ -282,7 +302,7 @@ k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, fl
     fcg_request<J, T, NT>(r, u, sm_f, part, res, sflag, ta, tb, mp.ntap, mp.inv_s2, sa.lam_m, sb.lam_m, act, mbits,
                           counter, netin, s_a, s_b, sl_a, sl_b);
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) U[vb + e] = u[e];
+    for (int e = 0; e < EPT; ++e) U[vb + (size_t)e * T] = u[e];
     sa.s = s_a;
     sb.s = s_b;
     sa.slot = sl_a;
@@ -299,7 +319,7 @@ k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, fl
 // True residual b - A x (FP32 operator, FP64 norms) and the per-column outputs.
 template <int J, int T, int RMAX, int NT>
 __global__ void __launch_bounds__(T, 1)
-k5_fcg_finish(const float2* __restrict__ d2, const float2* __restrict__ X, const uint8_t* __restrict__ mask,
+k5_fcg_finish(const float2* __restrict__ d2, float2* __restrict__ X, const uint8_t* __restrict__ mask,
               const float* __restrict__ prior, const float* __restrict__ window, int N, MLParams mp,
               const FcgCol* __restrict__ cs, int* __restrict__ iters, float* __restrict__ resid) {
   constexpr int EPT = J / T;
@@ -317,8 +337,11 @@ k5_fcg_finish(const float2* __restrict__ d2, const float2* __restrict__ X, const
   float2 b[EPT];
   build_rhs<J, T, RMAX>(d2 + (size_t)p * J, mask, prior, N, p, j0, ta, tb, mp.inv_s2, mp.lam, mbits, b);
 #pragma unroll
-  for (int e = 0; e < EPT; ++e) sm_p[pidx(j0 + e)] = X[(size_t)p * J + j0 + e];
+  for (int e = 0; e < EPT; ++e) sm_p[pidx(j0 + e)] = X[(size_t)p * J + (size_t)e * T + tid];
   __syncthreads();
+  // X back to frame order for the caller (every read of X precedes the barrier)
+#pragma unroll
+  for (int i = 0; i < EPT; ++i) X[(size_t)p * J + tid + i * T] = sm_p[pidx(tid + i * T)];
   float2 xw[WIN];
   load_window<J, T, RMAX>(sm_p, j0, xw);
   float q[2] = {0.0f, 0.0f};
