@@ -27,7 +27,7 @@ size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 // flexible-CG vectors, the net requests and outputs, per-column state, two request
 // counters and the packed BF16 weights.
 struct FcgLayout {
-  size_t d2, X, R, P, Z, U, Y, netin, cs, cnt, pack, total;
+  size_t d2, X, R, P, Z, U, Y, netin, cs, mb, cnt, pack, total;
 };
 FcgLayout fcg_layout(int N, int J) {
   const size_t vec = (size_t)J * (size_t)N * sizeof(float);
@@ -41,6 +41,8 @@ FcgLayout fcg_layout(int N, int J) {
   o = al256(o + 2 * vec);
   L.cs = o;
   o = al256(o + (size_t)N * fcg_col_bytes());
+  L.mb = o;
+  o = al256(o + (size_t)(N / 2) * (size_t)fcg_threads(J) * sizeof(uint32_t));
   L.cnt = o;
   o = al256(o + 4 * sizeof(int));
   L.pack = o;
@@ -546,6 +548,7 @@ int ml_solve_learned(const ipfb_geom* g, const uint8_t* codes, const float* scal
   b.Y = reinterpret_cast<float*>(w + L.Y);
   b.netin = reinterpret_cast<float*>(w + L.netin);
   b.cs = reinterpret_cast<FcgCol*>(w + L.cs);
+  b.mb = reinterpret_cast<uint32_t*>(w + L.mb);
   int* cnt = reinterpret_cast<int*>(w + L.cnt);
   uint8_t* packed = w + L.pack;
   {

@@ -136,7 +136,7 @@ k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, fl
             float2* __restrict__ Pv, float2* __restrict__ Z, float2* __restrict__ U, const uint8_t* __restrict__ mask,
             const float* __restrict__ prior, const float* __restrict__ window, int N, MLParams mp,
             FcgCol* __restrict__ cs, const float* __restrict__ Y, float* __restrict__ netin,
-            int* __restrict__ counter) {
+            uint32_t* __restrict__ mbc, int* __restrict__ counter) {
   constexpr int EPT = J / T;
   constexpr int WIN = EPT + 2 * RMAX;
   constexpr int NMAX = NT > 0 ? NT : kMlMaxTaps;
@@ -163,6 +163,7 @@ k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, fl
   float2 r[EPT];
   if (phase == 0) {
     build_rhs<J, T, RMAX>(d2 + (size_t)p * J, mask, prior, N, p, j0, ta, tb, mp.inv_s2, mp.lam, mbits, r);
+    mbc[(size_t)p * T + tid] = mbits;  // the mask bits of this thread's frames, for the later steps
     float q[4] = {0.0f, 0.0f, (float)__popc(mbits & 0xFFFFu), (float)__popc(mbits >> 16)};
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
@@ -207,7 +208,7 @@ k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, fl
 #pragma unroll
     for (int e = 0; e < EPT; ++e) R[vb + (size_t)e * T] = r[e];
   } else {
-    mbits = load_mbits<EPT>(mask, N, p, j0);
+    mbits = mbc[(size_t)p * T + tid];
     const bool aa = sa.active, ab = sb.active;
     float2 z[EPT];
 #pragma unroll

@@ -4,28 +4,24 @@
 
 namespace ipfb {
 namespace {
-template <int J>
-constexpr int fcg_threads() {
-  return (J / 16 < 32) ? 32 : (J / 16 > 512 ? 512 : J / 16);
-}
 
 template <int J>
 cudaError_t fcg_step(int phase, const float2* d2, const FcgBufs& b, const uint8_t* mask, const float* prior,
                      const float* window, int N, const MLParams& mp, int* counter, cudaStream_t st) {
-  constexpr int T = fcg_threads<J>();
+  constexpr int T = fcg_threads(J);
   auto kern = k5_fcg_step<J, T, 3, 4>;
   const size_t smem = fcg_smem_bytes<J, T>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<N / 2, T, smem, st>>>(phase, d2, b.X, b.R, b.P, b.Z, b.U, mask, prior, window, N, mp, b.cs, b.Y, b.netin,
-                               counter);
+                               b.mb, counter);
   return cudaGetLastError();
 }
 
 template <int J>
 cudaError_t fcg_finish(const float2* d2, const FcgBufs& b, const uint8_t* mask, const float* prior,
                        const float* window, int N, const MLParams& mp, int* iters, float* resid, cudaStream_t st) {
-  constexpr int T = fcg_threads<J>();
+  constexpr int T = fcg_threads(J);
   auto kern = k5_fcg_finish<J, T, 3, 4>;
   const size_t smem = fcg_smem_bytes<J, T>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -37,7 +33,7 @@ cudaError_t fcg_finish(const float2* d2, const FcgBufs& b, const uint8_t* mask, 
 template <int J>
 cudaError_t net_pairs(const float2* xs, const float2* xk, const int* pl, int npairs, const uint8_t* mask,
                       const float* window, int N, const MLParams& mp, float* xin, float* target, cudaStream_t st) {
-  constexpr int T = fcg_threads<J>();
+  constexpr int T = fcg_threads(J);
   auto kern = k5_net_pairs<J, T, 3, 4>;
   const size_t smem = fcg_smem_bytes<J, T>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -79,7 +79,10 @@ struct FcgBufs {
   FcgCol* cs;                 // [N] per-column state
   float* Y;                   // [N][J] net outputs (request slots)
   float* netin;               // [N][2][J] net inputs (request slots)
+  uint32_t* mb;               // [P][fcg_threads(J)] prior-mask bits of each thread's frames
 };
+// threads per column pair of the flexible-CG kernels (16 frames per thread)
+constexpr int fcg_threads(int J) { return J / 16 < 32 ? 32 : (J / 16 > 512 ? 512 : J / 16); }
 size_t fcg_col_bytes();
 cudaError_t launch_fcg_step(int J, int phase, const float2* d2, const FcgBufs& b, const uint8_t* mask,
                             const float* prior, const float* window, int N, const MLParams& mp, int* counter,

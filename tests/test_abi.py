@@ -47,8 +47,10 @@ def test_learned_workspace_sizes():
     ml = ipfb.workspace_size(g, ipfb.OP_ML)
     learned = ipfb.workspace_size(g, ipfb.OP_ML_LEARNED)
     vec = 4096 * 8192 * 4
-    # d, five FCG vectors, net outputs (one vector) and inputs (two), plus small state
-    assert 9 * vec <= learned <= 9 * vec + (1 << 20)
+    # d, five FCG vectors, net outputs (one vector) and inputs (two), the prior-mask
+    # bits of every thread (one 32-bit word per 16 frames of a column pair), small state
+    mbits = 2048 * (8192 // 16) * 4
+    assert 9 * vec + mbits <= learned <= 9 * vec + mbits + (1 << 20)
     assert ml == 2 * vec
     assert ipfb.workspace_size(g, ipfb.OP_ML_PAIRS) == 2 * vec + 2048 * 4
     with pytest.raises(ipfb.IpfbError):
