@@ -194,6 +194,42 @@ def test_learned_fcg_matches_oracle(N, J):
     assert abs(e_gpu - e_or) <= 1e-3 * e_or
 
 
+def test_learned_initial_guess():
+    """x0 enters in frame order and the solution leaves in frame order: with no
+    iteration the output is x0 bit for bit; from x0 the learned FCG reaches the same
+    reconstruction as the oracle's FCG started from the same x0."""
+    N, J = 64, 256
+    x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 27)
+    th = _theta(28, scale3=0.2, jitter=0.01)
+    rng = np.random.default_rng(29)
+    x0 = (x + 0.3 * rng.standard_normal(x.shape)).astype(np.float32)
+    args = (cuda(codes), cuda(scale), cuda(w.astype(np.float32)), sig2, cuda(mask), cuda(prior))
+    x_same, it0, _ = ipfb.ml_solve(*args, precond="learned", net=cuda(th.astype(np.float32)), tol=1e-6,
+                                   max_iter=0, x0=cuda(x0))
+    assert np.array_equal(x_same.cpu().numpy(), x0)
+    assert np.all(it0.cpu().numpy() == 0)
+    tol = 1e-6
+    xl, itl, rl = ipfb.ml_solve(*args, precond="learned", net=cuda(th.astype(np.float32)), tol=tol,
+                                max_iter=2000, x0=cuda(x0))
+    xl = xl.cpu().numpy().reshape(J, N).astype(np.float64)
+    itl, rl = itl.cpu().numpy(), rl.cpu().numpy()
+    M = mask.reshape(J, N).astype(np.float64)
+    P = prior.reshape(J, N).astype(np.float64)
+    A = lambda V: oml.normal_operator_fft(w, V, sig2, M, 1.0)  # noqa: E731
+    B = oml.rhs(w, d, sig2, M, P, 1.0)
+    pr = onet.unflatten(th.astype(np.float32).astype(np.float64))
+    pre = lambda R: onet.apply_precond(pr, oml.wiener_precond(w, R, sig2, M, 1.0), M, emulate_bf16=True)  # noqa
+    Xo, ito, _ = onet.fcg(A, B, x0.reshape(J, N).astype(np.float64), pre, tol, 2000)
+    assert np.all(rl[0] <= tol)
+    tr = oml.true_relative_residual(d, w, sig2, M, P, 1.0, xl)
+    assert np.all(tr <= 5 * tol), tr.max()
+    assert np.all(np.abs(itl - ito) <= np.maximum(3, 0.25 * ito)), (itl, ito)
+    xt = x.reshape(J, N)
+    e_gpu = np.linalg.norm(xl - xt) / np.linalg.norm(xt)
+    e_or = np.linalg.norm(Xo - xt) / np.linalg.norm(xt)
+    assert abs(e_gpu - e_or) <= 1e-3 * e_or
+
+
 def test_learned_requires_net_and_ntap4():
     N, J = 64, 128
     x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 26)
