@@ -25,5 +25,6 @@ Modules
 
 Parity unpinned: the paper's end-to-end accuracy figures (Sec. 4.3) are
 statistical results on a different quantizer step and mask scheme; they are
-context only.  The learned preconditioner has no paper pin (plain CG judges it).
+context only.  The learned preconditioner has no paper pin (its answers are checked
+against plain CG on the same system).
 """
