@@ -151,3 +151,4 @@ def test_binding_refuses_cpu_tensors():
         ipfb.pfb_forward(x, w)
     with pytest.raises(TypeError):
         ipfb.upchannelize(x, 1024)
+
