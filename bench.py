@@ -321,6 +321,69 @@ def make_inputs(torch, ipfb, dev):
     return xg, w, codes, scale, phi2
 
 
+def cufft_pipeline(torch, codes, scale, w, phi2, upfactor):
+    """The benchmark step written with torch.fft (cuFFT) and torch's elementwise
+    kernels, timed only as a comparison: unpack the 4-bit codes times the channel
+    steps, N-point inverse real FFT per spectrum, per phase column a real FFT along
+    frames, the Wiener gain G = W (1 + phi^2) / (|W|^2 + phi^2) with W the sub-filter
+    eigenvalues of Sec. 3.1 (Eq. decorrelation with Eq. wiener weights; G is
+    Hermitian in k, so half the modes suffice), the inverse real FFT, then the real
+    FFT of every upfactor * N-sample block.  G is formed once, outside the returned
+    step.  Returns step() -> spectra [nblocks, upfactor N / 2 + 1] complex64."""
+    J, half = codes.shape
+    N = 2 * half
+    dev = codes.device
+    k = torch.arange(J // 2 + 1, dtype=torch.float64, device=dev)
+    W = torch.zeros((J // 2 + 1, N), dtype=torch.complex128, device=dev)
+    for r in range(w.shape[0]):
+        ang = -2.0 * math.pi * torch.remainder(r * k, J) / J
+        W += torch.polar(torch.ones_like(ang), ang)[:, None] * w[r].double()[None, :]
+    G = (W * (1.0 + phi2) / (W.abs() ** 2 + phi2)).to(torch.complex64)
+    del W
+    s = scale.float()
+    L = upfactor * N
+    nb = (J * N) // L
+
+    def step():
+        lo = (codes & 0xF).to(torch.int16)
+        hi = (codes >> 4).to(torch.int16)
+        lo = torch.where(lo >= 8, lo - 16, lo).float()
+        hi = torch.where(hi >= 8, hi - 16, hi).float()
+        re = torch.zeros((J, half + 1), dtype=torch.float32, device=dev)
+        im = torch.zeros_like(re)
+        re[:, :half] = lo
+        re[:, half] = hi[:, 0]
+        im[:, 1:half] = hi[:, 1:]
+        d = torch.fft.irfft(torch.complex(re * s, im * s), n=N, dim=1)
+        x = torch.fft.irfft(torch.fft.rfft(d, dim=0) * G, n=J, dim=0)
+        return torch.fft.rfft(x.reshape(-1)[: nb * L].reshape(nb, L), dim=1)
+
+    return step
+
+
+def run_cufft_comparison(torch, codes, scale, w, phi2, ours, reps=5):
+    """Time cufft_pipeline on the benchmark's resident codes (CUDA events, after two
+    warm-up runs) and compare its spectra with the library's."""
+    stream = torch.cuda.current_stream()
+    step = cufft_pipeline(torch, codes, scale, w, phi2, UPFACTOR)
+    for _ in range(2):
+        spec = step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        spec = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    rel = float(torch.linalg.norm(spec - ours) / torch.linalg.norm(ours))
+    del spec, step
+    torch.cuda.empty_cache()
+    return {"what": "the same step with torch.fft (cuFFT) and torch elementwise kernels; the Wiener gain "
+                    "precomputed outside the timed steps", "ms": ms, "gsas": NSAMP / (ms * 1e-3) / 1e9,
+            "ours_ms": None, "rel_diff_to_ours": rel}
+
+
 ML_LBLOCK, ML_NFRAMES = 4096, 8192
 
 
@@ -668,6 +731,14 @@ def run_ours(args):
         "clocks": clk.summary(),
     }
     result["stages"]["stream_overlap_save"] = run_stream(torch, ipfb, dev, codes, scale, w, phi2)
+    if not args.no_cufft:
+        try:
+            cmp = run_cufft_comparison(torch, codes, scale, w, phi2, out)
+            cmp["ours_ms"] = ms
+            result["cufft_comparison"] = cmp
+        except Exception as exc:  # a comparison only: its failure must not cost the benchmark line
+            result["cufft_comparison"] = {"error": repr(exc)[:300]}
+            torch.cuda.empty_cache()
     if not args.no_ml:
         theta, tinfo = (None, None) if args.no_learned else train_learned(torch, dev)
         result["ml"] = run_ml(torch, ipfb, dev, theta=theta)
@@ -756,6 +827,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true",
                     help="skip training the learned preconditioner and its ML timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-streams timing")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the torch.fft (cuFFT) comparison")
     ap.add_argument("--profile-case", nargs=3, type=int, metavar=("LBLOCK", "NFRAMES", "REPS"),
                     help="run a smaller case of the pipeline (for ncu captures) and exit")
     ap.add_argument("--profile-batched", type=int, metavar="NSTREAMS",
