@@ -378,6 +378,10 @@ def run_cufft_comparison(torch, codes, scale, w, phi2, ours, reps=5):
     ms = e0.elapsed_time(e1) / reps
     rel = float(torch.linalg.norm(spec - ours) / torch.linalg.norm(ours))
     del spec, step
+    try:
+        torch.backends.cuda.cufft_plan_cache.clear()  # the plans' work areas
+    except Exception:
+        pass
     torch.cuda.empty_cache()
     return {"what": "the same step with torch.fft (cuFFT) and torch elementwise kernels; the Wiener gain "
                     "precomputed outside the timed steps", "ms": ms, "gsas": NSAMP / (ms * 1e-3) / 1e9,
