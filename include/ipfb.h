@@ -259,7 +259,10 @@ int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const flo
  * r_new.(z_new - z_old) / r_old.z_old.  precond 2 requires ntap = 4, runs two
  * launches per iteration and synchronizes the stream every fourth iteration to
  * test for completion (it cannot be captured in a CUDA graph); its workspace is
- * ipfb_workspace_size(g, IPFB_OP_ML_LEARNED).
+ * ipfb_workspace_size(g, IPFB_OP_ML_LEARNED).  If any column ends with a
+ * non-finite residual (a net that returns NaN or Inf), the solve is redone by
+ * plain CG (precond 0) from the same start, and x_inout, iters and resid are
+ * plain CG's.
  * prior_mask: uint8 [J*N] time order (nonzero = saved sample); prior_values:
  * float [J*N]; x_inout: float [J*N], the initial guess when use_x0 != 0 (else
  * zero is used), the solution on return.  iters: int [N] iterations per column;

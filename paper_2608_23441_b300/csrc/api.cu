@@ -600,6 +600,27 @@ int ml_solve_learned(const ipfb_geom* g, const uint8_t* codes, const float* scal
     CK(launch_fcg_finish(J, d2, b, mask, prior, window, N, mp, iters, resid, st), "k5_fcg_finish");
     t.done();
   }
+  // Fallback: a net that returns a non-finite value leaves a non-finite residual in
+  // the columns it touched (flexible CG cannot recover from it).  Then the whole solve
+  // is redone by plain CG from the same start, so the caller gets plain CG's answer,
+  // iteration counts and residuals.
+  std::vector<float> rh((size_t)2 * N);
+  CK(cudaMemcpyAsync(rh.data(), resid, rh.size() * sizeof(float), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+  CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  bool finite = true;
+  for (float v : rh) finite = finite && std::isfinite(v);
+  if (!finite) {
+    if (use_x0) {
+      Stage t("k_time_to_pairs", st);
+      CK(launch_time_to_pairs(x_inout, b.X, N, J, st), "k_time_to_pairs");
+      t.done();
+    }
+    MLParams plain = mp;
+    plain.precond = 0;
+    Stage t("k5_ml_cg", st);
+    CK(launch_k5(J, d2, b.X, mask, prior, window, N, plain, iters, resid, st), "k5_ml_cg");
+    t.done();
+  }
   Stage t("k_pairs_to_time", st);
   CK(launch_pairs_to_time(b.X, x_inout, N, 1, J, st), "k_pairs_to_time");
   t.done();

@@ -230,6 +230,20 @@ def test_learned_initial_guess():
     assert abs(e_gpu - e_or) <= 1e-3 * e_or
 
 
+def test_learned_nonfinite_net_falls_back_to_plain_cg():
+    """A net that returns NaN: flexible CG ends with non-finite residuals, and the call
+    hands back plain CG's solve from the same start, bit for bit."""
+    N, J = 64, 256
+    x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 30)
+    th = _theta(31).astype(np.float32)
+    th[:] = np.nan
+    args = (cuda(codes), cuda(scale), cuda(w.astype(np.float32)), sig2, cuda(mask), cuda(prior))
+    xp, itp, rp = ipfb.ml_solve(*args, precond="none", tol=1e-6, max_iter=500)
+    xl, itl, rl = ipfb.ml_solve(*args, precond="learned", net=cuda(th), tol=1e-6, max_iter=500)
+    assert torch.equal(xl, xp) and torch.equal(itl, itp) and torch.equal(rl, rp)
+    assert bool(torch.isfinite(xl).all())
+
+
 def test_learned_requires_net_and_ntap4():
     N, J = 64, 128
     x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 26)
