@@ -108,17 +108,29 @@ def make_training_set(torch, dev, seeds, iters=(1, 3, 8, 20, 50), pairs_per: int
 
 
 def train(torch, dev, xin, target, epochs: int = 10, batch: int = 16, lr: float = 2e-3, seed: int = 0,
-          theta0: np.ndarray | None = None, log=None):
+          theta0: np.ndarray | None = None, log=None, state: dict | None = None, return_state: bool = False):
     """Adam on mini-batches of `batch` consecutive training columns (batch / 2 randomly
     drawn column pairs of one instance and iterate), the batches visited in a new
-    random order every epoch; returns (theta device tensor, per-epoch mean loss)."""
+    random order every epoch; returns (theta device tensor, per-epoch mean loss), and
+    with return_state=True also the training state (theta, Adam moments m and v, step
+    count, batch-order generator state) that save_checkpoint writes and `state=`
+    resumes from: training E1 epochs, then E2 more from the saved state, visits the
+    same batches with the same Adam steps as E1 + E2 epochs in one run."""
     n = xin.shape[0]
-    theta = torch.from_numpy(init_theta(seed) if theta0 is None else theta0.astype(np.float32)).to(dev)
-    m = torch.zeros_like(theta)
-    v = torch.zeros_like(theta)
+    if state is not None:
+        theta = torch.from_numpy(_host_f32(state["theta"]).astype(np.float32)).to(dev)
+        m = torch.from_numpy(_host_f32(state["m"]).astype(np.float32)).to(dev)
+        v = torch.from_numpy(_host_f32(state["v"]).astype(np.float32)).to(dev)
+        step = int(state["step"])
+        rng = np.random.default_rng()
+        rng.bit_generator.state = state["rng"]
+    else:
+        theta = torch.from_numpy(init_theta(seed) if theta0 is None else theta0.astype(np.float32)).to(dev)
+        m = torch.zeros_like(theta)
+        v = torch.zeros_like(theta)
+        rng = np.random.default_rng(seed + 1)
+        step = 0
     ws = torch.empty(ipfb.net_workspace_size(ipfb.NET_GRAD, batch, xin.shape[2]), dtype=torch.uint8, device=dev)
-    rng = np.random.default_rng(seed + 1)
-    step = 0
     hist = []
     nb = n // batch
     for ep in range(epochs):
@@ -133,4 +145,64 @@ def train(torch, dev, xin, target, epochs: int = 10, batch: int = 16, lr: float 
         hist.append(ep_loss)
         if log:
             log(f"epoch {ep}: loss {ep_loss:.5f}")
+    if return_state:
+        return theta, hist, {"theta": theta, "m": m, "v": v, "step": step, "rng": rng.bit_generator.state}
     return theta, hist
+
+
+# ---------------------------------------------------------------------------
+# Checkpoints: the net's parameters with the Adam state, as one file
+#   8 bytes magic "IPFBNET1", 4 bytes little-endian header length H, H bytes of JSON
+#   (nparams, step, has_adam, the batch-order generator state, free-form info), then
+#   theta, and with has_adam m and v, each nparams little-endian float32.
+# ---------------------------------------------------------------------------
+CKPT_MAGIC = b"IPFBNET1"
+
+
+def _host_f32(a) -> np.ndarray:
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(np.asarray(a, dtype="<f4")).reshape(-1)
+
+
+def save_checkpoint(path: str, theta, m=None, v=None, step: int = 0, rng_state: dict | None = None,
+                    info: dict | None = None) -> None:
+    """Write theta (and the Adam moments m, v when given) to `path` (see above)."""
+    import json
+    th = _host_f32(theta)
+    if th.size != ipfb.NET_NPARAMS:
+        raise ValueError(f"theta has {th.size} values, expected {ipfb.NET_NPARAMS}")
+    has_adam = m is not None and v is not None
+    arrays = [th] + ([_host_f32(m), _host_f32(v)] if has_adam else [])
+    if any(a.size != th.size for a in arrays):
+        raise ValueError("m and v must have as many values as theta")
+    header = json.dumps({"nparams": int(th.size), "step": int(step), "has_adam": bool(has_adam),
+                         "rng": rng_state, "info": info or {}}).encode()
+    with open(path, "wb") as fh:
+        fh.write(CKPT_MAGIC)
+        fh.write(len(header).to_bytes(4, "little"))
+        fh.write(header)
+        for a in arrays:
+            fh.write(a.tobytes())
+
+
+def load_checkpoint(path: str) -> dict:
+    """Read a checkpoint: {"theta", "m", "v" (None without Adam state), "step", "rng",
+    "info"}; the arrays are float32 numpy vectors."""
+    import json
+    with open(path, "rb") as fh:
+        blob = fh.read()
+    if blob[:8] != CKPT_MAGIC:
+        raise ValueError(f"{path}: not a net checkpoint")
+    hlen = int.from_bytes(blob[8:12], "little")
+    header = json.loads(blob[12:12 + hlen].decode())
+    n = int(header["nparams"])
+    if n != ipfb.NET_NPARAMS:
+        raise ValueError(f"{path}: {n} parameters, expected {ipfb.NET_NPARAMS}")
+    narr = 3 if header["has_adam"] else 1
+    body = blob[12 + hlen:]
+    if len(body) != narr * n * 4:
+        raise ValueError(f"{path}: {len(body)} bytes of arrays, expected {narr * n * 4}")
+    arrs = [np.frombuffer(body, dtype="<f4", count=n, offset=i * n * 4).astype(np.float32) for i in range(narr)]
+    return {"theta": arrs[0], "m": arrs[1] if narr == 3 else None, "v": arrs[2] if narr == 3 else None,
+            "step": int(header["step"]), "rng": header.get("rng"), "info": header.get("info", {})}

@@ -307,3 +307,21 @@ def test_trained_net_gain_over_plain_cg():
     ep = float(torch.linalg.norm(xp - x) / torch.linalg.norm(x))
     el = float(torch.linalg.norm(xl - x) / torch.linalg.norm(x))
     assert abs(el - ep) <= 1e-3 * ep, (el, ep)
+
+
+def test_training_resumes_exactly_from_a_checkpoint(tmp_path):
+    """Two epochs, a checkpoint written and read back, two more epochs: the same
+    parameters, bit for bit, as four epochs in one run (Adam moments, step count and
+    batch order all restored)."""
+    from paper_2608_23441_b300 import precond_train as pt
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(41)
+    xin = cuda(_xin(64, 512, 42).astype(np.float32))
+    tgt = cuda(rng.standard_normal((64, 512)).astype(np.float32))
+    th4, h4 = pt.train(torch, dev, xin, tgt, epochs=4, batch=16, seed=3)
+    th2, h2, st = pt.train(torch, dev, xin, tgt, epochs=2, batch=16, seed=3, return_state=True)
+    p = str(tmp_path / "net.ckpt")
+    pt.save_checkpoint(p, st["theta"], st["m"], st["v"], step=st["step"], rng_state=st["rng"])
+    thr, hr = pt.train(torch, dev, xin, tgt, epochs=2, batch=16, state=pt.load_checkpoint(p))
+    assert torch.equal(thr, th4)
+    assert h2 + hr == h4
