@@ -301,6 +301,10 @@ int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, 
  * y, target: device float [nslots][J].
  *
  * ipfb_net_forward: y = net(xin).  Workspace ipfb_net_workspace_size(IPFB_NET_FORWARD).
+ *   Layer 2 waits for its tensor-core accumulators with a bound of about a second
+ *   of SM clocks; a CTA that gives up writes NaN at the first output frame of its
+ *   tile and stops (so a learned solve sees a non-finite residual and falls back
+ *   to plain CG).  The call itself returns 0: the status is in y.
  * ipfb_net_grad: loss = sum over slots and frames of (y - target)^2 / (nslots J)
  *   (device float [1], may be NULL) and its gradient with respect to theta
  *   (device float [IPFB_NET_NPARAMS], may be NULL), the BF16 rounding of weights
