@@ -206,3 +206,57 @@ def load_checkpoint(path: str) -> dict:
     arrs = [np.frombuffer(body, dtype="<f4", count=n, offset=i * n * 4).astype(np.float32) for i in range(narr)]
     return {"theta": arrs[0], "m": arrs[1] if narr == 3 else None, "v": arrs[2] if narr == 3 else None,
             "step": int(header["step"]), "rng": header.get("rng"), "info": header.get("info", {})}
+
+
+def parse_seeds(text: str) -> list[int]:
+    """"1000-1007" -> [1000, ..., 1007]; "3,5,9" -> [3, 5, 9]; ranges and single seeds
+    mix ("1-2,7"); seeds are non-negative."""
+    out: list[int] = []
+    for part in text.split(","):
+        part = part.strip()
+        if not part:
+            continue
+        if "-" in part:
+            a, b = part.split("-", 1)
+            lo, hi = int(a), int(b)
+            if hi < lo:
+                raise ValueError(f"empty seed range {part!r}")
+            out.extend(range(lo, hi + 1))
+        else:
+            out.append(int(part))
+    if not out:
+        raise ValueError("no seeds")
+    return out
+
+
+def main(argv=None) -> int:
+    """Train the net on the training recipe above and write a checkpoint:
+
+        python -m paper_2608_23441_b300.precond_train --out net.ckpt
+            [--seeds 1000-1007] [--epochs 8] [--resume earlier.ckpt]
+
+    With --resume, training continues from that checkpoint's parameters, Adam state and
+    batch order (the training pairs are rebuilt from the same seeds)."""
+    import argparse
+    import json
+    import torch
+    ap = argparse.ArgumentParser(description="train the learned CG preconditioner")
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--seeds", default="1000-1007")
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--resume", default=None)
+    args = ap.parse_args(argv)
+    seeds = parse_seeds(args.seeds)
+    dev = torch.device("cuda", 0)
+    xin, tgt, info = make_training_set(torch, dev, seeds)
+    state = load_checkpoint(args.resume) if args.resume else None
+    theta, hist, st = train(torch, dev, xin, tgt, epochs=args.epochs, state=state, return_state=True)
+    info.update({"seeds": args.seeds, "epochs": args.epochs, "loss_per_epoch": hist,
+                 "resumed_from": args.resume})
+    save_checkpoint(args.out, st["theta"], st["m"], st["v"], step=st["step"], rng_state=st["rng"], info=info)
+    print(json.dumps({"out": args.out, "step": st["step"], "loss_per_epoch": hist}))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -60,3 +60,12 @@ def test_rejects_bad_files(tmp_path):
     (tmp_path / "magic").write_bytes(b"XXXXXXXX" + blob[8:])
     with pytest.raises(ValueError):
         pt.load_checkpoint(str(tmp_path / "magic"))
+
+
+def test_parse_seeds():
+    assert pt.parse_seeds("1000-1003") == [1000, 1001, 1002, 1003]
+    assert pt.parse_seeds("3, 5,9") == [3, 5, 9]
+    assert pt.parse_seeds("1-2,7") == [1, 2, 7]
+    for bad in ("", "5-3", "-4", "a"):
+        with pytest.raises(ValueError):
+            pt.parse_seeds(bad)
