@@ -82,16 +82,30 @@ def test_pfb_forward_parity(N, J):
     want = opfb.pack_codes(q_re, q_im)
     got = codes2.cpu().numpy()
     bad = got != want
-    frac = bad.mean()
-    assert frac < 2e-3
-    if bad.any():
-        # every flipped byte sits within 1e-3 steps of a half-integer in the oracle
-        t_re = spec_or.real[:, : N // 2] / scale_or[None, : N // 2]
-        t_im = spec_or.imag[:, : N // 2] / scale_or[None, : N // 2]
-        dist = np.minimum(np.abs(np.abs(t_re) % 1 - 0.5), np.abs(np.abs(t_im) % 1 - 0.5))
-        t_ny = spec_or.real[:, N // 2] / scale_or[N // 2]
-        dist[:, 0] = np.minimum(np.abs(np.abs(t_re[:, 0]) % 1 - 0.5), np.abs(np.abs(t_ny) % 1 - 0.5))
-        assert np.all(dist[bad] < 1e-3)
+    # Sec. 4.3 quantizer read as a float32 decision (the oracle's channel step, the
+    # GPU's FP32 spectrum): a code may differ from the FP64 oracle's only where the
+    # FP32 spectrum's own error moves v / Delta across a decision boundary, i.e. the
+    # oracle's v / Delta lies within 1e-5 steps of a half-integer.  The flips are
+    # counted and reported.
+    t_re = spec_or.real[:, : N // 2] / scale_or[None, : N // 2]
+    t_im = spec_or.imag[:, : N // 2] / scale_or[None, : N // 2]
+    dist = np.minimum(np.abs(np.abs(t_re) % 1 - 0.5), np.abs(np.abs(t_im) % 1 - 0.5))
+    t_ny = spec_or.real[:, N // 2] / scale_or[N // 2]
+    dist[:, 0] = np.minimum(np.abs(np.abs(t_re[:, 0]) % 1 - 0.5), np.abs(np.abs(t_ny) % 1 - 0.5))
+    # the FP32 spectrum's error in steps, largest over all values
+    e_re = np.abs(spec.real - spec_or.real) / scale_or[None, :]
+    e_im = np.abs(spec.imag - spec_or.imag) / scale_or[None, :]
+    err_steps = float(max(e_re.max(), e_im.max()))
+    nflip = int(bad.sum())
+    print(f"pfb_forward N={N} J={J}: {nflip} of {bad.size} code bytes differ from the FP64 oracle; "
+          f"FP32 spectrum error up to {err_steps:.2e} steps")
+    assert err_steps < 1e-5
+    if nflip:
+        assert np.all(dist[bad] <= err_steps)
+    # the same codes again from the GPU's own FP32 spectrum with the same step: the
+    # decision itself is bit-exact
+    want32 = opfb.pack_codes(*opfb.quantize_spectra(spec.astype(np.complex128), scale_or))
+    assert np.array_equal(got, want32)
 
 
 # ----------------------------------------------------------------------------- inverse

@@ -140,3 +140,39 @@ def test_forward_quantized_dc_nyquist_folding():
     y = pfb.dequantize(codes, scale)
     err = np.var(y - spec) / np.var(spec)
     assert 0.005 < err < 0.03
+
+
+def test_channel_rms_hand_cases():
+    # Sec. 4.3 quantizer step, read per channel (workload spec): RMS_c over the real
+    # and imaginary parts of channel c, i.e. sqrt(sum_j (Re^2 + Im^2) / (2 J)) for
+    # interior channels and sqrt(sum_j Re^2 / J) at DC and Nyquist (no imaginary
+    # part).  Values worked out by hand: a /J-for-/(2J) slip (a factor sqrt 2), a
+    # dropped Im term, or treating DC / Nyquist like interior channels all fail.
+    J, C = 4, 5
+    spec = np.zeros((J, C), np.complex128)
+    spec[:, 1] = 3 + 4j                      # every interior sample 3 + 4i
+    spec[:, 2] = [1, 1j, 3 + 4j, 0]          # 1 + 1 + 25 + 0 = 27 over 2J = 8 values
+    spec[:, 3] = [2j, -2j, 2j, -2j]          # imaginary only: 16 / 8 = 2
+    spec[:, 0] = [2, -2, 2, -2]              # DC, real only: 16 / 4
+    spec[:, 4] = [1, -1, 3, 0]               # Nyquist: 1 + 1 + 9 + 0 = 11 over J = 4
+    rms = pfb.channel_rms(spec)
+    want = np.array([2.0, np.sqrt(12.5), np.sqrt(27 / 8), np.sqrt(2.0), np.sqrt(11 / 4)])
+    assert np.allclose(rms, want, rtol=0, atol=1e-15)
+    # Delta_c = RMS_c / 2.5, formed in FP64 and rounded once to float32
+    sc = pfb.channel_scale(spec)
+    assert sc.dtype == np.float32
+    assert np.array_equal(sc, (want / 2.5).astype(np.float32))
+    assert sc[0] == np.float32(0.8) and sc[1] == np.float32(np.sqrt(12.5) / 2.5)
+
+
+def test_channel_rms_of_gaussian_spectra_is_sigma():
+    # A real-input spectrum of white noise of variance s^2 has E|Y_c|^2 = N s^2 for
+    # every channel; the interior channels split it equally between Re and Im
+    # (N s^2 / 2 each), DC and Nyquist are real with variance N s^2.  So the
+    # per-part RMS is sqrt(N/2) s inside and sqrt(N) s at the two real channels --
+    # a ratio of sqrt 2 that the special case must reproduce.
+    N, J, s = 64, 4000, 1.7
+    x = np.random.default_rng(3).standard_normal((J, N)) * s
+    rms = pfb.channel_rms(np.fft.rfft(x, axis=1))
+    assert np.allclose(rms[1:-1], np.sqrt(N / 2) * s, rtol=0.03)
+    assert np.allclose(rms[[0, -1]], np.sqrt(N) * s, rtol=0.04)
