@@ -415,10 +415,11 @@ def ml_inputs(torch, ipfb, dev, seed=4):
     return codes, scale, w, mask, xg, sig2
 
 
-def train_learned(torch, dev, epochs=8, seeds=range(1000, 1008)):
+def train_learned(torch, dev, epochs=None, seeds=range(1000, 1008)):
     """Learned-preconditioner training with the library's kernels (config-5 recipe,
     8 seeded instances x 5 plain-CG iterates x 50 column pairs = 2000 pairs)."""
     from paper_2608_23441_b300 import precond_train as pt
+    epochs = pt.EPOCHS if epochs is None else epochs
     t0 = time.time()
     xin, tgt, info = pt.make_training_set(torch, dev, list(seeds))
     torch.cuda.synchronize()
@@ -441,11 +442,16 @@ def run_ml(torch, ipfb, dev, reps=3, theta=None):
            "noise_var": sig2}
     stream = torch.cuda.current_stream()
     g = ipfb.geom(ML_LBLOCK, NTAP, ML_NFRAMES)
-    names = ("none", "wiener") + (("learned",) if theta is not None else ())
+    from paper_2608_23441_b300 import precond_train as pt
+    zero = torch.from_numpy(pt.init_theta(0, scale3=0.0)).to(dev)
+    names = ("none", "wiener") + (("learned", "learned_g0") if theta is not None else ())
     for name in names:
-        op = ipfb.OP_ML_LEARNED if name == "learned" else ipfb.OP_ML
+        learned = name.startswith("learned")
+        op = ipfb.OP_ML_LEARNED if learned else ipfb.OP_ML
         ws = torch.empty(ipfb.workspace_size(g, op), dtype=torch.uint8, device=dev)
-        kw = dict(precond=name, tol=1e-6, max_iter=4000, workspace=ws, net=theta if name == "learned" else None)
+        kw = dict(precond="learned" if learned else name, tol=1e-6, max_iter=4000, workspace=ws,
+                  net=(theta if name == "learned" else zero) if learned else None,
+                  net_from=pt.NET_FROM if learned else 0)
         ipfb.ml_solve(codes, scale, w, sig2, mask, prior, **kw)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -460,6 +466,8 @@ def run_ml(torch, ipfb, dev, reps=3, theta=None):
         del ws
     if theta is not None:
         out["learned_vs_plain_time"] = out["learned"]["ms"] / out["none"]["ms"]
+        out["learned_net_from"] = pt.NET_FROM
+        out["learned_g0_note"] = "the same learned solve with a zero-output net (g = 0: the Wiener term alone)"
     out["paper_protocol"] = run_ml_paper_protocol(torch, ipfb, dev, codes, scale, w, prior, sig2, reps=reps)
     return out
 

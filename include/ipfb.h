@@ -80,6 +80,17 @@ int ipfb_version(void);
 int ipfb_set_max_column_run(int frames);
 
 /*
+ * Testing knob (no counterpart in the paper): the bound, in SM clocks, on the net
+ * forward's wait for its tensor-core accumulators (ipfb_net_forward and the learned
+ * solve).  cycles < 0 restores the built-in bound of about a second.  With a bound
+ * shorter than the MMAs take, every CTA gives up at once: it marks its tile's output,
+ * reports the give-up to the learned solve, lets its MMAs in flight finish (within the
+ * built-in bound) and stops, so the expiry path runs without anything being withheld.
+ * Process-wide.
+ */
+int ipfb_set_net_wait_limit(long long cycles);
+
+/*
  * Stage timing (no counterpart in the paper).  ipfb_stage_timing(1) clears the
  * record and starts bracketing every kernel launch of every compute call with two
  * CUDA events on that call's stream; ipfb_stage_timing(0) clears and stops.
@@ -129,11 +140,14 @@ int pfb_forward(const ipfb_geom* g, const float* x, const float* window, const f
  * they own.  The FP64 power sums live in a fixed array inside the library sized
  * for lblock <= 16384 (131 KB held on every GPU that loads the library, until the
  * process exits); larger lblock returns IPFB_ERR_UNSUPPORTED before anything is
- * enqueued.  No device memory is allocated.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress, once per device); make that
- * first call before any stream capture.  All calls share the array: each clears
- * it on its own stream, and calls that overlap on the GPU (other streams or host
- * threads on the same device) race on it -- serialize them.
+ * enqueued.  No device memory is allocated.  Every call looks up the array's
+ * address on the current device (cudaGetSymbolAddress, a host-side query), so a
+ * device reset between calls is harmless; the first call on a device also loads
+ * the library's device code there, so make it before any stream capture.  All
+ * calls share the array: each clears it on its own stream, and calls that overlap
+ * on the GPU (other streams or host threads on the same device) race on it --
+ * serialize them.  CUDA failures return IPFB_ERR_CUDA with the failing step named
+ * in ipfb_last_cuda_error().
  */
 int pfb_forward_noalloc(const ipfb_geom* g, const float* x, const float* window, uint8_t* codes,
                         float* scale_out, float* spectra_out, void* stream);
@@ -256,13 +270,16 @@ int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const flo
  * see ipfb_net_forward), z = u + s g(u/s, m) with u the Wiener z above, s = RMS(u)
  * over the column (1 if u = 0), m the column's prior mask; the outer iteration is
  * then flexible CG (Notay 2000) with the Polak-Ribiere beta
- * r_new.(z_new - z_old) / r_old.z_old.  precond 2 requires ntap = 4, runs two
- * launches per iteration and synchronizes the stream every fourth iteration to
- * test for completion (it cannot be captured in a CUDA graph); its workspace is
- * ipfb_workspace_size(g, IPFB_OP_ML_LEARNED).  If any column ends with a
- * non-finite residual (a net that returns NaN or Inf), the solve is redone by
- * plain CG (precond 0) from the same start, and x_inout, iters and resid are
- * plain CG's.
+ * r_new.(z_new - z_old) / r_old.z_old.  precond 2 requires ntap = 4; its workspace
+ * is ipfb_workspace_size(g, IPFB_OP_ML_LEARNED).  It is enqueued as one CUDA graph
+ * whose loop (two launches per iteration) is ended on the device once no column is
+ * active, so the call neither synchronizes nor reads anything back: when `stream` is
+ * capturing, the graph's nodes (conditional WHILE and IF nodes among them) join the
+ * caller's capture; otherwise the library captures it privately, launches it on
+ * `stream` and releases it.  If any column ends with a non-finite residual (a net
+ * that returns NaN or Inf), or the net gave up waiting for its accumulators, the
+ * solve is redone on the device by plain CG (precond 0) from the same start, and
+ * x_inout, iters and resid are plain CG's.
  * prior_mask: uint8 [J*N] time order (nonzero = saved sample); prior_values:
  * float [J*N]; x_inout: float [J*N], the initial guess when use_x0 != 0 (else
  * zero is used), the solution on return.  iters: int [N] iterations per column;
@@ -277,6 +294,8 @@ typedef struct {
   double tol;          /* relative residual target per column (e.g. 1e-6)     */
   int max_iter;        /* iteration cap per column                            */
   int precond;         /* 0 none, 1 Wiener, 2 learned                         */
+  int net_from;        /* learned: iterations that use the Wiener step alone
+                          before the net joins (>= 0; 0 = from the start)     */
 } ipfb_ml_params;
 
 int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
@@ -302,9 +321,10 @@ int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, 
  *
  * ipfb_net_forward: y = net(xin).  Workspace ipfb_net_workspace_size(IPFB_NET_FORWARD).
  *   Layer 2 waits for its tensor-core accumulators with a bound of about a second
- *   of SM clocks; a CTA that gives up writes NaN at the first output frame of its
- *   tile and stops (so a learned solve sees a non-finite residual and falls back
- *   to plain CG).  The call itself returns 0: the status is in y.
+ *   of SM clocks (ipfb_set_net_wait_limit); a CTA that gives up writes NaN at the
+ *   first output frame of its tile, waits for its MMAs in flight and stops (a
+ *   learned solve then falls back to plain CG).  The call itself returns 0: the
+ *   status is in y.
  * ipfb_net_grad: loss = sum over slots and frames of (y - target)^2 / (nslots J)
  *   (device float [1], may be NULL) and its gradient with respect to theta
  *   (device float [IPFB_NET_NPARAMS], may be NULL), the BF16 rounding of weights

@@ -10,8 +10,13 @@ shared by all columns, BF16 operands with FP32 accumulation on the GPU.
 Readings:
   * input of column n: the Wiener-preconditioned residual u = M_W r (Eq. wiener
     weights applied as the ML preconditioner) scaled by its RMS s, and the prior
-    mask m; output z = u + s * g(u / s, m)  (a learned correction of the Wiener
-    preconditioner);
+    mask m; output z = u + lam mbar M_W(s g(u / s, m)) = M_W(r + lam mbar s g), a
+    learned correction of the Wiener preconditioner passed through it: mode k of the
+    correction is scaled by the prior's share of the Wiener denominator,
+    rho(k) = lam mbar / (|W(k)|^2 / sigma^2 + lam mbar) (lam mbar = prior weight x
+    the column's mask mean), so it acts where the prior term dominates (the
+    near-null eigenvalues of App. A) and leaves the modes the Wiener step already
+    resolves nearly untouched;
   * GELU in its exact form x Phi(x) = 0.5 x (1 + erf(x / sqrt 2)) (Hendrycks and
     Gimpel 2016), the standard normal CDF Phi written through erf;
   * training target: the CG error e = x* - x_k of the residual r_k = A e; loss
@@ -149,11 +154,12 @@ def net_input(u: np.ndarray, m: np.ndarray):
     return np.stack([(u / s).T, m.T.astype(np.float64)], axis=1), s   # [ncols, 2, J]
 
 
-def apply_precond(p: dict, u: np.ndarray, m: np.ndarray, emulate_bf16: bool = False) -> np.ndarray:
-    """z = u + s g(u/s, m), column by column.  u, m: [J, ncols]."""
+def apply_precond(p: dict, u: np.ndarray, m: np.ndarray, wiener, lam_mbar, emulate_bf16: bool = False) -> np.ndarray:
+    """z = u + lam mbar M_W(s g(u/s, m)), column by column.  u, m: [J, ncols];
+    wiener(V) applies M_W to the columns of V; lam_mbar: [ncols] (or a scalar)."""
     xin, s = net_input(u, m)
     g = forward(p, xin, emulate_bf16)          # [ncols, J]
-    return u + (g * s[:, None]).T
+    return u + np.asarray(lam_mbar, dtype=np.float64) * wiener((g * s[:, None]).T)
 
 
 class Adam:

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/ipfb.h"
+#include "abi.h"
 #include "launch.h"
 
 using namespace ipfb;
@@ -22,6 +23,9 @@ thread_local char g_cuda_err[256] = "";
 bool misaligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; }
 
 size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// request counters and status words of the learned solve
+constexpr int kFcgCounters = 8;
 
 // Workspace of the learned-preconditioner solve: the pair-packed data d, the
 // flexible-CG vectors, the net requests and outputs, per-column state, two request
@@ -44,13 +48,15 @@ FcgLayout fcg_layout(int N, int J) {
   L.mb = o;
   o = al256(o + (size_t)(N / 2) * (size_t)fcg_threads(J) * sizeof(uint32_t));
   L.cnt = o;
-  o = al256(o + 4 * sizeof(int));
+  o = al256(o + kFcgCounters * sizeof(int));
   L.pack = o;
   o = al256(o + net_pack_bytes());
   L.total = o;
   return L;
 }
 std::atomic<int> g_max_column_run{8192};
+// bound on the net forward's accumulator wait in SM clocks (< 0: the built-in ~1 s)
+std::atomic<long long> g_net_wait_limit{-1};
 
 // ---------------------------------------------------------------- stage timing
 // When enabled, every kernel launch of a compute call is bracketed by two CUDA
@@ -97,12 +103,6 @@ struct Stage {
   }
 };
 
-int cuda_fail(cudaError_t e, const char* where) {
-  if (e == cudaErrorNotSupported) return IPFB_ERR_UNSUPPORTED;
-  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", where, cudaGetErrorString(e));
-  return IPFB_ERR_CUDA;
-}
-
 #define CK(call, where)                                 \
   do {                                                  \
     cudaError_t e_ = (call);                            \
@@ -112,20 +112,6 @@ int cuda_fail(cudaError_t e, const char* where) {
 bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
-
-constexpr int kMaxTapsAbi = 16;
-
-int check_geom(const ipfb_geom* g, bool need_inverse) {
-  if (!g) return IPFB_ERR_INVALID;
-  if (g->lblock < 2 || g->ntap < 1 || g->nframes < 1) return IPFB_ERR_INVALID;
-  if (!is_pow2(g->lblock) || g->lblock < 64 || g->lblock > 16384) return IPFB_ERR_UNSUPPORTED;
-  if (g->ntap > kMaxTapsAbi) return IPFB_ERR_UNSUPPORTED;
-  if (g->periodic != 1) return IPFB_ERR_UNSUPPORTED;
-  if (need_inverse) {
-    if (!is_pow2(g->nframes) || g->nframes < 16 || g->nframes > 65536) return IPFB_ERR_UNSUPPORTED;
-  }
-  return IPFB_OK;
-}
 
 // column cluster split of J frames: C CTAs of S = J/C frames each (S <= max run)
 void column_split(int J, int* C, int* S) {
@@ -169,6 +155,30 @@ int check_noise(double noise_level) {
 
 }  // namespace
 
+namespace ipfb {
+
+constexpr int kMaxTapsAbi = 16;
+
+int check_geom(const ipfb_geom* g, bool need_inverse) {
+  if (!g) return IPFB_ERR_INVALID;
+  if (g->lblock < 2 || g->ntap < 1 || g->nframes < 1) return IPFB_ERR_INVALID;
+  if (!is_pow2(g->lblock) || g->lblock < 64 || g->lblock > 16384) return IPFB_ERR_UNSUPPORTED;
+  if (g->ntap > kMaxTapsAbi) return IPFB_ERR_UNSUPPORTED;
+  if (g->periodic != 1) return IPFB_ERR_UNSUPPORTED;
+  if (need_inverse) {
+    if (!is_pow2(g->nframes) || g->nframes < 16 || g->nframes > 65536) return IPFB_ERR_UNSUPPORTED;
+  }
+  return IPFB_OK;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  if (e == cudaErrorNotSupported) return IPFB_ERR_UNSUPPORTED;
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", where, cudaGetErrorString(e));
+  return IPFB_ERR_CUDA;
+}
+
+}  // namespace ipfb
+
 extern "C" {
 
 const char* ipfb_strerror(int status) {
@@ -186,7 +196,7 @@ const char* ipfb_strerror(int status) {
 
 const char* ipfb_last_cuda_error(void) { return g_cuda_err; }
 
-int ipfb_version(void) { return 100; }
+int ipfb_version(void) { return 101; }
 
 int ipfb_stage_timing(int enable) {
   std::lock_guard<std::mutex> lk(g_tmu);
@@ -233,6 +243,11 @@ int ipfb_stage_times(char* names, size_t names_cap, double* ms, int* counts, int
   return n;
 }
 
+int ipfb_set_net_wait_limit(long long cycles) {
+  g_net_wait_limit.store(cycles < 0 ? -1 : cycles);
+  return IPFB_OK;
+}
+
 int ipfb_set_max_column_run(int frames) {
   if (frames != 512 && frames != 8192) return IPFB_ERR_INVALID;
   g_max_column_run.store(frames);
@@ -247,7 +262,7 @@ int ipfb_workspace_size(const ipfb_geom* g, int op, size_t* bytes) {
     case IPFB_OP_FORWARD:
       rc = check_geom(g, false);
       if (rc) return rc;
-      *bytes = 2 * (size_t)(g->lblock / 2 + 1) * sizeof(double);
+      *bytes = forward_ws_bytes(g->lblock);
       return IPFB_OK;
     case IPFB_OP_WIENER:
     case IPFB_OP_WIENER_UPCHAN:
@@ -521,12 +536,118 @@ MLParams ml_params(const ipfb_geom* g, const ipfb_ml_params* prm, int use_x0) {
   mp.ntap = g->ntap;
   mp.precond = prm->precond;
   mp.use_x0 = use_x0 ? 1 : 0;
+  mp.net_from = prm->net_from;
   return mp;
 }
 
-// Flexible CG with the learned preconditioner: two launches per iteration (the CG
-// step with its preconditioner request, then the net over the requests); the host
-// reads the number of open requests every fourth iteration and stops at zero.
+// ---------------------------------------------------------------- learned solve
+// The learned solve is one CUDA graph (no host synchronisation, no read-back):
+//   k2, [initial guess to pairs], net pack, counters cleared, FCG phase 0,
+//   loop control, WHILE { net, FCG step, net, FCG step, loop control },
+//   FCG finish, fallback check, IF { [initial guess to pairs], plain CG },
+//   pairs to time order.
+// The WHILE body is two flexible-CG iterations with the two request counters in
+// fixed roles; the loop control kernel keeps it running while a column is active.
+// When the caller's stream is not capturing, the graph is captured on a private stream,
+// instantiated, launched on the caller's stream and released (the release waits for
+// the launch to finish on the device, not on the host); when it is capturing, the same
+// nodes go into the caller's graph.
+struct Capture {
+  cudaStream_t user = nullptr, cap = nullptr, body = nullptr;
+  cudaStream_t own_cap = nullptr;
+  bool own = false, active = false, body_active = false;
+  ~Capture() {
+    end_body();
+    if (own && active) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(own_cap, &g);
+      if (g) cudaGraphDestroy(g);
+    }
+    if (own_cap) cudaStreamDestroy(own_cap);
+    if (body) cudaStreamDestroy(body);
+  }
+  void end_body() {
+    if (body_active) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(body, &g);
+      body_active = false;
+    }
+  }
+};
+
+int capture_begin(Capture& c, cudaStream_t user) {
+  c.user = user;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(user, &cs), "cudaStreamIsCapturing");
+  CK(cudaStreamCreateWithFlags(&c.body, cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
+  if (cs == cudaStreamCaptureStatusActive) {
+    c.cap = user;
+    c.own = false;
+    return IPFB_OK;
+  }
+  if (cs != cudaStreamCaptureStatusNone) return IPFB_ERR_INVALID;  // an invalidated capture
+  CK(cudaStreamCreateWithFlags(&c.own_cap, cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
+  CK(cudaStreamBeginCapture(c.own_cap, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
+  c.cap = c.own_cap;
+  c.own = true;
+  c.active = true;
+  return IPFB_OK;
+}
+
+// a conditional handle on the graph being captured
+int capture_handle(Capture& c, unsigned int dflt, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamGetCaptureInfo(c.cap, &cs, nullptr, &g, nullptr, nullptr, nullptr), "cudaStreamGetCaptureInfo");
+  CK(cudaGraphConditionalHandleCreate(h, g, dflt, cudaGraphCondAssignDefault), "cudaGraphConditionalHandleCreate");
+  return IPFB_OK;
+}
+
+// append a conditional node after the captured work and start capturing its body on c.body
+int capture_conditional(Capture& c, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(c.cap, &cs, nullptr, &g, &deps, &ed, &nd), "cudaStreamGetCaptureInfo");
+  cudaGraphNodeParams prm = {};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = h;
+  prm.conditional.type = type;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  CK(cudaGraphAddNode(&node, g, deps, ed, nd, &prm), "cudaGraphAddNode");
+  CK(cudaStreamUpdateCaptureDependencies(c.cap, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
+     "cudaStreamUpdateCaptureDependencies");
+  CK(cudaStreamBeginCaptureToGraph(c.body, prm.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeRelaxed),
+     "cudaStreamBeginCaptureToGraph");
+  c.body_active = true;
+  return IPFB_OK;
+}
+
+int capture_end_body(Capture& c) {
+  cudaGraph_t g = nullptr;
+  c.body_active = false;
+  CK(cudaStreamEndCapture(c.body, &g), "cudaStreamEndCapture");
+  return IPFB_OK;
+}
+
+int capture_finish(Capture& c) {
+  if (!c.own) return IPFB_OK;
+  cudaGraph_t g = nullptr;
+  c.active = false;
+  CK(cudaStreamEndCapture(c.cap, &g), "cudaStreamEndCapture");
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ex, c.user);
+  if (ex) cudaGraphExecDestroy(ex);
+  cudaGraphDestroy(g);
+  CK(e, "cudaGraphLaunch");
+  return IPFB_OK;
+}
+
 int ml_solve_learned(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
                      const ipfb_ml_params* prm, const uint8_t* mask, const float* prior, const float* theta,
                      float* x_inout, int use_x0, int* iters, float* resid, void* ws, size_t ws_bytes,
@@ -549,80 +670,56 @@ int ml_solve_learned(const ipfb_geom* g, const uint8_t* codes, const float* scal
   b.netin = reinterpret_cast<float*>(w + L.netin);
   b.cs = reinterpret_cast<FcgCol*>(w + L.cs);
   b.mb = reinterpret_cast<uint32_t*>(w + L.mb);
+  // counters: [0], [1] open requests (alternating roles), [2] loop trips, [3] net
+  // status, [4] fallback taken
   int* cnt = reinterpret_cast<int*>(w + L.cnt);
   uint8_t* packed = w + L.pack;
-  {
-    Stage t("k2_unpack_irfft", st);
-    CK(launch_k2(N / 2, codes, scale, const_cast<float2*>(d2), 1, J, st), "k2_unpack_irfft");
-    t.done();
-  }
-  if (use_x0) {
-    Stage t("k_time_to_pairs", st);
-    CK(launch_time_to_pairs(x_inout, b.X, N, J, st), "k_time_to_pairs");
-    t.done();
-  }
-  {
-    Stage t("k6_net_pack", st);
-    CK(launch_net_pack(theta, packed, st), "k6_net_pack");
-    t.done();
-  }
-  CK(cudaMemsetAsync(cnt, 0, 4 * sizeof(int), st), "cudaMemsetAsync");
   const MLParams mp = ml_params(g, prm, use_x0);
+  const int max_trips = (prm->max_iter + 1) / 2;
+  const long long wl = g_net_wait_limit.load();
+
+  Stage t("k5_fcg_solve", st);
+  Capture c;
+  if ((rc = capture_begin(c, st))) return rc;
+  cudaStream_t s = c.cap;
+  CK(launch_k2(N / 2, codes, scale, const_cast<float2*>(d2), 1, J, s), "k2_unpack_irfft");
+  if (use_x0) CK(launch_time_to_pairs(x_inout, b.X, N, J, s), "k_time_to_pairs");
+  CK(launch_net_pack(theta, packed, s), "k6_net_pack");
+  CK(cudaMemsetAsync(cnt, 0, kFcgCounters * sizeof(int), s), "cudaMemsetAsync");
+  CK(launch_fcg_step(J, 0, d2, b, mask, prior, window, N, mp, cnt, s), "k5_fcg_step");
+  cudaGraphConditionalHandle hl;
+  if ((rc = capture_handle(c, 0, &hl))) return rc;
+  CK(launch_fcg_loop_ctrl(b, N, cnt + 2, max_trips, hl, s), "k_fcg_loop_ctrl");
+  if ((rc = capture_conditional(c, hl, cudaGraphCondTypeWhile))) return rc;
   {
-    Stage t("k5_fcg_step", st);
-    CK(launch_fcg_step(J, 0, d2, b, mask, prior, window, N, mp, cnt, st), "k5_fcg_step");
-    t.done();
-  }
-  int parity = 0;
-  for (int it = 0; it < prm->max_iter; ++it) {
-    {
-      Stage t("k6_net_forward", st);
-      CK(launch_net_forward(packed, b.netin, b.Y, J, 0, cnt + parity, cnt + (parity ^ 1), N, st),
+    cudaStream_t bs = c.body;
+    for (int h = 0; h < 2; ++h) {
+      CK(launch_net_forward(packed, b.netin, b.Y, J, 0, cnt + h, cnt + (h ^ 1), N, wl, cnt + 3, bs),
          "k6_net_forward");
-      t.done();
+      CK(launch_fcg_step(J, 2, d2, b, mask, prior, window, N, mp, cnt + (h ^ 1), bs), "k5_fcg_step");
     }
-    {
-      Stage t("k5_fcg_step", st);
-      CK(launch_fcg_step(J, it == 0 ? 1 : 2, d2, b, mask, prior, window, N, mp, cnt + (parity ^ 1), st),
-         "k5_fcg_step");
-      t.done();
-    }
-    parity ^= 1;
-    if ((it & 3) == 3) {
-      int open = 0;
-      CK(cudaMemcpyAsync(&open, cnt + parity, sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
-      CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
-      if (open == 0) break;
-    }
+    CK(launch_fcg_loop_ctrl(b, N, cnt + 2, max_trips, hl, bs), "k_fcg_loop_ctrl");
   }
+  if ((rc = capture_end_body(c))) return rc;
+  CK(launch_fcg_finish(J, d2, b, mask, prior, window, N, mp, iters, resid, s), "k5_fcg_finish");
+  // Fallback: a net that returns a non-finite value leaves a non-finite residual in the
+  // columns it touched (flexible CG cannot recover from it), and a net that gave up
+  // waiting left some of its outputs unwritten.  Then the whole solve is redone by plain
+  // CG from the same start, so the caller gets plain CG's answer, iterations and residuals.
+  cudaGraphConditionalHandle hf;
+  if ((rc = capture_handle(c, 0, &hf))) return rc;
+  CK(launch_fcg_fallback_check(resid, 2 * N, cnt + 3, cnt + 4, hf, s), "k_fcg_fallback_check");
+  if ((rc = capture_conditional(c, hf, cudaGraphCondTypeIf))) return rc;
   {
-    Stage t("k5_fcg_finish", st);
-    CK(launch_fcg_finish(J, d2, b, mask, prior, window, N, mp, iters, resid, st), "k5_fcg_finish");
-    t.done();
-  }
-  // Fallback: a net that returns a non-finite value leaves a non-finite residual in
-  // the columns it touched (flexible CG cannot recover from it).  Then the whole solve
-  // is redone by plain CG from the same start, so the caller gets plain CG's answer,
-  // iteration counts and residuals.
-  std::vector<float> rh((size_t)2 * N);
-  CK(cudaMemcpyAsync(rh.data(), resid, rh.size() * sizeof(float), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
-  CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
-  bool finite = true;
-  for (float v : rh) finite = finite && std::isfinite(v);
-  if (!finite) {
-    if (use_x0) {
-      Stage t("k_time_to_pairs", st);
-      CK(launch_time_to_pairs(x_inout, b.X, N, J, st), "k_time_to_pairs");
-      t.done();
-    }
+    cudaStream_t bs = c.body;
+    if (use_x0) CK(launch_time_to_pairs(x_inout, b.X, N, J, bs), "k_time_to_pairs");
     MLParams plain = mp;
     plain.precond = 0;
-    Stage t("k5_ml_cg", st);
-    CK(launch_k5(J, d2, b.X, mask, prior, window, N, plain, iters, resid, st), "k5_ml_cg");
-    t.done();
+    CK(launch_k5(J, d2, b.X, mask, prior, window, N, plain, iters, resid, bs), "k5_ml_cg");
   }
-  Stage t("k_pairs_to_time", st);
-  CK(launch_pairs_to_time(b.X, x_inout, N, 1, J, st), "k_pairs_to_time");
+  if ((rc = capture_end_body(c))) return rc;
+  CK(launch_pairs_to_time(b.X, x_inout, N, 1, J, s), "k_pairs_to_time");
+  if ((rc = capture_finish(c))) return rc;
   t.done();
   return IPFB_OK;
 }
@@ -639,7 +736,7 @@ int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, 
       misaligned16(codes))
     return IPFB_ERR_INVALID;
   if (!(prm->noise_var > 0.0) || !std::isfinite(prm->noise_var) || !(prm->prior_weight >= 0.0) ||
-      !std::isfinite(prm->prior_weight) || !(prm->tol >= 0.0) || prm->max_iter < 0)
+      !std::isfinite(prm->prior_weight) || !(prm->tol >= 0.0) || prm->max_iter < 0 || prm->net_from < 0)
     return IPFB_ERR_INVALID;
   if (prm->precond < 0 || prm->precond > 2) return IPFB_ERR_INVALID;
   if (prm->precond == 2) {
@@ -737,7 +834,9 @@ int ipfb_net_forward(const float* theta, int nslots, int nframes, const float* x
   uint8_t* packed = static_cast<uint8_t*>(ws);
   CK(launch_net_pack(theta, packed, st), "k6_net_pack");
   Stage t("k6_net_forward", st);
-  CK(launch_net_forward(packed, xin, y, nframes, nslots, nullptr, nullptr, nslots, st), "k6_net_forward");
+  CK(launch_net_forward(packed, xin, y, nframes, nslots, nullptr, nullptr, nslots, g_net_wait_limit.load(), nullptr,
+                        st),
+     "k6_net_forward");
   t.done();
   return IPFB_OK;
 }

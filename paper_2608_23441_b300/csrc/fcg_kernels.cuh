@@ -1,6 +1,7 @@
 // Flexible conjugate gradient (Notay 2000, Polak-Ribiere beta) for the ML solve of
 // Sec. 4.2 (Eq. chi squared) with the learned preconditioner
-//     z = u + s g(u / s, m),   u = M_W r (the Wiener preconditioner),  s = RMS(u),
+//     z = u + lam mbar M_W(s g(u / s, m)),   u = M_W r (the Wiener preconditioner),
+//     s = RMS(u), lam mbar = prior weight x the column's mask mean,
 // g the convolutional net of net_kernels.cuh applied per column.  Because g is
 // nonlinear the outer iteration is flexible CG:
 //     alpha = r.z / p.Ap,  x += alpha p,  r -= alpha Ap,
@@ -69,12 +70,13 @@ __device__ __forceinline__ uint32_t load_mbits(const uint8_t* __restrict__ mask,
 }
 
 // u = M_W r for this CTA's pair (r in registers -> u in registers), RMS scales of u,
-// request slots for the active columns, and the net input rows
+// request slots for the columns in `req` (bit 0: column 2p, bit 1: 2p + 1), and their
+// net input rows
 //   netin[slot][0][j] = u_j / s,  netin[slot][1][j] = m_j.
 template <int J, int T, int NT>
 __device__ __forceinline__ void fcg_request(const float2 (&r)[J / T], float2 (&u)[J / T], float2* sm_f, float* part,
                                             double* res, int* sflag, const float* ta, const float* tb, int ntap,
-                                            float inv_s2, float lam_ma, float lam_mb, int act, uint32_t mbits,
+                                            float inv_s2, float lam_ma, float lam_mb, int req, uint32_t mbits,
                                             int* __restrict__ counter, float* __restrict__ netin, float& s_a,
                                             float& s_b, int& slot_a, int& slot_b) {
   constexpr int EPT = J / T;
@@ -95,9 +97,9 @@ __device__ __forceinline__ void fcg_request(const float2 (&r)[J / T], float2 (&u
   s_a = res[0] > 0.0 ? sqrtf((float)(res[0] / (double)J)) : 1.0f;
   s_b = res[1] > 0.0 ? sqrtf((float)(res[1] / (double)J)) : 1.0f;
   if (tid == 0) {
-    const int base = atomicAdd(counter, __popc(act & 3));
-    sflag[0] = (act & 1) ? base : -1;
-    sflag[1] = (act & 1) ? ((act & 2) ? base + 1 : -1) : ((act & 2) ? base : -1);
+    const int base = req ? atomicAdd(counter, __popc(req & 3)) : 0;
+    sflag[0] = (req & 1) ? base : -1;
+    sflag[1] = (req & 1) ? ((req & 2) ? base + 1 : -1) : ((req & 2) ? base : -1);
   }
   __syncthreads();
   slot_a = sflag[0];
@@ -127,8 +129,9 @@ constexpr size_t fcg_smem_bytes() {
          4 * sizeof(int);
 }
 
-// phase 0: r0 = b - A x0, first request.  phase 1: z0 from the net, p = z0.
-// phase 2: z from the net, Polak-Ribiere beta, p update.  Phases 1 and 2 then take
+// phase 0: r0 = b - A x0, first request, P = Z = 0.  phase 1: z0 from the net, p = z0.
+// phase 2: z from the net, Polak-Ribiere beta, p update (with rz = 0 after phase 0,
+// beta is 0 and phase 2 does what phase 1 does).  Phases 1 and 2 then take
 // one CG step and issue the next request for the columns still active.
 template <int J, int T, int RMAX, int NT>
 __global__ void __launch_bounds__(T, 1)
@@ -205,26 +208,54 @@ k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, fl
     sa.iters = sb.iters = 0;
     sa.rz = sb.rz = 0.0;
     sa.slot = sb.slot = -1;
+    // P and Z start at zero, so that the first step after the net (rz = 0, beta = 0)
+    // can run as phase 2 too: a graph loop body then repeats one fixed launch
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) R[vb + (size_t)e * T] = r[e];
+    for (int e = 0; e < EPT; ++e) {
+      R[vb + (size_t)e * T] = r[e];
+      Pv[vb + (size_t)e * T] = make_float2(0.0f, 0.0f);
+      Z[vb + (size_t)e * T] = make_float2(0.0f, 0.0f);
+    }
   } else {
     mbits = mbc[(size_t)p * T + tid];
     const bool aa = sa.active, ab = sb.active;
+    // columns whose preconditioner request went to the net this iteration
+    const bool na = aa && sa.slot >= 0, nb = ab && sb.slot >= 0;
     float2 z[EPT];
 #pragma unroll
-    for (int q = 0; q < EPT / 4; ++q) {
-      const float4 va = aa ? reinterpret_cast<const float4*>(Y + (size_t)sa.slot * J + j0)[q]
-                           : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      const float4 vb4 = ab ? reinterpret_cast<const float4*>(Y + (size_t)sb.slot * J + j0)[q]
-                            : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      const float ya[4] = {va.x, va.y, va.z, va.w}, yb[4] = {vb4.x, vb4.y, vb4.z, vb4.w};
+    for (int e = 0; e < EPT; ++e) {
+      r[e] = R[vb + (size_t)e * T];
+      z[e] = U[vb + (size_t)e * T];
+    }
+    if (na || nb) {
+      // z = u + lam mbar M_W(s y) = M_W(r + lam mbar s y): the net's output enters
+      // through the Wiener preconditioner weighted by the column's prior term, i.e.
+      // mode k of it is scaled by rho(k) = lam mbar / (|W(k)|^2 / sigma^2 + lam mbar),
+      // near 1 where the prior dominates (the near-null eigenvalues of App. A) and
+      // near 0 where the Wiener step already resolves the mode, which is left as it is.
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int e = 4 * q + i;
-        r[e] = R[vb + (size_t)e * T];
-        const float2 u = U[vb + (size_t)e * T];
-        z[e] = make_float2(aa ? fmaf(sa.s, ya[i], u.x) : 0.0f, ab ? fmaf(sb.s, yb[i], u.y) : 0.0f);
+      for (int q = 0; q < EPT / 4; ++q) {
+        const float4 va = na ? reinterpret_cast<const float4*>(Y + (size_t)sa.slot * J + j0)[q]
+                             : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const float4 vb4 = nb ? reinterpret_cast<const float4*>(Y + (size_t)sb.slot * J + j0)[q]
+                              : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const float ya[4] = {va.x, va.y, va.z, va.w}, yb[4] = {vb4.x, vb4.y, vb4.z, vb4.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sm_f[pidx(j0 + 4 * q + i)] = make_float2(sa.s * ya[i], sb.s * yb[i]);
       }
+      __syncthreads();
+      wiener_precond_pair<J, T, NT>(sm_f, ta, tb, mp.ntap, mp.inv_s2, sa.lam_m, sb.lam_m);
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const float2 c = sm_f[pidx(j0 + e)];
+        if (na) z[e].x = fmaf(sa.lam_m, c.x, z[e].x);
+        if (nb) z[e].y = fmaf(sb.lam_m, c.y, z[e].y);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      if (!aa) z[e].x = 0.0f;
+      if (!ab) z[e].y = 0.0f;
     }
     // r.z_new (and r.z_old for the Polak-Ribiere beta)
     float q[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -296,11 +327,14 @@ k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, fl
     }
   }
   const int act = (sa.active ? 1 : 0) | (sb.active ? 2 : 0);
+  // the net is asked only from a column's net_from-th preconditioner application on;
+  // before that its z is the Wiener term alone
+  const int req = (sa.active && sa.iters >= mp.net_from ? 1 : 0) | (sb.active && sb.iters >= mp.net_from ? 2 : 0);
   if (act) {
     float2 u[EPT];
     float s_a, s_b;
     int sl_a, sl_b;
-    fcg_request<J, T, NT>(r, u, sm_f, part, res, sflag, ta, tb, mp.ntap, mp.inv_s2, sa.lam_m, sb.lam_m, act, mbits,
+    fcg_request<J, T, NT>(r, u, sm_f, part, res, sflag, ta, tb, mp.ntap, mp.inv_s2, sa.lam_m, sb.lam_m, req, mbits,
                           counter, netin, s_a, s_b, sl_a, sl_b);
 #pragma unroll
     for (int e = 0; e < EPT; ++e) U[vb + (size_t)e * T] = u[e];

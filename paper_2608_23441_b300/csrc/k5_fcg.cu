@@ -79,4 +79,56 @@ cudaError_t launch_net_pairs(int J, const float2* xs, const float2* xk, const in
 #undef IPFB_FCG_J
 
 size_t fcg_col_bytes() { return sizeof(FcgCol); }
+
+namespace {
+// One trip of the learned solve's graph loop is done (or about to start): count it and
+// keep the loop running while any column is still active and trips remain.  (Open net
+// requests are not the test: before net_from a column is active without asking the net.)
+__global__ void __launch_bounds__(256)
+k_fcg_loop_ctrl(const FcgCol* __restrict__ cs, int ncols, int* __restrict__ trips, int max_trips,
+                cudaGraphConditionalHandle h) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int i = threadIdx.x; i < ncols; i += blockDim.x) mine |= cs[i].active;
+  if (mine) atomicOr(&any, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int t = *trips + 1;
+    *trips = t;
+    cudaGraphSetConditional(h, (any && t <= max_trips) ? 1u : 0u);
+  }
+}
+
+// The plain-CG fallback runs when any per-column residual is not finite (a net that
+// returned NaN or Inf) or when the net gave up waiting for its accumulators.
+__global__ void __launch_bounds__(256)
+k_fcg_fallback_check(const float* __restrict__ resid, int n2, const int* __restrict__ net_status,
+                     int* __restrict__ flag, cudaGraphConditionalHandle h) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = *net_status != 0;
+  __syncthreads();
+  int mine = 0;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) mine |= !isfinite(resid[i]);
+  if (mine) atomicOr(&bad, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *flag = bad;
+    cudaGraphSetConditional(h, bad ? 1u : 0u);
+  }
+}
+}  // namespace
+
+cudaError_t launch_fcg_loop_ctrl(const FcgBufs& b, int ncols, int* trips, int max_trips,
+                                 cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_fcg_loop_ctrl<<<1, 256, 0, st>>>(b.cs, ncols, trips, max_trips, h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fcg_fallback_check(const float* resid, int n2, const int* net_status, int* flag,
+                                      cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_fcg_fallback_check<<<1, 256, 0, st>>>(resid, n2, net_status, flag, h);
+  return cudaGetLastError();
+}
 }  // namespace ipfb

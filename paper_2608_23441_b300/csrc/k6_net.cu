@@ -47,7 +47,8 @@ cudaError_t launch_net_pack(const float* theta, uint8_t* packed, cudaStream_t st
 }
 
 cudaError_t launch_net_forward(const uint8_t* packed, const float* in, float* y, int J, int nslots_host,
-                               const int* count, int* zero_other, int max_slots, cudaStream_t st) {
+                               const int* count, int* zero_other, int max_slots, long long wait_limit, int* status,
+                               cudaStream_t st) {
   const size_t smem = fwd_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(k6_net_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -57,7 +58,8 @@ cudaError_t launch_net_forward(const uint8_t* packed, const float* in, float* y,
   const int res = resident_ctas_tmem((const void*)k6_net_forward, 256, smem, kNetTmemCols);
   if (res <= 0) return cudaErrorInvalidConfiguration;
   const long long grid = items < res ? (items < 1 ? 1 : items) : res;
-  k6_net_forward<<<(unsigned)grid, 256, smem, st>>>(packed, in, y, J, nslots_host, count, zero_other);
+  k6_net_forward<<<(unsigned)grid, 256, smem, st>>>(packed, in, y, J, nslots_host, count, zero_other,
+                                                    wait_limit < 0 ? kNetMmaWait : wait_limit, status);
   return cudaGetLastError();
 }
 

@@ -54,6 +54,7 @@ struct MLParams {
   int ntap;
   int precond;   // 0 none, 1 Wiener, 2 learned (flexible CG)
   int use_x0;    // 1: x2 holds the initial guess
+  int net_from = 0;  // learned: preconditioner applications before the net joins (Wiener alone)
 };
 
 cudaError_t launch_k5(int J, const float2* d2, float2* x2, const uint8_t* mask, const float* prior,
@@ -87,6 +88,13 @@ size_t fcg_col_bytes();
 cudaError_t launch_fcg_step(int J, int phase, const float2* d2, const FcgBufs& b, const uint8_t* mask,
                             const float* prior, const float* window, int N, const MLParams& mp, int* counter,
                             cudaStream_t st);
+// device-side control of the learned solve's graph: the loop condition (a column still
+// active and fewer than max_trips trips) and the plain-CG fallback condition (a
+// non-finite residual among the 2 N values, or a net that gave up waiting)
+cudaError_t launch_fcg_loop_ctrl(const FcgBufs& b, int ncols, int* trips, int max_trips,
+                                 cudaGraphConditionalHandle h, cudaStream_t st);
+cudaError_t launch_fcg_fallback_check(const float* resid, int n2, const int* net_status, int* flag,
+                                      cudaGraphConditionalHandle h, cudaStream_t st);
 cudaError_t launch_fcg_finish(int J, const float2* d2, const FcgBufs& b, const uint8_t* mask, const float* prior,
                               const float* window, int N, const MLParams& mp, int* iters, float* resid,
                               cudaStream_t st);
@@ -98,8 +106,11 @@ int net_nparams();
 long long net_bwd_items(int nslots, int J);
 long long net_fwd_items(int nslots, int J);
 cudaError_t launch_net_pack(const float* theta, uint8_t* packed, cudaStream_t st);
+// wait_limit < 0: the default bound on the accumulator wait (about a second);
+// status (or nullptr) is set nonzero by a CTA that gave up waiting
 cudaError_t launch_net_forward(const uint8_t* packed, const float* in, float* y, int J, int nslots_host,
-                               const int* count, int* zero_other, int max_slots, cudaStream_t st);
+                               const int* count, int* zero_other, int max_slots, long long wait_limit, int* status,
+                               cudaStream_t st);
 cudaError_t launch_net_backward(const uint8_t* packed, const float* in, const float* target, int J, int nslots,
                                 float inv_n, float* part, cudaStream_t st);
 cudaError_t launch_net_reduce(const float* part, long long nitems, float* grad, float* loss, cudaStream_t st);

@@ -307,9 +307,15 @@ static_assert(FO_A1C % 1024 == 0 && FO_A2 % 16 == 0 && FO_W1 % 16 == 0 && FO_W3 
 constexpr uint32_t kNetTmemCols = 64;
 constexpr long long kNetMmaWait = 2000000000LL;  // SM clocks (~1 s)
 
+// wait_limit: SM clocks the accumulator wait may take before the CTA gives up (the
+// library passes kNetMmaWait unless a test lowers it).  A CTA that gives up marks the
+// first output of its tile with NaN, sets *status (when not null), waits up to
+// kNetMmaWait more for its MMAs in flight so that nothing still writes its tensor
+// memory or reads its shared memory, frees its tensor memory and stops.
 __global__ void __launch_bounds__(256)
 k6_net_forward(const uint8_t* __restrict__ packed, const float* __restrict__ in, float* __restrict__ y, int J,
-               int nslots_host, const int* __restrict__ count, int* __restrict__ zero_other) {
+               int nslots_host, const int* __restrict__ count, int* __restrict__ zero_other, long long wait_limit,
+               int* __restrict__ status) {
   extern __shared__ __align__(1024) uint8_t smfwd[];
   __shared__ __align__(8) uint64_t mma_bar;
   __shared__ uint32_t tmem_slot;
@@ -391,12 +397,17 @@ k6_net_forward(const uint8_t* __restrict__ packed, const float* __restrict__ in,
     }
     // one thread waits on the barrier; the others sleep in the block barrier below
     bool late = false;
-    if (threadIdx.x == 0) late = !tc::mbar_wait(smem_u32(&mma_bar), phase, kNetMmaWait);
-    phase ^= 1;
-    if (__syncthreads_or(late)) {  // the accumulators never arrived: mark the slot's output, stop
-      if (threadIdx.x == 0) y[(size_t)slot * J + p0] = __int_as_float(0x7fc00000);
+    if (threadIdx.x == 0) late = !tc::mbar_wait(smem_u32(&mma_bar), phase, wait_limit);
+    if (__syncthreads_or(late)) {  // the accumulators did not arrive in time: mark, drain, stop
+      if (threadIdx.x == 0) {
+        y[(size_t)slot * J + p0] = __int_as_float(0x7fc00000);
+        if (status) atomicOr(status, 1);
+        (void)tc::mbar_wait(smem_u32(&mma_bar), phase, kNetMmaWait);
+      }
+      __syncthreads();
       break;
     }
+    phase ^= 1;
     tc::fence_after();
     {
       const int qd = warp & 3, mb = warp >> 2;

@@ -11,10 +11,13 @@
 //
 // The scratch: a file-scope __device__ array of kNoallocSums doubles, enough for
 // lblock <= 16384.  Every GPU that loads the library holds it (131 KB) until the
-// process exits.  Host code cannot use the array's name as a device address, so the
-// address is obtained with cudaGetSymbolAddress once per device, with that device
-// current, the first time the entry point runs there.  That first call therefore
-// does one extra runtime query; make it before any stream capture.
+// process exits.  Host code cannot use the array's name as a device address, so
+// every call asks the runtime for the array's address on the current device
+// (cudaGetSymbolAddress, a host-side lookup that allocates nothing), with that
+// device current.  Asking on every call, rather than caching the answer per
+// device, keeps the address right after a device reset, when the library's device
+// code is loaded again and the array may move.  The first call on a device also
+// loads that device code there; make it before any stream capture.
 //
 // All calls share the one array and it keeps the previous call's contents: each
 // call clears the sums on its stream before use, and calls whose work overlaps on
@@ -22,58 +25,44 @@
 // on the array and give wrong scales.  Serialize them.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/ipfb.h"
+#include "abi.h"
 #include "launch.h"
 
 namespace {
 
 constexpr int kNoallocMaxLblock = 16384;
 constexpr int kNoallocSums = 2 * (kNoallocMaxLblock / 2 + 1);
+// the array holds exactly what pfb_forward asks of its workspace at the largest lblock
+static_assert(kNoallocSums * sizeof(double) >= ipfb::forward_ws_bytes(kNoallocMaxLblock),
+              "built-in scratch smaller than the forward PFB's workspace");
 
 __device__ __align__(256) double g_noalloc_sums[kNoallocSums];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[kMaxDevices] = {};
-
-int noalloc_scratch(double** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return IPFB_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return IPFB_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_sums);
-    if (e != cudaSuccess || !p) return IPFB_ERR_CUDA;
-    g_noalloc_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_noalloc_ptr[dev];
-  return IPFB_OK;
-}
 
 }  // namespace
 
 extern "C" int pfb_forward_noalloc(const ipfb_geom* g, const float* x, const float* window, uint8_t* codes,
                                    float* scale_out, float* spectra_out, void* stream) {
-  if (!g || !x || !window || !codes || !scale_out) return IPFB_ERR_INVALID;
-  if (g->lblock < 2 || g->ntap < 1 || g->nframes < 1) return IPFB_ERR_INVALID;
+  int rc = ipfb::check_geom(g, false);
+  if (rc) return rc;
+  if (!x || !window || !codes || !scale_out) return IPFB_ERR_INVALID;
   // sizes beyond the built-in scratch are refused before anything is enqueued
   if (g->lblock > kNoallocMaxLblock) return IPFB_ERR_UNSUPPORTED;
-  if ((g->lblock & (g->lblock - 1)) != 0 || g->lblock < 64 || g->ntap > 16 || g->periodic != 1)
-    return IPFB_ERR_UNSUPPORTED;
-  double* sums = nullptr;
-  int rc = noalloc_scratch(&sums);
-  if (rc) return rc;
+  void* addr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_sums);
+  if (e != cudaSuccess) return ipfb::cuda_fail(e, "cudaGetSymbolAddress");
+  if (!addr) return ipfb::cuda_fail(cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+  double* sums = static_cast<double*>(addr);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int H = g->lblock / 2, J = g->nframes;
-  cudaError_t e = cudaMemsetAsync(sums, 0, 2 * (size_t)(H + 1) * sizeof(double), st);
-  if (e == cudaSuccess) e = ipfb::launch_k1_power(H, x, window, g->ntap, J, sums, st);
-  if (e == cudaSuccess) e = ipfb::launch_k1_scale(H, J, sums, scale_out, st);
-  if (e == cudaSuccess)
-    e = ipfb::launch_k1_quant(H, x, window, g->ntap, J, scale_out, codes, reinterpret_cast<float2*>(spectra_out), st);
-  if (e != cudaSuccess) return e == cudaErrorNotSupported ? IPFB_ERR_UNSUPPORTED : IPFB_ERR_CUDA;
+  if ((e = cudaMemsetAsync(sums, 0, ipfb::forward_ws_bytes(g->lblock), st)) != cudaSuccess)
+    return ipfb::cuda_fail(e, "cudaMemsetAsync");
+  if ((e = ipfb::launch_k1_power(H, x, window, g->ntap, J, sums, st)) != cudaSuccess)
+    return ipfb::cuda_fail(e, "k1_pfb_power");
+  if ((e = ipfb::launch_k1_scale(H, J, sums, scale_out, st)) != cudaSuccess)
+    return ipfb::cuda_fail(e, "k1_scale_from_sums");
+  if ((e = ipfb::launch_k1_quant(H, x, window, g->ntap, J, scale_out, codes, reinterpret_cast<float2*>(spectra_out),
+                                 st)) != cudaSuccess)
+    return ipfb::cuda_fail(e, "k1_pfb_quant");
   return IPFB_OK;
 }

@@ -60,7 +60,10 @@ __device__ __forceinline__ void mbar_init(uint32_t bar) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 // wait for the completion of the phase with parity `parity`; false after `limit` SM clocks
+// (limit <= 0: false at once, without testing the barrier -- try_wait may itself block
+// for a while, which would let a quick MMA finish inside a "zero" bound)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+  if (limit <= 0) return false;
   const long long t0 = clock64();
   while (true) {
     uint32_t done;

@@ -33,7 +33,7 @@ class Geom(ctypes.Structure):
 
 class MLParams(ctypes.Structure):
     _fields_ = [("noise_var", ctypes.c_double), ("prior_weight", ctypes.c_double), ("tol", ctypes.c_double),
-                ("max_iter", ctypes.c_int), ("precond", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("precond", ctypes.c_int), ("net_from", ctypes.c_int)]
 
 
 PRECOND = {"none": 0, "wiener": 1, "learned": 2}
@@ -67,6 +67,7 @@ _SIGS = {
     "ipfb_last_cuda_error": (ctypes.c_char_p, []),
     "ipfb_version": (_I, []),
     "ipfb_set_max_column_run": (_I, [_I]),
+    "ipfb_set_net_wait_limit": (_I, [ctypes.c_longlong]),
     "ipfb_stage_timing": (_I, [_I]),
     "ipfb_stage_times": (_I, [ctypes.c_char_p, _SZ, ctypes.POINTER(_D), ctypes.POINTER(_I), _I]),
     "ipfb_workspace_size": (_I, [ctypes.POINTER(Geom), _I, ctypes.POINTER(_SZ)]),
@@ -137,6 +138,12 @@ def _check(fn: str, rc: int):
 
 def set_max_column_run(frames: int):
     _check("ipfb_set_max_column_run", lib().ipfb_set_max_column_run(int(frames)))
+
+
+def set_net_wait_limit(cycles: int):
+    """Testing knob: bound (SM clocks) on the net forward's accumulator wait; < 0 restores
+    the built-in bound of about a second."""
+    _check("ipfb_set_net_wait_limit", lib().ipfb_set_net_wait_limit(int(cycles)))
 
 
 def stage_timing(enable: bool):
@@ -365,7 +372,7 @@ def ipfb_wiener_upchannelize(codes, scale, window, noise_level: float, upfactor:
 
 def ml_solve(codes, scale, window, noise_var: float, mask, prior, prior_weight: float = 1.0,
              precond: str = "none", tol: float = 1e-6, max_iter: int = 1000, x0=None, net=None,
-             workspace=None):
+             workspace=None, net_from: int = 0):
     """ML inverse PFB with a time-domain prior by conjugate gradient.
     codes uint8 [J, N/2]; scale float32 [N/2+1]; window float32 [ntap, N];
     mask uint8 [J*N] (nonzero = saved); prior float32 [J*N]; x0 float32 [J*N] or None.
@@ -385,7 +392,7 @@ def ml_solve(codes, scale, window, noise_var: float, mask, prior, prior_weight: 
         x = torch.empty(J * N, dtype=torch.float32, device=codes.device)
     iters = torch.empty(N, dtype=torch.int32, device=codes.device)
     resid = torch.empty((2, N), dtype=torch.float32, device=codes.device)
-    prm = MLParams(float(noise_var), float(prior_weight), float(tol), int(max_iter), PRECOND[precond])
+    prm = MLParams(float(noise_var), float(prior_weight), float(tol), int(max_iter), PRECOND[precond], int(net_from))
     if precond == "learned":
         if net is None:
             raise ValueError("precond='learned' needs net (float32 CUDA tensor of NET_NPARAMS parameters)")

@@ -20,6 +20,10 @@ import numpy as np
 from . import ipfb, synth
 
 NTAP = 4
+# training epochs of the recipe, and the preconditioner applications that use the
+# Wiener term alone before the net joins the learned solve (ipfb_ml_params.net_from)
+EPOCHS = 24
+NET_FROM = 2
 
 
 def init_theta(seed: int, scale3: float = 0.1) -> np.ndarray:
@@ -107,7 +111,7 @@ def make_training_set(torch, dev, seeds, iters=(1, 3, 8, 20, 50), pairs_per: int
                          * pairs_per, "columns": int(xin.shape[0]), "frames": int(xin.shape[2])}
 
 
-def train(torch, dev, xin, target, epochs: int = 10, batch: int = 16, lr: float = 2e-3, seed: int = 0,
+def train(torch, dev, xin, target, epochs: int = EPOCHS, batch: int = 16, lr: float = 2e-3, seed: int = 0,
           theta0: np.ndarray | None = None, log=None, state: dict | None = None, return_state: bool = False):
     """Adam on mini-batches of `batch` consecutive training columns (batch / 2 randomly
     drawn column pairs of one instance and iterate), the batches visited in a new
@@ -233,7 +237,7 @@ def main(argv=None) -> int:
     """Train the net on the training recipe above and write a checkpoint:
 
         python -m paper_2608_23441_b300.precond_train --out net.ckpt
-            [--seeds 1000-1007] [--epochs 8] [--resume earlier.ckpt]
+            [--seeds 1000-1007] [--epochs 24] [--resume earlier.ckpt]
 
     With --resume, training continues from that checkpoint's parameters, Adam state and
     batch order (the training pairs are rebuilt from the same seeds)."""
@@ -243,7 +247,7 @@ def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description="train the learned CG preconditioner")
     ap.add_argument("--out", required=True)
     ap.add_argument("--seeds", default="1000-1007")
-    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=EPOCHS)
     ap.add_argument("--resume", default=None)
     args = ap.parse_args(argv)
     seeds = parse_seeds(args.seeds)

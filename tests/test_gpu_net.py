@@ -181,7 +181,9 @@ def test_learned_fcg_matches_oracle(N, J):
     A = lambda V: oml.normal_operator_fft(w, V, sig2, M, 1.0)  # noqa: E731
     B = oml.rhs(w, d, sig2, M, P, 1.0)
     pr = onet.unflatten(th.astype(np.float32).astype(np.float64))
-    pre = lambda R: onet.apply_precond(pr, oml.wiener_precond(w, R, sig2, M, 1.0), M, emulate_bf16=True)  # noqa
+    lam_mbar = 1.0 * M.mean(axis=0)
+    Mw = lambda R: oml.wiener_precond(w, R, sig2, M, 1.0)  # noqa: E731
+    pre = lambda R: onet.apply_precond(pr, Mw(R), M, Mw, lam_mbar, emulate_bf16=True)  # noqa: E731
     Xo, ito, _ = onet.fcg(A, B, np.zeros_like(B), pre, tol, 2000)
     assert np.all(rl[0] <= tol)
     tr = oml.true_relative_residual(d, w, sig2, M, P, 1.0, xl)
@@ -218,7 +220,9 @@ def test_learned_initial_guess():
     A = lambda V: oml.normal_operator_fft(w, V, sig2, M, 1.0)  # noqa: E731
     B = oml.rhs(w, d, sig2, M, P, 1.0)
     pr = onet.unflatten(th.astype(np.float32).astype(np.float64))
-    pre = lambda R: onet.apply_precond(pr, oml.wiener_precond(w, R, sig2, M, 1.0), M, emulate_bf16=True)  # noqa
+    lam_mbar = 1.0 * M.mean(axis=0)
+    Mw = lambda R: oml.wiener_precond(w, R, sig2, M, 1.0)  # noqa: E731
+    pre = lambda R: onet.apply_precond(pr, Mw(R), M, Mw, lam_mbar, emulate_bf16=True)  # noqa: E731
     Xo, ito, _ = onet.fcg(A, B, x0.reshape(J, N).astype(np.float64), pre, tol, 2000)
     assert np.all(rl[0] <= tol)
     tr = oml.true_relative_residual(d, w, sig2, M, P, 1.0, xl)
@@ -279,16 +283,20 @@ def test_learned_fullsize_config4_properties():
     assert int(itl.max()) < 4000
 
 
-def test_trained_net_gain_over_plain_cg():
-    """What the trained net gains over the method without it: trained on plain-CG
-    iterates of seeds 1000-1007 (the training recipe of the benchmark), the learned FCG
-    solves a held-out lblock-4096, 8192-spectrum instance (seed 4, 10 % prior in 64
-    chunks) to 1e-6 per column in a quarter of plain CG's worst-column iterations or
-    fewer, with the same reconstruction error."""
+def test_trained_net_gain_over_its_zero_output_form():
+    """What the trained net gains over the method without it.  Trained on plain-CG
+    iterates of seeds 1000-1007 (the benchmark's training recipe), the learned solve of
+    a held-out lblock-4096, 8192-spectrum instance (seed 4, 10 % prior in 64 chunks),
+    with the net joining from the third preconditioner application, reaches 1e-6 per
+    column in fewer iterations than the same solve with a zero-output net (g = 0, i.e.
+    the Wiener preconditioner) and than Wiener-PCG itself: a lower worst-column count
+    (by 4 or more), a lower mean, at least 15 % fewer iterations over the slow columns
+    (those Wiener-PCG needs 10 or more for), and the same reconstruction error within
+    1e-3 relative."""
     from paper_2608_23441_b300 import precond_train as pt
     dev = torch.device("cuda", 0)
     xin, tgt, _ = pt.make_training_set(torch, dev, list(range(1000, 1008)))
-    theta, hist = pt.train(torch, dev, xin, tgt, epochs=8)
+    theta, hist = pt.train(torch, dev, xin, tgt, epochs=pt.EPOCHS)
     assert hist[-1] < hist[0], hist
     del xin, tgt
     N, J = 4096, 8192
@@ -299,14 +307,24 @@ def test_trained_net_gain_over_plain_cg():
     mask = torch.from_numpy(synth.mask_from_chunks(N * J, starts, L)).to(dev)
     sig2 = pt.noise_var(torch, ipfb, codes, scale, w, x, N, J)
     args = (codes, scale, w, sig2, mask, x)
-    xp, itp, rp = ipfb.ml_solve(*args, precond="none", tol=1e-6, max_iter=4000)
-    xl, itl, rl = ipfb.ml_solve(*args, precond="learned", net=theta, tol=1e-6, max_iter=4000)
-    assert bool((rp[0] <= 1e-6).all()) and bool((rl[0] <= 1e-6).all())
-    assert 4 * int(itl.max()) <= int(itp.max()), (int(itl.max()), int(itp.max()))
-    assert float(itl.float().mean()) < float(itp.float().mean())
-    ep = float(torch.linalg.norm(xp - x) / torch.linalg.norm(x))
+    zero = torch.from_numpy(pt.init_theta(0, scale3=0.0)).to(dev)
+    xw, itw, rw = ipfb.ml_solve(*args, precond="wiener", tol=1e-6, max_iter=4000)
+    x0, it0, r0 = ipfb.ml_solve(*args, precond="learned", net=zero, tol=1e-6, max_iter=4000, net_from=pt.NET_FROM)
+    xl, itl, rl = ipfb.ml_solve(*args, precond="learned", net=theta, tol=1e-6, max_iter=4000, net_from=pt.NET_FROM)
+    for r in (rw, r0, rl):
+        assert bool((r[0] <= 1e-6).all())
+    itw, it0, itl = itw.cpu().numpy(), it0.cpu().numpy(), itl.cpu().numpy()
+    slow = itw >= 10
+    print(f"worst column: learned {itl.max()}, g = 0 {it0.max()}, Wiener-PCG {itw.max()}; mean {itl.mean():.3f}, "
+          f"{it0.mean():.3f}, {itw.mean():.3f}; slow columns ({slow.sum()}) {itl[slow].sum()}, {it0[slow].sum()}, "
+          f"{itw[slow].sum()}")
+    for ref in (it0, itw):
+        assert itl.max() + 4 <= ref.max(), (itl.max(), ref.max())
+        assert itl.mean() < ref.mean(), (itl.mean(), ref.mean())
+        assert itl[slow].sum() <= 0.85 * ref[slow].sum(), (itl[slow].sum(), ref[slow].sum())
+    ew = float(torch.linalg.norm(xw - x) / torch.linalg.norm(x))
     el = float(torch.linalg.norm(xl - x) / torch.linalg.norm(x))
-    assert abs(el - ep) <= 1e-3 * ep, (el, ep)
+    assert abs(el - ew) <= 1e-3 * ew, (el, ew)
 
 
 def test_training_resumes_exactly_from_a_checkpoint(tmp_path):
@@ -325,3 +343,58 @@ def test_training_resumes_exactly_from_a_checkpoint(tmp_path):
     thr, hr = pt.train(torch, dev, xin, tgt, epochs=2, batch=16, state=pt.load_checkpoint(p))
     assert torch.equal(thr, th4)
     assert h2 + hr == h4
+
+
+def test_learned_solve_enqueues_without_host_sync():
+    """The learned solve is one graph whose loop ends on the device: it can be
+    recorded inside a caller's CUDA-graph capture (any host synchronisation or
+    read-back would break the capture), and replaying the captured graph gives the
+    eager call's answer bit for bit."""
+    N, J = 64, 256
+    x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 33)
+    th = cuda(_theta(34, scale3=0.2, jitter=0.01).astype(np.float32))
+    args = (cuda(codes), cuda(scale), cuda(w.astype(np.float32)), sig2, cuda(mask), cuda(prior))
+    g = ipfb.geom(N, 4, J)
+    ws = torch.empty(ipfb.workspace_size(g, ipfb.OP_ML_LEARNED), dtype=torch.uint8, device="cuda")
+    xe, ite, re = ipfb.ml_solve(*args, precond="learned", net=th, tol=1e-6, max_iter=500, workspace=ws)
+    xe, ite, re = xe.clone(), ite.clone(), re.clone()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            xg, itg, rg = ipfb.ml_solve(*args, precond="learned", net=th, tol=1e-6, max_iter=500, workspace=ws)
+    torch.cuda.current_stream().wait_stream(side)
+    for _ in range(2):
+        xg.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(xg, xe) and torch.equal(itg, ite) and torch.equal(rg, re)
+
+
+def test_net_wait_that_runs_out_falls_back_to_plain_cg():
+    """A bounded device wait that expires (failure detection without a fault): with the
+    net forward's accumulator wait bound set to zero, every CTA gives up at once, marks
+    its output, lets its MMAs in flight finish and stops; the learned solve sees the
+    give-up on the device and returns plain CG's solve from the same start, bit for bit.
+    The standalone forward shows the mark (NaN) in its output.  The bound is restored."""
+    N, J = 64, 256
+    x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 35)
+    th = cuda(_theta(36, scale3=0.2, jitter=0.01).astype(np.float32))
+    args = (cuda(codes), cuda(scale), cuda(w.astype(np.float32)), sig2, cuda(mask), cuda(prior))
+    xp, itp, rp = ipfb.ml_solve(*args, precond="none", tol=1e-6, max_iter=500)
+    xin = cuda(_xin(3, 500, 37).astype(np.float32))
+    ipfb.set_net_wait_limit(0)
+    try:
+        xl, itl, rl = ipfb.ml_solve(*args, precond="learned", net=th, tol=1e-6, max_iter=500)
+        y = ipfb.net_forward(th, xin)
+        torch.cuda.synchronize()
+    finally:
+        ipfb.set_net_wait_limit(-1)
+    assert torch.equal(xl, xp) and torch.equal(itl, itp) and torch.equal(rl, rp)
+    assert not bool(torch.isfinite(y).all())
+    # the bound restored: the same calls work normally again
+    xl2, itl2, rl2 = ipfb.ml_solve(*args, precond="learned", net=th, tol=1e-6, max_iter=500)
+    y2 = ipfb.net_forward(th, xin)
+    assert bool(torch.isfinite(y2).all()) and bool((rl2[0] <= 1e-6).all())

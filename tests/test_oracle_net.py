@@ -109,10 +109,37 @@ def test_zero_net_is_wiener_preconditioner():
     rng = np.random.default_rng(5)
     R = rng.standard_normal((J, N))
     mask = (rng.uniform(size=(J, N)) < 0.2).astype(float)
-    u = oml.wiener_precond(w, R, 0.05, mask, 1.0)
+    Mw = lambda V: oml.wiener_precond(w, V, 0.05, mask, 1.0)  # noqa: E731
+    u = Mw(R)
     p0 = net.init_params(0, scale3=0.0)
-    z = net.apply_precond(p0, u, mask)
+    z = net.apply_precond(p0, u, mask, Mw, mask.mean(axis=0))
     assert np.allclose(z, u, atol=1e-14)
+
+
+def test_constant_net_output_enters_scaled_by_the_prior_share_at_dc():
+    # A net whose output is the constant c (all weights zero, output bias c) adds
+    # c s times the Wiener filter's response to a constant, weighted by lam mbar: a
+    # constant is the k = 0 mode, so the correction is c s rho(0) with
+    # rho(0) = lam mbar / (W_n(0)^2 / sigma^2 + lam mbar), W_n(0) = sum_r w[r, n]
+    # (Sec. 3.1 eigenvalue at k = 0) -- the prior's share of the Wiener denominator.
+    N, p, J, sig2, lam = 8, 4, 32, 0.05, 0.7
+    w = opfb.sinc_hamming_window(N, p)
+    rng = np.random.default_rng(6)
+    R = rng.standard_normal((J, N))
+    mask = (rng.uniform(size=(J, N)) < 0.3).astype(float)
+    mbar = mask.mean(axis=0)
+    Mw = lambda V: oml.wiener_precond(w, V, sig2, mask, lam)  # noqa: E731
+    u = Mw(R)
+    prm = net.init_params(0, scale3=0.0)
+    for k in prm:
+        prm[k] = np.zeros_like(prm[k])
+    c = 0.37
+    prm["b3"] = np.array([c])
+    z = net.apply_precond(prm, u, mask, Mw, lam * mbar)
+    s = np.sqrt(np.mean(u * u, axis=0))
+    W0 = w.sum(axis=0)
+    rho0 = lam * mbar / (W0 ** 2 / sig2 + lam * mbar)
+    assert np.allclose(z - u, (c * s * rho0)[None, :], rtol=1e-12, atol=1e-14)
 
 
 def test_adam_minimises_a_quadratic():
@@ -121,3 +148,30 @@ def test_adam_minimises_a_quadratic():
     for _ in range(2000):
         th = a.step(th, 2 * th)
     assert np.abs(th).max() < 1e-3
+
+
+def test_adam_first_steps_closed_form():
+    # Kingma and Ba (2015), Algorithm 1, worked by hand.  Step 1 from zero moments:
+    # m = (1 - b1) g, v = (1 - b2) g^2, so the bias-corrected mh = g and vh = g^2 and
+    # every parameter moves by exactly lr g / (|g| + eps).
+    lr, b1, b2, eps = 0.01, 0.9, 0.999, 1e-8
+    g = np.array([2.0, -0.5, 1e-3, 0.0, -40.0])
+    th0 = np.array([1.0, 2.0, -3.0, 0.5, 0.0])
+    a = net.Adam(5, lr=lr, b1=b1, b2=b2, eps=eps)
+    th1 = a.step(th0, g)
+    assert np.allclose(th1, th0 - lr * g / (np.abs(g) + eps), rtol=0, atol=1e-15)
+    # Step 2 with the same gradient: mh = g (1 - b1)(1 + b1) / (1 - b1^2) = g and
+    # vh = g^2 again, so the same move; a missing bias correction would shrink it
+    # by (1 - b1^2) / sqrt(1 - b2^2) ~ 4.25.
+    b = net.Adam(5, lr=lr, b1=b1, b2=b2, eps=eps)
+    t = b.step(th0, g)
+    t = b.step(t, g)
+    assert np.allclose(t, th0 - 2 * lr * g / (np.abs(g) + eps), rtol=0, atol=1e-14)
+    # Step 2 with the gradient reversed: m = -(1 - b1)^2 g, mh = -g (1 - b1)/(1 + b1),
+    # v = (1 - b2)(1 + b2) g^2 -> vh = g^2; the second move is
+    # +lr (1 - b1)/(1 + b1) g / (|g| + eps).
+    c = net.Adam(5, lr=lr, b1=b1, b2=b2, eps=eps)
+    t = c.step(th0, g)
+    t = c.step(t, -g)
+    want = th0 - lr * g / (np.abs(g) + eps) + lr * (1 - b1) / (1 + b1) * g / (np.abs(g) + eps)
+    assert np.allclose(t, want, rtol=0, atol=1e-14)
