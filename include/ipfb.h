@@ -55,6 +55,7 @@ extern "C" {
 #define IPFB_OP_ML_LEARNED 5 /* ipfb_ml_solve with precond = 2        */
 #define IPFB_OP_ML_PAIRS 6   /* ipfb_ml_training_pairs                 */
 #define IPFB_OP_WIENER_STREAM 7 /* ipfb_wiener_stream (nframes = chunk) */
+#define IPFB_OP_ML_STREAM 8     /* ipfb_ml_solve_stream (nframes = chunk) */
 
 typedef struct {
   int lblock;   /* N: power of two, 32 <= N <= 16384                              */
@@ -302,6 +303,29 @@ int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, 
                   const ipfb_ml_params* prm, const uint8_t* prior_mask, const float* prior_values,
                   const void* net, float* x_inout, int use_x0, int* iters, float* resid, void* ws,
                   size_t ws_bytes, void* stream);
+
+/*
+ * ipfb_ml_solve_stream: the ML reconstruction of ipfb_ml_solve (precond 0 or 1) for a
+ * run of nspec spectra longer than one solve, overlap-save like ipfb_wiener_stream
+ * (Sec. 4.2 solved block by block; the solution's dependence on data far away decays
+ * along the frame axis, so a chunk solved as if periodic agrees with the solve of the
+ * whole run away from the chunk's edges).  g->nframes is the chunk length J
+ * (128 <= J <= 8192, a power of two); chunks of J spectra step by J - 2 margin, the
+ * last one aligned to the end of the run; each is solved with its own stretch of
+ * prior_mask, prior_values and (when x0 != NULL) initial guess x0, and its frames
+ * margin .. J - margin are kept.  codes: uint8 [nspec][N/2] (16-byte aligned; N/2 a
+ * multiple of 16); scale: float [N/2 + 1] of the whole run; window: float [p][N];
+ * prior_mask: uint8 [nspec*N]; prior_values, x0: float [nspec*N], time order;
+ * x_out: float [(nspec - 2 margin) N], frames margin .. nspec - margin - 1; iters:
+ * int [N] and resid: float [2][N], the largest over the chunks of ipfb_ml_solve's
+ * per-column counts and residuals.  0 <= margin, J - 2 margin >= 1, nspec >= J;
+ * precond 2 returns IPFB_ERR_UNSUPPORTED.  Workspace:
+ * ipfb_workspace_size(g, IPFB_OP_ML_STREAM).
+ */
+int ipfb_ml_solve_stream(const ipfb_geom* g, int64_t nspec, const uint8_t* codes, const float* scale,
+                         const float* window, const ipfb_ml_params* prm, const uint8_t* prior_mask,
+                         const float* prior_values, const float* x0, int margin, float* x_out, int* iters,
+                         float* resid, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * Learned preconditioner net.  The paper has no learned component: this is the

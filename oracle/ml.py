@@ -203,3 +203,33 @@ def dense_ml_column(d_col, window_col, noise_var, mask_col, prior_col, prior_wei
     A = Cm.T @ Cm / noise_var + prior_weight * np.diag(mask_col.astype(np.float64))
     b = Cm.T @ d_col / noise_var + prior_weight * mask_col * prior_col
     return np.linalg.solve(A, b)
+
+
+def ml_solve_stream(codes: np.ndarray, scale: np.ndarray, window: np.ndarray, noise_var: float,
+                    mask_flat: np.ndarray, prior_flat: np.ndarray, chunk: int, margin: int,
+                    prior_weight: float = 1.0, precond: str = "none", tol: float = 1e-6,
+                    max_iter: int = 1000, x0_flat: np.ndarray | None = None):
+    """Overlap-save ML reconstruction of a run of spectra longer than one solve (the
+    Sec. 4.2 system solved chunk by chunk, as the Wiener inverse is in
+    ipfb.ipfb_wiener_stream): every chunk of `chunk` spectra, with its mask, prior
+    values and initial guess, is solved by ml_solve as a periodic system, and its frames
+    margin .. chunk - margin are kept (chunk starts from ipfb.stream_chunks).  The
+    solution's dependence on data far away decays along the frame axis, so away from a
+    chunk's edges it agrees with the solve of the whole run.
+    Returns (frames [margin, nspec - margin) in time order [(nspec - 2 margin) * N],
+    per-column maxima over the chunks of the iteration counts and of the residuals)."""
+    from .ipfb import stream_chunks
+    p, N = window.shape
+    nspec = codes.shape[0]
+    out = np.zeros((nspec - 2 * margin, N))
+    it_max = np.zeros(N, dtype=np.int64)
+    rel_max = np.zeros(N)
+    for st in stream_chunks(nspec, chunk, margin):
+        sl = slice(st * N, (st + chunk) * N)
+        x0 = None if x0_flat is None else np.asarray(x0_flat)[sl]
+        xc, it, rel = ml_solve(codes[st:st + chunk], scale, window, noise_var, np.asarray(mask_flat)[sl],
+                               np.asarray(prior_flat)[sl], prior_weight, precond, tol, max_iter, x0)
+        out[st:st + chunk - 2 * margin] = xc.reshape(chunk, N)[margin:chunk - margin]
+        it_max = np.maximum(it_max, it)
+        rel_max = np.maximum(rel_max, rel)
+    return out.reshape(-1), it_max, rel_max

@@ -16,9 +16,12 @@ sqrt(Var[x - x_hat]) / sigma_x.  One JSON object is printed, with the paper's
 quoted figures beside the measured ones.
 
 Every transform, inverse and solve runs in libipfb; torch only holds the arrays and
-forms the averages.  The ML kernels hold a column of up to 8192 frames, so the
-stream is 2048 x 8192 = 2^24 samples (the paper's is 2^27) and delta(f) is averaged
-over its 128 re-channelized blocks.
+forms the averages.  The default run is the paper's: 2048 x 65536 = 2^27 samples,
+delta(f) averaged over its 1024 re-channelized blocks.  A single ML solve holds up to
+8192 frames, so beyond that the ML reconstruction is the overlap-save solve
+(ipfb_ml_solve_stream: chunks of 8192 frames stepping by 8192 - 2 x 512, each solved
+with its own stretch of the mask, the prior and the Wiener start); the run's first
+and last 512 frames, which no chunk covers from both sides, keep the Wiener start.
 """
 from __future__ import annotations
 
@@ -47,7 +50,10 @@ def _delta_stats(delta: np.ndarray, upfactor: int) -> dict:
             "median": float(np.median(interior))}
 
 
-def run(torch, dev, nframes: int = 8192, seed: int = 11, betas=(0.01, 0.03, 0.10), iters: int = 25,
+ML_CHUNK, ML_MARGIN = 8192, 512
+
+
+def run(torch, dev, nframes: int = 65536, seed: int = 11, betas=(0.01, 0.03, 0.10), iters: int = 25,
         prior_weights=("1", "1/sigma2")) -> dict:
     N, J = LBLOCK, nframes
     T = N * J
@@ -67,15 +73,23 @@ def run(torch, dev, nframes: int = 8192, seed: int = 11, betas=(0.01, 0.03, 0.10
     wd = w.double()
     ce = sum(wd[r][None, :] * torch.roll(e, -r, dims=0) for r in range(NTAP))
     sig2 = float(ce.var())
-    g = ipfb.geom(N, NTAP, J)
-    ws = torch.empty(ipfb.workspace_size(g, ipfb.OP_ML), dtype=torch.uint8, device=dev)
+    chunked = J > ML_CHUNK
+    g = ipfb.geom(N, NTAP, ML_CHUNK if chunked else J)
+    ws = torch.empty(ipfb.workspace_size(g, ipfb.OP_ML_STREAM if chunked else ipfb.OP_ML), dtype=torch.uint8,
+                     device=dev)
     for beta in betas:
         L = synth.saved_paths(N, beta)
         mask = torch.from_numpy(synth.path_sample_mask(N, J, L)).to(dev)
         for pw in prior_weights:
             lam = 1.0 if pw == "1" else 1.0 / sig2
-            xm, _, _ = ipfb.ml_solve(codes, scale, w, sig2, mask, x, prior_weight=lam, tol=0.0, max_iter=iters,
-                                     x0=recon["wiener"], workspace=ws)
+            if chunked:
+                xm = recon["wiener"].clone()
+                ipfb.ml_solve_stream(codes, scale, w, sig2, mask, x, ML_CHUNK, ML_MARGIN, prior_weight=lam, tol=0.0,
+                                     max_iter=iters, x0=recon["wiener"], out=xm[ML_MARGIN * N:(J - ML_MARGIN) * N],
+                                     workspace=ws)
+            else:
+                xm, _, _ = ipfb.ml_solve(codes, scale, w, sig2, mask, x, prior_weight=lam, tol=0.0, max_iter=iters,
+                                         x0=recon["wiener"], workspace=ws)
             recon[f"ml_beta_{beta:.2f}_prior_{pw}"] = xm
     del ws
 
@@ -89,7 +103,8 @@ def run(torch, dev, nframes: int = 8192, seed: int = 11, betas=(0.01, 0.03, 0.10
                        f"({T // Lup} blocks averaged), seed {seed}",
            "phi2": phi2, "sigma2_d": sig2,
            "ml": f"every 4th frame of L central paths, Wiener start, {iters} CG steps; data term weight 1/sigma2_d, "
-                 "prior weight 1 or 1/sigma2_d (the latter = unit weights on both terms)",
+                 "prior weight 1 or 1/sigma2_d (the latter = unit weights on both terms)"
+                 + (f"; overlap-save solves of {ML_CHUNK} frames, {ML_MARGIN}-frame margins" if chunked else ""),
            "paper": {"delta_channel_centre": "~1.1 % (-19 dB)", "wiener_max": "~10 %", "no_filter_max": "> 100 %",
                      "ml_beta_0.03_max": "< half of the Wiener maximum", "ml_beta_0.10_max": "~2 %",
                      "timestream_error": "~10 % for most frame samples"},
@@ -108,7 +123,7 @@ def run(torch, dev, nframes: int = 8192, seed: int = 11, betas=(0.01, 0.03, 0.10
 def main(argv=None) -> int:
     import torch
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--nframes", type=int, default=8192)
+    ap.add_argument("--nframes", type=int, default=65536)
     ap.add_argument("--seed", type=int, default=11)
     args = ap.parse_args(argv)
     dev = torch.device("cuda", 0)

@@ -283,6 +283,15 @@ int ipfb_workspace_size(const ipfb_geom* g, int op, size_t* bytes) {
       if (g->nframes < 128 || g->nframes > 8192) return IPFB_ERR_UNSUPPORTED;
       *bytes = 2 * (size_t)g->nframes * (size_t)g->lblock * sizeof(float);
       return IPFB_OK;
+    case IPFB_OP_ML_STREAM:
+      rc = check_geom(g, true);
+      if (rc) return rc;
+      if (g->nframes < 128 || g->nframes > 8192) return IPFB_ERR_UNSUPPORTED;
+      // one chunk's solve, the chunk's time-order solution, its iterations and residuals
+      *bytes = al256(2 * (size_t)g->nframes * (size_t)g->lblock * sizeof(float)) +
+               al256((size_t)g->nframes * (size_t)g->lblock * sizeof(float)) +
+               al256((size_t)g->lblock * sizeof(int)) + al256(2 * (size_t)g->lblock * sizeof(float));
+      return IPFB_OK;
     case IPFB_OP_ML_LEARNED:
     case IPFB_OP_ML_PAIRS:
       rc = check_geom(g, true);
@@ -723,6 +732,35 @@ int ml_solve_learned(const ipfb_geom* g, const uint8_t* codes, const float* scal
   t.done();
   return IPFB_OK;
 }
+// Plain / Wiener-preconditioned ML solve (precond 0 or 1) of one J-frame block:
+// unpack + per-frame inverse FFT, [initial guess to pairs], k5_ml_cg, back to time order.
+int ml_solve_core(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
+                  const ipfb_ml_params* prm, const uint8_t* prior_mask, const float* prior_values, float* x_inout,
+                  int use_x0, int* iters, float* resid, void* ws, cudaStream_t st) {
+  const int N = g->lblock, J = g->nframes;
+  float2* d2 = reinterpret_cast<float2*>(ws);
+  float2* x2 = d2 + (size_t)J * (N / 2);
+  {
+    Stage t("k2_unpack_irfft", st);
+    CK(launch_k2(N / 2, codes, scale, d2, 1, J, st), "k2_unpack_irfft");
+    t.done();
+  }
+  if (use_x0) {
+    Stage t("k_time_to_pairs", st);
+    CK(launch_time_to_pairs(x_inout, x2, N, J, st), "k_time_to_pairs");
+    t.done();
+  }
+  const MLParams mp = ml_params(g, prm, use_x0);
+  {
+    Stage t("k5_ml_cg", st);
+    CK(launch_k5(J, d2, x2, prior_mask, prior_values, window, N, mp, iters, resid, st), "k5_ml_cg");
+    t.done();
+  }
+  Stage t("k_pairs_to_time", st);
+  CK(launch_pairs_to_time(x2, x_inout, N, 1, J, st), "k_pairs_to_time");
+  t.done();
+  return IPFB_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -748,30 +786,62 @@ int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, 
   size_t need = 0;
   if ((rc = ipfb_workspace_size(g, IPFB_OP_ML, &need))) return rc;
   if (!ws || ws_bytes < need) return IPFB_ERR_WORKSPACE;
+  if (g->nframes / 16 < g->ntap - 1 && g->ntap > 4) return IPFB_ERR_UNSUPPORTED;
+  return ml_solve_core(g, codes, scale, window, prm, prior_mask, prior_values, x_inout, use_x0, iters, resid, ws,
+                       as_stream(stream));
+}
+
+int ipfb_ml_solve_stream(const ipfb_geom* g, int64_t nspec, const uint8_t* codes, const float* scale,
+                         const float* window, const ipfb_ml_params* prm, const uint8_t* prior_mask,
+                         const float* prior_values, const float* x0, int margin, float* x_out, int* iters,
+                         float* resid, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_geom(g, true);
+  if (rc) return rc;
+  if (!codes || !scale || !window || !prm || !prior_mask || !prior_values || !x_out || !iters || !resid ||
+      misaligned16(codes))
+    return IPFB_ERR_INVALID;
+  if (!(prm->noise_var > 0.0) || !std::isfinite(prm->noise_var) || !(prm->prior_weight >= 0.0) ||
+      !std::isfinite(prm->prior_weight) || !(prm->tol >= 0.0) || prm->max_iter < 0 || prm->net_from < 0)
+    return IPFB_ERR_INVALID;
+  if (prm->precond < 0 || prm->precond > 2) return IPFB_ERR_INVALID;
+  if (prm->precond == 2) return IPFB_ERR_UNSUPPORTED;
   const int N = g->lblock, J = g->nframes;
+  if (margin < 0 || J - 2 * margin < 1 || nspec < J) return IPFB_ERR_INVALID;
+  if (((size_t)N / 2) % 16 != 0) return IPFB_ERR_UNSUPPORTED;  // chunk starts must stay 16-byte aligned
   if (J / 16 < g->ntap - 1 && g->ntap > 4) return IPFB_ERR_UNSUPPORTED;
+  size_t need = 0;
+  if ((rc = ipfb_workspace_size(g, IPFB_OP_ML_STREAM, &need))) return rc;
+  if (!ws || ws_bytes < need) return IPFB_ERR_WORKSPACE;
   cudaStream_t st = as_stream(stream);
-  float2* d2 = reinterpret_cast<float2*>(ws);
-  float2* x2 = d2 + (size_t)J * (N / 2);
-  {
-    Stage t("k2_unpack_irfft", st);
-    CK(launch_k2(N / 2, codes, scale, d2, 1, J, st), "k2_unpack_irfft");
-    t.done();
+  size_t ml_bytes = 0;
+  ipfb_workspace_size(g, IPFB_OP_ML, &ml_bytes);
+  const size_t chunk_vals = (size_t)J * (size_t)N;
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  float* xc = reinterpret_cast<float*>(w + al256(ml_bytes));
+  int* itc = reinterpret_cast<int*>(w + al256(ml_bytes) + al256(chunk_vals * sizeof(float)));
+  float* rc2 = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(itc) + al256((size_t)N * sizeof(int)));
+  const long long step = J - 2 * margin;
+  long long start = 0;
+  bool first = true;
+  while (true) {
+    const bool last = start + J >= nspec;
+    if (last) start = nspec - J;
+    const size_t off = (size_t)start * (size_t)N;
+    if (x0)
+      CK(cudaMemcpyAsync(xc, x0 + off, chunk_vals * sizeof(float), cudaMemcpyDeviceToDevice, st), "cudaMemcpyAsync");
+    rc = ml_solve_core(g, codes + (size_t)start * (N / 2), scale, window, prm, prior_mask + off, prior_values + off,
+                       xc, x0 ? 1 : 0, first ? iters : itc, first ? resid : rc2, ws, st);
+    if (rc) return rc;
+    if (!first) CK(launch_max_merge(iters, itc, resid, rc2, N, st), "k_max_merge");
+    // frames margin .. J - margin of this chunk are frames start + margin .. of the run,
+    // stored from x_out[start N] (x_out begins at frame `margin`)
+    CK(cudaMemcpyAsync(x_out + off, xc + (size_t)margin * N, (size_t)step * N * sizeof(float),
+                       cudaMemcpyDeviceToDevice, st),
+       "cudaMemcpyAsync");
+    first = false;
+    if (last) break;
+    start += step;
   }
-  if (use_x0) {
-    Stage t("k_time_to_pairs", st);
-    CK(launch_time_to_pairs(x_inout, x2, N, J, st), "k_time_to_pairs");
-    t.done();
-  }
-  const MLParams mp = ml_params(g, prm, use_x0);
-  {
-    Stage t("k5_ml_cg", st);
-    CK(launch_k5(J, d2, x2, prior_mask, prior_values, window, N, mp, iters, resid, st), "k5_ml_cg");
-    t.done();
-  }
-  Stage t("k_pairs_to_time", st);
-  CK(launch_pairs_to_time(x2, x_inout, N, 1, J, st), "k_pairs_to_time");
-  t.done();
   return IPFB_OK;
 }
 

@@ -44,6 +44,25 @@ cudaError_t launch_k5(int J, const float2* d2, float2* x2, const uint8_t* mask, 
   return k5_j<15, 0, 0>(J, d2, x2, mask, prior, window, N, mp, iters, resid, st);
 }
 
+namespace {
+// per-column maxima over the chunks of an overlap-save solve (a NaN residual is kept)
+__global__ void k_max_merge(int* __restrict__ it, const int* __restrict__ itc, float* __restrict__ res,
+                            const float* __restrict__ resc, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) it[i] = max(it[i], itc[i]);
+  if (i < 2 * N) {
+    const float a = res[i], b = resc[i];
+    res[i] = (b > a || isnan(b)) ? b : a;
+  }
+}
+}  // namespace
+
+cudaError_t launch_max_merge(int* iters, const int* iters_c, float* resid, const float* resid_c, int N,
+                             cudaStream_t st) {
+  k_max_merge<<<(2 * N + 255) / 256, 256, 0, st>>>(iters, iters_c, resid, resid_c, N);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_time_to_pairs(const float* x, float2* x2, int N, int J, cudaStream_t st) {
   dim3 grid((N / 2 + 31) / 32, (J + 31) / 32);
   k_time_to_pairs<<<grid, 256, 0, st>>>(x, x2, N, J);

@@ -60,6 +60,9 @@ struct MLParams {
 cudaError_t launch_k5(int J, const float2* d2, float2* x2, const uint8_t* mask, const float* prior,
                       const float* window, int N, const MLParams& mp, int* iters, float* resid, cudaStream_t st);
 cudaError_t launch_time_to_pairs(const float* x, float2* x2, int N, int J, cudaStream_t st);
+// iters[n] = max(iters[n], iters_c[n]), resid[i] = max(resid[i], resid_c[i]) (NaN kept), i < 2N
+cudaError_t launch_max_merge(int* iters, const int* iters_c, float* resid, const float* resid_c, int N,
+                             cudaStream_t st);
 cudaError_t launch_block_polyphase(const float* x, const float* w, int L, int ntap, long long nb, float* xs,
                                    cudaStream_t st);
 cudaError_t launch_upchan(const UpchanSrc& src, int L, long long nblocks, float2* out, float* x_out,

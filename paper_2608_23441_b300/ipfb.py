@@ -22,6 +22,7 @@ OK = 0
 ERR_INVALID, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA = -1, -2, -3, -4, -5, -6
 OP_FORWARD, OP_WIENER, OP_WIENER_UPCHAN, OP_ML, OP_ML_LEARNED, OP_ML_PAIRS = 1, 2, 3, 4, 5, 6
 OP_WIENER_STREAM = 7
+OP_ML_STREAM = 8
 NET_FORWARD, NET_GRAD = 1, 2
 NET_NPARAMS = 10145
 
@@ -77,6 +78,8 @@ _SIGS = {
     "ipfb_wiener": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _D, _I, _P, _P, _SZ, _P]),
     "ipfb_filter": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _I, _D, _P, _P, _P, _SZ, _P]),
     "ipfb_wiener_stream": (_I, [ctypes.POINTER(Geom), _I64, _P, _P, _P, _D, _I, _I, _P, _P, _SZ, _P]),
+    "ipfb_ml_solve_stream": (_I, [ctypes.POINTER(Geom), _I64, _P, _P, _P, ctypes.POINTER(MLParams), _P, _P, _P, _I,
+                                  _P, _P, _P, _P, _SZ, _P]),
     "upchannelize": (_I, [_P, _I64, _I64, _P, _P, _SZ, _P]),
     "upchannelize_pfb": (_I, [_P, _I64, _I64, _I, _P, _P, _P, _SZ, _P]),
     "ipfb_wiener_upchannelize": (_I, [ctypes.POINTER(Geom), _P, _P, _P, _D, _I, _I, _P, _P, _P, _SZ, _P]),
@@ -327,6 +330,35 @@ def ipfb_wiener_stream(codes, scale, window, noise_level: float, chunk: int, mar
                                                           _ptr(window), float(noise_level), int(bool(normalize)),
                                                           int(margin), _ptr(x), _ptr(ws), wsb, _stream()))
     return x
+
+
+def ml_solve_stream(codes, scale, window, noise_var: float, mask, prior, chunk: int, margin: int,
+                    prior_weight: float = 1.0, precond: str = "none", tol: float = 1e-6, max_iter: int = 1000,
+                    x0=None, out=None, workspace=None):
+    """Overlap-save ML reconstruction of a long run (ipfb_ml_solve_stream): chunks of
+    `chunk` spectra, `margin` frames dropped at each chunk edge.  codes uint8
+    [nspec, N/2]; mask uint8 / prior, x0 float32 [nspec * N].  Returns (x float32
+    [(nspec - 2 margin) * N] frames margin .. nspec - margin - 1, iters int32 [N],
+    resid float32 [2, N], both the largest over the chunks)."""
+    torch = _torch()
+    codes = _dev(codes, torch.uint8, "codes")
+    scale = _dev(scale, torch.float32, "scale")
+    window = _dev(window, torch.float32, "window")
+    mask = _dev(mask, torch.uint8, "mask")
+    prior = _dev(prior, torch.float32, "prior")
+    x0 = None if x0 is None else _dev(x0, torch.float32, "x0")
+    p, N = window.shape
+    nspec = codes.shape[0]
+    g = geom(N, p, int(chunk))
+    x = out if out is not None else torch.empty((nspec - 2 * margin) * N, dtype=torch.float32, device=codes.device)
+    iters = torch.empty(N, dtype=torch.int32, device=codes.device)
+    resid = torch.empty((2, N), dtype=torch.float32, device=codes.device)
+    prm = MLParams(float(noise_var), float(prior_weight), float(tol), int(max_iter), PRECOND[precond], 0)
+    ws, wsb = _workspace(workspace_size(g, OP_ML_STREAM), codes.device, workspace)
+    _check("ipfb_ml_solve_stream", lib().ipfb_ml_solve_stream(
+        ctypes.byref(g), int(nspec), _ptr(codes), _ptr(scale), _ptr(window), ctypes.byref(prm), _ptr(mask),
+        _ptr(prior), _ptr(x0), int(margin), _ptr(x), _ptr(iters), _ptr(resid), _ptr(ws), wsb, _stream()))
+    return x, iters, resid
 
 
 def upchannelize_pfb(x, window, out=None, workspace=None):

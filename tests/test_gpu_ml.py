@@ -183,3 +183,54 @@ def test_accuracy_simulation_runs_and_orders_the_methods():
     assert m["wiener"]["max"] < m["no_filter"]["max"]
     assert m["wiener"]["timestream_error"] < m["no_filter"]["timestream_error"]
     assert m["no_filter"]["median_at_channel_centres"] < 0.05
+
+
+def test_ml_stream_matches_oracle_overlap_save():
+    """ipfb_ml_solve_stream (overlap-save ML over a run longer than one solve) against
+    the oracle's chunk-by-chunk solve with the same chunks: lblock 256, a run of 1280
+    spectra in chunks of 512 with 64-frame margins (three chunks, the last aligned to
+    the run's end), the Sec. 4.3 protocol per chunk (a fixed 25 plain-CG steps from a
+    given initial guess, unit weights), so both sides take the same Krylov steps and
+    agree to FP32 round-off amplified by 25 steps; iterations and residuals are the
+    largest over the chunks."""
+    N, chunk, margin, nspec = 256, 512, 64, 1280
+    x = synth.stream_config(N, nspec, 43)
+    w = opfb.sinc_hamming_window(N, 4).astype(np.float32).astype(np.float64)
+    codes, scale, spec = opfb.pfb_forward(x, w)
+    d = oml.polyphase_data(codes, scale, N)
+    sig2 = float(np.var(d - opfb.polyphase_sum(x, w)))
+    L = synth.saved_paths(N, 0.03)
+    mask = synth.path_sample_mask(N, nspec, L)
+    prior = x.astype(np.float32)
+    rng = np.random.default_rng(44)
+    x0 = (x + 0.3 * rng.standard_normal(x.shape)).astype(np.float32)
+    lam = 1.0 / sig2
+    xg, it, res = ipfb.ml_solve_stream(cuda(codes), cuda(scale), cuda(w.astype(np.float32)), sig2, cuda(mask),
+                                       cuda(prior), chunk, margin, prior_weight=lam, tol=0.0, max_iter=25,
+                                       x0=cuda(x0))
+    got = xg.cpu().numpy().astype(np.float64)
+    assert got.shape == ((nspec - 2 * margin) * N,)
+    ref, oit, _ = oml.ml_solve_stream(codes, scale, w, sig2, mask, prior.astype(np.float64), chunk, margin, lam,
+                                      "none", 0.0, 25, x0.astype(np.float64))
+    rel = np.sqrt(np.mean((got - ref) ** 2) / np.mean(ref ** 2))
+    assert rel < 1e-4, rel
+    assert int(it.max()) == 25 and np.all(it.cpu().numpy() <= 25)
+    # the interior of every chunk is written once: no frame left at the initial guess
+    x0k = x0.reshape(nspec, N)[margin:nspec - margin].reshape(-1).astype(np.float64)
+    assert np.min(np.abs(got - x0k).reshape(-1, N).max(axis=1)) > 0
+
+
+def test_ml_stream_argument_checks():
+    N, chunk = 256, 512
+    g = ipfb.geom(N, 4, chunk)
+    f = ipfb.lib().ipfb_ml_solve_stream
+    fake = torch.empty(1 << 16, device="cuda")
+    p = ipfb.ctypes.c_void_p(fake.data_ptr())
+    prm = ipfb.MLParams(0.1, 1.0, 1e-6, 10, 2, 0)
+    # the learned preconditioner is not offered chunk by chunk
+    assert f(ipfb.ctypes.byref(g), 1024, p, p, p, ipfb.ctypes.byref(prm), p, p, None, 64, p, p, p, p, 1 << 30,
+             None) == ipfb.ERR_UNSUPPORTED
+    prm = ipfb.MLParams(0.1, 1.0, 1e-6, 10, 0, 0)
+    for nspec, margin in ((500, 64), (1024, 256), (1024, -1)):
+        assert f(ipfb.ctypes.byref(g), nspec, p, p, p, ipfb.ctypes.byref(prm), p, p, None, margin, p, p, p, p,
+                 1 << 30, None) == ipfb.ERR_INVALID

@@ -149,3 +149,30 @@ def test_pfb_upchannelize_reduces_to_block_dft_and_matches_pfb():
     X = upchan.pfb_upchannelize(np.cos(2 * np.pi * c0 * t / L), w)
     pw = np.mean(np.abs(X) ** 2, axis=0)
     assert pw[c0] > 1e3 * np.delete(pw, c0).max()
+
+
+def test_ml_stream_single_chunk_is_the_solve_and_chunks_stitch_in_place():
+    from oracle import pfb as opfb
+    # One chunk covering the run (margin 0) is exactly ml_solve.  With the prior on
+    # every sample (a short-ranged inverse operator, decay of a few frames) the chunked
+    # solve agrees with the solve of the whole run on every kept frame, which checks
+    # the chunk starts, the kept range and the stitching offsets: a one-frame shift
+    # anywhere fails.
+    from oracle import ml as oml
+    N, p, J = 8, 4, 192
+    rng = np.random.default_rng(3)
+    w = opfb.sinc_hamming_window(N, p)
+    x = rng.standard_normal(J * N)
+    codes, scale, spec = opfb.pfb_forward(x, w)
+    mask = np.ones(J * N, np.uint8)
+    sig2, lam = 0.02, 50.0   # |W|^2 / sigma^2 + lam within [50, 100]: decay well under a frame
+    xa, ia, ra = oml.ml_solve(codes, scale, w, sig2, mask, x, lam, "wiener", 1e-12, 500)
+    xs, is_, rs = oml.ml_solve_stream(codes, scale, w, sig2, mask, x, J, 0, lam, "wiener", 1e-12, 500)
+    assert np.array_equal(xs, xa) and np.array_equal(is_, ia)
+    chunk, margin = 64, 24
+    xs, _, _ = oml.ml_solve_stream(codes, scale, w, sig2, mask, x, chunk, margin, lam, "wiener", 1e-12, 500)
+    ref = xa.reshape(J, N)[margin:J - margin].reshape(-1)
+    assert np.max(np.abs(xs - ref)) <= 1e-8 * np.max(np.abs(ref))
+    # a stitching error shows: the same solve shifted by one frame is far off
+    shifted = xa.reshape(J, N)[margin + 1:J - margin + 1].reshape(-1)
+    assert np.max(np.abs(xs - shifted)) > 0.1 * np.max(np.abs(ref))
