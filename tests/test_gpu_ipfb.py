@@ -223,7 +223,10 @@ def test_upchannelize_tone_and_nyquist():
 # ----------------------------------------------------------------------------- pipeline
 @pytest.mark.parametrize("N,J,U,run", [(256, 512, 64, 8192), (512, 256, 64, 8192), (64, 1024, 64, 512),
                                        (2048, 128, 64, 8192), (1024, 256, 64, 8192), (1024, 1024, 64, 512),
-                                       (4096, 128, 64, 8192)])
+                                       (4096, 128, 64, 8192),
+                                       # columns longer than the run: clusters of C = 4 and 8 CTAs
+                                       # of S = 512 frames, lblock 1024 / 2048 / 4096
+                                       (1024, 2048, 64, 512), (2048, 4096, 64, 512), (4096, 4096, 64, 512)])
 def test_ipfb_wiener_upchannelize(N, J, U, run):
     ipfb.set_max_column_run(run)
     x = synth.stream_config(N, J, 13, ntones=4)
