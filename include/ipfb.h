@@ -394,8 +394,10 @@ int ipfb_ml_training_pairs(const ipfb_geom* g, const float* window, const ipfb_m
  * ipfb_batched_plan builds the host-side plan (no device work) and returns the
  * workspace size; tune_cache (a file path, or NULL) supplies per-M kernel
  * variants written by ipfb_batched_autotune.  ipfb_batched_prepare uploads the
- * descriptors and builds the chirp and FFT(chirp) tables in the workspace; it
- * synchronizes `stream` and cannot be captured.  ipfb_batched_run enqueues the
+ * descriptors (from host arrays the plan owns until ipfb_batched_free) and builds the
+ * chirp and FFT(chirp) tables in the workspace, asynchronously on `stream`; its
+ * copies come from pageable host memory, so it cannot be captured in a CUDA graph
+ * (replan and prepare outside the capture).  ipfb_batched_run enqueues the
  * inversion (a counter reset and the persistent kernels, no host
  * synchronization); after a prepare with the same workspace it can be captured
  * in a CUDA graph and replayed.  ipfb_batched_autotune times every kernel

@@ -48,6 +48,7 @@ struct Plan {
   size_t off_streams = 0, off_items2 = 0, off_items4 = 0, off_items3[kNumMClass] = {}, off_counters = 0;
   size_t off_Js = 0, off_Ms = 0, off_chirp_ptr = 0, off_bhat_ptr = 0;
   std::vector<size_t> off_chirp, off_bhat, off_d2;
+  std::vector<float2*> chirp_ptr, bhat_ptr;  // device addresses of the tables, uploaded by prepare
   size_t total = 0;
   // defaults = the autotuner's choice on the 256-stream batch (M = 2048 .. 32768)
   int variant[kNumMClass] = {0, 2, 2, 0, 3};
@@ -136,7 +137,12 @@ int prepare(Plan& P, char* ws, cudaStream_t stream) {
     P.st[s].chirp = reinterpret_cast<const float2*>(ws + P.off_chirp[P.jidx[s]]);
     P.st[s].bhat = reinterpret_cast<const float2*>(ws + P.off_bhat[P.jidx[s]]);
   }
-  std::vector<float2*> cp(P.Js.size()), bp(P.Js.size());
+  // the pointer tables live in the plan, like every other uploaded array, so that the
+  // host side of every copy outlives it without a synchronisation here
+  std::vector<float2*>& cp = P.chirp_ptr;
+  std::vector<float2*>& bp = P.bhat_ptr;
+  cp.assign(P.Js.size(), nullptr);
+  bp.assign(P.Js.size(), nullptr);
   for (size_t t = 0; t < P.Js.size(); ++t) {
     cp[t] = reinterpret_cast<float2*>(ws + P.off_chirp[t]);
     bp[t] = reinterpret_cast<float2*>(ws + P.off_bhat[t]);
@@ -154,8 +160,6 @@ int prepare(Plan& P, char* ws, cudaStream_t stream) {
   BCK(up(P.off_Ms, P.Ms.data(), P.Ms.size() * sizeof(int)), "upload M");
   BCK(up(P.off_chirp_ptr, cp.data(), cp.size() * sizeof(float2*)), "upload ptr");
   BCK(up(P.off_bhat_ptr, bp.data(), bp.size() * sizeof(float2*)), "upload ptr");
-  // the host vectors above must outlive the copies: make them complete here
-  BCK(cudaStreamSynchronize(stream), "prepare sync");
   const int nJ = (int)P.Js.size();
   const int* dJ = reinterpret_cast<const int*>(ws + P.off_Js);
   const int* dM = reinterpret_cast<const int*>(ws + P.off_Ms);
