@@ -25,8 +25,8 @@ struct Variant {
   const char* name;
 };
 constexpr Variant kVariants[] = {{4, 256, 32, "c4_t256_r32"}, {4, 256, 16, "c4_t256_r16"}, {2, 256, 32, "c2_t256_r32"},
-                                 {8, 256, 32, "c8_t256_r32"}};
-constexpr int kNumVariants = 4;
+                                 {8, 256, 32, "c8_t256_r32"}, {1, 512, 32, "c1_t512_r32"}};
+constexpr int kNumVariants = 5;
 constexpr int kNumMClass = 5;  // M = 2048 .. 32768
 
 int mclass(int M) {
@@ -34,7 +34,11 @@ int mclass(int M) {
   while ((2048 << c) < M) ++c;
   return c;
 }
-bool variant_ok(int v, int M) { return M / kVariants[v].C <= 8192 && M / kVariants[v].C >= 512; }
+// a CTA of a cluster holds up to 8192 elements (two buffers); a single CTA up to 16384 (one)
+bool variant_ok(int v, int M) {
+  const int S = M / kVariants[v].C;
+  return S <= (kVariants[v].C == 1 ? 16384 : 8192) && S >= 512;
+}
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -108,6 +112,7 @@ cudaError_t kb3_launch_v0(int, const BStream*, const BItem*, int, int*, cudaStre
 cudaError_t kb3_launch_v1(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb3_launch_v2(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb3_launch_v3(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb3_launch_v4(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 }  // namespace ipfb
 
 namespace {
@@ -125,6 +130,7 @@ int launch_kb3(const Plan& P, char* ws, int cls, int v, cudaStream_t stream) {
     case 1: e = kb3_launch_v1(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
     case 2: e = kb3_launch_v2(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
     case 3: e = kb3_launch_v3(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
+    case 4: e = kb3_launch_v4(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
   }
   if (e != cudaSuccess) return fail(e, "kb3_columns");
   return IPFB_OK;

@@ -166,7 +166,8 @@ __device__ __forceinline__ void column_item(const BStream& st, int p, float2* sm
     __syncthreads();
   }
   // 3. pair split + gain: partner -k mod J lives in CTA (-k mod J) % C; X'[k] goes to
-  //    the second buffer sm2 so that partners still read unmodified X.
+  //    the second buffer sm2 so that partners still read unmodified X.  One CTA (C = 1)
+  //    holds both modes of every pair, so one thread splits k and J - k in place.
   float2* sm2 = sm + padded_len(S);
   float ta[4], tb[4];
 #pragma unroll
@@ -181,6 +182,22 @@ __device__ __forceinline__ void column_item(const BStream& st, int p, float2* sm
   gp.J = J;
   gp.out_block_major = 0;
   gp.ntap = 4;
+  if constexpr (C == 1) {
+#pragma unroll 1
+    for (int k = threadIdx.x; k <= J / 2; k += T) {
+      const int km = (J - k) % J;
+      float2 xk = sm[pidx(k)], xm = sm[pidx(km)];
+      const float2 e1 = twiddle<false>(k, J);
+      const float2 ga = gain_at<4>(ta, k, e1, gp), gb = gain_at<4>(tb, k, e1, gp);
+      split_gain(xk, xm, ga, gb);
+      // 4. the inverse transform's input: a'[k] = conj(X'[k]) w[k]
+      sm[pidx(k)] = cmul(cconj(xk), __ldg(w + k));
+      if (km != k) sm[pidx(km)] = cmul(cconj(xm), __ldg(w + km));
+    }
+#pragma unroll 1
+    for (int k = J + threadIdx.x; k < S; k += T) sm[pidx(k)] = make_float2(0.0f, 0.0f);  // zero padding
+    __syncthreads();
+  } else {
 #pragma unroll 1
   for (int m = threadIdx.x; m < S; m += T) {
     const int k = C * m + r;
@@ -207,6 +224,7 @@ __device__ __forceinline__ void column_item(const BStream& st, int p, float2* sm
 #pragma unroll 1
   for (int m = threadIdx.x; m < S; m += T) sm[pidx(m)] = sm2[pidx(m)];
   __syncthreads();
+  }
   conv_engine<C, S, T, MAXR, false>(sm, st.bhat, nullptr, r);
   // 5. x[j] = conj(w[j] conv'[j] / M)
 #pragma unroll 1
@@ -278,7 +296,7 @@ kb2_unpack(const BStream* __restrict__ streams, const BItem* __restrict__ items,
 // the largest and spilled ~3.7 KB per thread), and limited to 128 registers so two
 // CTAs share an SM (measured faster than one CTA with 255 registers).
 template <int C, int S, int T, int MAXR>
-__global__ void __launch_bounds__(T, 2)
+__global__ void __launch_bounds__(T, (C == 1 ? 1 : 2))
 kb3_columns(const BStream* __restrict__ streams, const BItem* __restrict__ items, int nitems, int* counter) {
   extern __shared__ float2 smem[];
   (void)counter;
@@ -306,7 +324,8 @@ struct Kb3Launch {
   template <int S>
   static cudaError_t go(const BStream* s, const BItem* it, int n, int* ctr, cudaStream_t stream, int* nclusters) {
     auto kern = kb3_columns<C, S, T, MAXR>;
-    const size_t smem = 2 * (size_t)padded_len(S) * sizeof(float2);
+    // one buffer for a single CTA (the pair split runs in place), two for a cluster
+    const size_t smem = (C == 1 ? 1 : 2) * (size_t)padded_len(S) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -334,6 +353,9 @@ struct Kb3Launch {
   }
   static cudaError_t launch(int M, const BStream* s, const BItem* it, int n, int* ctr, cudaStream_t stream,
                             int* nclusters) {
+    if constexpr (C == 1) {
+      if (M == 16384) return go<16384>(s, it, n, ctr, stream, nclusters);
+    }
     switch (M / C) {
       case 512: return go<512>(s, it, n, ctr, stream, nclusters);
       case 1024: return go<1024>(s, it, n, ctr, stream, nclusters);

@@ -23,7 +23,12 @@ SHAPES = [(1024, 1031), (2048, 1500), (4096, 1024), (1024, 2310), (2048, 4099), 
 
 
 # column-kernel variants (cluster size, threads, largest radix) and their cluster sizes
-VARIANTS = {"c4_t256_r32": 4, "c4_t256_r16": 4, "c2_t256_r32": 2, "c8_t256_r32": 8}
+VARIANTS = {"c4_t256_r32": 4, "c4_t256_r16": 4, "c2_t256_r32": 2, "c8_t256_r32": 8, "c1_t512_r32": 1}
+
+
+def _in_range(M, C):
+    # a CTA of a cluster holds up to 8192 elements, a single CTA up to 16384
+    return 512 <= M // C <= (16384 if C == 1 else 8192)
 
 
 def relrms(a, b):
@@ -99,8 +104,8 @@ def test_batched_autotune_cache_and_graph_replay():
 @pytest.mark.parametrize("name", sorted(VARIANTS))
 def test_batched_each_variant_matches_oracle(name):
     # one stream per Bluestein length class M = 4096 .. 32768, every class forced to
-    # `name` through a tune cache (classes outside the variant's range M / C in
-    # [512, 8192] keep the default variant)
+    # `name` through a tune cache (classes outside the variant's range, M / C in
+    # [512, 8192] for a cluster and up to 16384 for one CTA, keep the default variant)
     shapes = [(1024, 1031), (2048, 1500), (1024, 2310), (2048, 4099), (1024, 9000)]
     streams, host = _streams(shapes, 700)
     C = VARIANTS[name]
@@ -112,7 +117,7 @@ def test_batched_each_variant_matches_oracle(name):
         plan = ipfb.BatchedPlan(streams, tune_cache=cache)
         for c in range(5):
             M = 2048 << c
-            if 512 <= M // C <= 8192:
+            if _in_range(M, C):
                 assert plan.variant(M) == name, M
     xs = plan.run()
     torch.cuda.synchronize()
