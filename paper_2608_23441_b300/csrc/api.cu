@@ -558,9 +558,9 @@ MLParams ml_params(const ipfb_geom* g, const ipfb_ml_params* prm, int use_x0) {
 // The WHILE body is two flexible-CG iterations with the two request counters in
 // fixed roles; the loop control kernel keeps it running while a column is active.
 // When the caller's stream is not capturing, the graph is captured on a private stream,
-// instantiated, launched on the caller's stream and released (the release waits for
-// the launch to finish on the device, not on the host); when it is capturing, the same
-// nodes go into the caller's graph.
+// instantiated and launched on the caller's stream, and released by a later call once
+// an event recorded after the launch reports it finished; when the caller's stream is
+// capturing, the same nodes go into the caller's graph.
 struct Capture {
   cudaStream_t user = nullptr, cap = nullptr, body = nullptr;
   cudaStream_t own_cap = nullptr;
@@ -643,17 +643,54 @@ int capture_end_body(Capture& c) {
   return IPFB_OK;
 }
 
+// Executable graphs launched by the library, each with an event recorded after its
+// launch.  Destroying an executable graph that holds conditional nodes waits on the host
+// until its launch has finished, so a graph is released only once its event reports
+// completion, by a later call's sweep (cudaEventQuery does not block).
+struct LaunchedGraph {
+  cudaGraphExec_t exec;
+  cudaEvent_t done;
+};
+std::mutex g_graph_mu;
+std::vector<LaunchedGraph> g_graphs;
+
+void sweep_finished_graphs() {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  size_t keep = 0;
+  for (size_t i = 0; i < g_graphs.size(); ++i) {
+    const cudaError_t q = cudaEventQuery(g_graphs[i].done);
+    if (q == cudaErrorNotReady) {
+      g_graphs[keep++] = g_graphs[i];
+      continue;
+    }
+    if (q != cudaSuccess) (void)cudaGetLastError();  // e.g. a context reset since: drop the entry
+    cudaGraphExecDestroy(g_graphs[i].exec);
+    cudaEventDestroy(g_graphs[i].done);
+  }
+  g_graphs.resize(keep);
+}
+
 int capture_finish(Capture& c) {
   if (!c.own) return IPFB_OK;
   cudaGraph_t g = nullptr;
   c.active = false;
   CK(cudaStreamEndCapture(c.cap, &g), "cudaStreamEndCapture");
+  sweep_finished_graphs();
   cudaGraphExec_t ex = nullptr;
+  cudaEvent_t done = nullptr;
   cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
-  if (e == cudaSuccess) e = cudaGraphLaunch(ex, c.user);
-  if (ex) cudaGraphExecDestroy(ex);
   cudaGraphDestroy(g);
-  CK(e, "cudaGraphLaunch");
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ex, c.user);
+  if (e == cudaSuccess) e = cudaEventRecord(done, c.user);
+  if (e != cudaSuccess) {
+    // nothing was enqueued, or the launch itself failed: nothing of ours is in flight
+    if (ex) cudaGraphExecDestroy(ex);
+    if (done) cudaEventDestroy(done);
+    CK(e, "cudaGraphLaunch");
+  }
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  g_graphs.push_back({ex, done});
   return IPFB_OK;
 }
 

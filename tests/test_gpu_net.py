@@ -398,3 +398,31 @@ def test_net_wait_that_runs_out_falls_back_to_plain_cg():
     xl2, itl2, rl2 = ipfb.ml_solve(*args, precond="learned", net=th, tol=1e-6, max_iter=500)
     y2 = ipfb.net_forward(th, xin)
     assert bool(torch.isfinite(y2).all()) and bool((rl2[0] <= 1e-6).all())
+
+
+def test_learned_solve_returns_before_the_device_finishes():
+    """The learned solve enqueues its graph and returns: on a config-4 instance (device
+    time ~10 ms) the call's host time is a small fraction of the device time, also on
+    later calls (a launched graph is released only once it has finished, by a later call,
+    never by waiting for it)."""
+    import time
+    from paper_2608_23441_b300 import precond_train as pt
+    dev = torch.device("cuda", 0)
+    inst = pt.instance(torch, dev, 4, fraction=0.1)
+    args = (inst["codes"], inst["scale"], inst["w"], inst["sig2"], inst["mask"], inst["x"])
+    th = torch.from_numpy(pt.init_theta(0, scale3=0.0)).to(dev)
+    g = ipfb.geom(4096, 4, 8192)
+    ws = torch.empty(ipfb.workspace_size(g, ipfb.OP_ML_LEARNED), dtype=torch.uint8, device=dev)
+    ipfb.ml_solve(*args, precond="learned", net=th, tol=1e-6, max_iter=4000, workspace=ws)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        t0 = time.perf_counter()
+        x, it, r = ipfb.ml_solve(*args, precond="learned", net=th, tol=1e-6, max_iter=4000, workspace=ws)
+        host_ms = 1e3 * (time.perf_counter() - t0)
+        e1.record()
+        torch.cuda.synchronize()
+        dev_ms = e0.elapsed_time(e1)
+        assert host_ms < 0.3 * dev_ms, (host_ms, dev_ms)
+        assert bool((r[0] <= 1e-6).all())
