@@ -184,12 +184,12 @@ def ipfb_column(codes: np.ndarray, scale: np.ndarray, window: np.ndarray, n: int
     return np.real(np.fft.ifft(G * Dn))
 
 
-def ipfb_columns(codes: np.ndarray, scale: np.ndarray, window: np.ndarray, ns,
-                 noise_level: float, normalize: bool = True, chunk: int = 4096) -> np.ndarray:
-    """Columns ns of the reconstruction, [J, len(ns)], evaluating step 1 only at the
-    requested indices (in chunks of spectra, so full-size inputs stay cheap)."""
+def data_columns(codes: np.ndarray, scale: np.ndarray, lblock: int, ns, chunk: int = 4096) -> np.ndarray:
+    """Columns ns of the polyphase data d (step 1: the N-point inverse real FFT of the
+    dequantized spectra), [J, len(ns)], evaluated only at the requested indices (in
+    chunks of spectra, so full-size inputs stay cheap)."""
     from .pfb import unpack_codes
-    p, N = window.shape
+    N = lblock
     ns = np.asarray(ns, dtype=np.int64)
     J, half = codes.shape
     C = half + 1
@@ -204,6 +204,17 @@ def ipfb_columns(codes: np.ndarray, scale: np.ndarray, window: np.ndarray, ns,
         q_re, q_im = unpack_codes(codes[j0:j0 + chunk])
         Y = (q_re.astype(np.float64) + 1j * q_im.astype(np.float64)) * s[None, :]
         d[j0:j0 + chunk] = np.real(Y @ ph) / N
+    return d
+
+
+def ipfb_columns(codes: np.ndarray, scale: np.ndarray, window: np.ndarray, ns,
+                 noise_level: float, normalize: bool = True, chunk: int = 4096) -> np.ndarray:
+    """Columns ns of the reconstruction, [J, len(ns)], evaluating step 1 only at the
+    requested indices (data_columns)."""
+    p, N = window.shape
+    ns = np.asarray(ns, dtype=np.int64)
+    J = codes.shape[0]
+    d = data_columns(codes, scale, N, ns, chunk)
     out = np.empty_like(d)
     for i, n in enumerate(ns):
         Wn = eigenvalues(window[:, n:n + 1], J)[:, 0]

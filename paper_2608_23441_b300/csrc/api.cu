@@ -278,20 +278,28 @@ int ipfb_workspace_size(const ipfb_geom* g, int op, size_t* bytes) {
       *bytes = 2 * al256((size_t)g->nframes * (size_t)g->lblock * sizeof(float));
       return IPFB_OK;
     case IPFB_OP_ML:
+    case IPFB_OP_ML_STREAM: {
       rc = check_geom(g, true);
       if (rc) return rc;
-      if (g->nframes < 128 || g->nframes > 8192) return IPFB_ERR_UNSUPPORTED;
-      *bytes = 2 * (size_t)g->nframes * (size_t)g->lblock * sizeof(float);
+      if (g->nframes < 128) return IPFB_ERR_UNSUPPORTED;
+      // columns up to the on-chip run are solved by one CTA per pair (d and x in pairs);
+      // longer ones keep the CG vectors in HBM in the column transform's residue layout
+      int C, S;
+      column_split(g->nframes, &C, &S);
+      size_t ml = 0;
+      if (C == 1) {
+        ml = 2 * (size_t)g->nframes * (size_t)g->lblock * sizeof(float);
+      } else {
+        if (S != 512 && S != 8192) return IPFB_ERR_UNSUPPORTED;  // the cluster transform's runs
+        ml = mlb_workspace(g->lblock, C, S);
+      }
+      // the stream adds the chunk's time-order solution, its iterations and residuals
+      *bytes = op == IPFB_OP_ML ? ml
+                                : al256(ml) + al256((size_t)g->nframes * (size_t)g->lblock * sizeof(float)) +
+                                      al256((size_t)g->lblock * sizeof(int)) +
+                                      al256(2 * (size_t)g->lblock * sizeof(float));
       return IPFB_OK;
-    case IPFB_OP_ML_STREAM:
-      rc = check_geom(g, true);
-      if (rc) return rc;
-      if (g->nframes < 128 || g->nframes > 8192) return IPFB_ERR_UNSUPPORTED;
-      // one chunk's solve, the chunk's time-order solution, its iterations and residuals
-      *bytes = al256(2 * (size_t)g->nframes * (size_t)g->lblock * sizeof(float)) +
-               al256((size_t)g->nframes * (size_t)g->lblock * sizeof(float)) +
-               al256((size_t)g->lblock * sizeof(int)) + al256(2 * (size_t)g->lblock * sizeof(float));
-      return IPFB_OK;
+    }
     case IPFB_OP_ML_LEARNED:
     case IPFB_OP_ML_PAIRS:
       rc = check_geom(g, true);
@@ -769,12 +777,79 @@ int ml_solve_learned(const ipfb_geom* g, const uint8_t* codes, const float* scal
   t.done();
   return IPFB_OK;
 }
+// Plain / Wiener-preconditioned ML solve with the CG vectors in HBM (columns longer than
+// the on-chip run), one CUDA graph:
+//   k2 (d in the residue layout), transpose of mask / prior / initial guess, right-hand
+//   side and r0, init, [K3 on z with r.z], control, WHILE { two CG iterations }, true
+//   residual and report, back to time order.
+// Each iteration is mlb_ap, mlb_xr, [K3 (ML gain, listed pairs, r.z)], mlb_ctl; the
+// two iterations of the body alternate the search-direction buffers, and the second
+// control sets the loop condition (a pair still listed and iterations left).
+int ml_solve_big(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
+                 const MLParams& mp, const uint8_t* mask, const float* prior, float* x_inout, int* iters,
+                 float* resid, void* ws, int C, int S, cudaStream_t st) {
+  const int N = g->lblock, J = g->nframes;
+  const MlbGeom G = mlb_geom(N, C, S);
+  MlbBufs b = mlb_carve(ws, N, C, S);
+  if (mp.precond == 0) b.Z = b.R;
+  MlGainParams gp;
+  gp.phi2 = 0.0f;
+  gp.gnorm = 1.0f;
+  gp.invJ = 1.0f / (float)J;
+  gp.J = J;
+  gp.ntap = g->ntap;
+  gp.out_block_major = 0;
+  gp.inv_s2 = mp.inv_s2;
+  gp.lam_m = b.lam_m;
+  gp.rz_out = b.rzk;
+  MlGainParams gl = gp;
+  gl.pair_list = b.list;
+  gl.pair_count = b.ctl;
+  int rc;
+  Stage t("k5_mlbig_solve", st);
+  Capture c;
+  if ((rc = capture_begin(c, st))) return rc;
+  cudaStream_t s = c.cap;
+  CK(launch_k2(N / 2, codes, scale, b.Q, C, S, s), "k2_unpack_irfft");
+  CK(launch_mlb_transpose(mask, prior, mp.use_x0 ? x_inout : nullptr, mp.lam, G, b, s), "k_mlb_transpose");
+  CK(launch_mlb_rhs(window, mp, G, b, s), "k_mlb_rhs");
+  CK(launch_mlb_init(mp, G, b, s), "k_mlb_init");
+  if (mp.precond == 1) CK(launch_k3_ml(C, S, b.Z, window, N, gp, s), "k3_column_ml");
+  cudaGraphConditionalHandle h;
+  if ((rc = capture_handle(c, 0, &h))) return rc;
+  CK(launch_mlb_ctl(1, 1, h, mp, G, b, s), "k_mlb_ctl");
+  if ((rc = capture_conditional(c, h, cudaGraphCondTypeWhile))) return rc;
+  {
+    cudaStream_t bs = c.body;
+    for (int half = 0; half < 2; ++half) {
+      CK(launch_mlb_ap(half, mp, G, b, bs), "k_mlb_ap");
+      CK(launch_mlb_xr(half ^ 1, mp, G, b, bs), "k_mlb_xr");
+      if (mp.precond == 1) CK(launch_k3_ml(C, S, b.Z, window, N, gl, bs), "k3_column_ml");
+      CK(launch_mlb_ctl(0, half, h, mp, G, b, bs), "k_mlb_ctl");
+    }
+  }
+  if ((rc = capture_end_body(c))) return rc;
+  CK(launch_mlb_finish(mp, G, b, iters, resid, s), "k_mlb_finish");
+  CK(launch_pairs_to_time(b.X, x_inout, N, C, S, s), "k_pairs_to_time");
+  if ((rc = capture_finish(c))) return rc;
+  t.done();
+  return IPFB_OK;
+}
+
 // Plain / Wiener-preconditioned ML solve (precond 0 or 1) of one J-frame block:
-// unpack + per-frame inverse FFT, [initial guess to pairs], k5_ml_cg, back to time order.
+// unpack + per-frame inverse FFT, [initial guess to pairs], k5_ml_cg, back to time order;
+// columns longer than the on-chip run take ml_solve_big.
 int ml_solve_core(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
                   const ipfb_ml_params* prm, const uint8_t* prior_mask, const float* prior_values, float* x_inout,
                   int use_x0, int* iters, float* resid, void* ws, cudaStream_t st) {
   const int N = g->lblock, J = g->nframes;
+  {
+    int C, S;
+    column_split(J, &C, &S);
+    if (C > 1)
+      return ml_solve_big(g, codes, scale, window, ml_params(g, prm, use_x0), prior_mask, prior_values, x_inout,
+                          iters, resid, ws, C, S, st);
+  }
   float2* d2 = reinterpret_cast<float2*>(ws);
   float2* x2 = d2 + (size_t)J * (N / 2);
   {

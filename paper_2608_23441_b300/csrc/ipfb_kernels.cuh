@@ -280,6 +280,126 @@ __device__ __forceinline__ void pair_gain(float2& zk, float2& zm, const float* t
   zm = make_float2(P.x - Q.x, Q.y - P.y);
 }
 
+// Gain policies of K3's per-mode step (modes k and -k of both columns of pair p):
+//   WienerGain: the eigenvalue filter of GainParams (Wiener in one fused step for a
+//     compile-time tap count; any filter mode with the generic taps);
+//   MlGain: the ML solve's Wiener preconditioner (Sec. 4.2), the real gain
+//     G = 1 / (|W|^2 inv_s2 + lam_m[col]) / J, 0 where the denominator vanishes.
+template <int NT>
+struct WienerGain {
+  __device__ __forceinline__ static void pair(float2& zk, float2& zm, const float* ta, const float* tb, int k,
+                                              float2 e1, const GainParams& gp, int p) {
+    if constexpr (NT > 0) {
+      pair_gain<NT>(zk, zm, ta, tb, k, e1, gp);
+    } else {
+      const float2 ga = filter_gain<NT>(ta, k, e1, gp, 2 * p), gb = filter_gain<NT>(tb, k, e1, gp, 2 * p + 1);
+      split_gain(zk, zm, ga, gb);
+    }
+  }
+  __device__ __forceinline__ static void single(float2& a, float2& b, const float* ta, const float* tb, int k,
+                                                float2 e1, const GainParams& gp, int p, bool self) {
+    (void)self;
+    const float2 ga = filter_gain<NT>(ta, k, e1, gp, 2 * p), gb = filter_gain<NT>(tb, k, e1, gp, 2 * p + 1);
+    split_gain(a, b, ga, gb);
+  }
+  __device__ __forceinline__ static void finish(const GainParams&, int) {}
+};
+
+template <int NT>
+struct MlGain {
+  // With the real gain g, z = M r has r.z = sum_k g(k) |R(k)|^2 (Parseval for the
+  // unnormalised transform pair), accumulated here per column while the gains are applied
+  float acc_a = 0.0f, acc_b = 0.0f;
+
+  // 1 / (|W|^2 inv_s2 + lam_m) / J from |W|^2; a preconditioner only needs a fixed
+  // positive gain, so the fast division serves (denominators below 1e-30 give 0)
+  __device__ __forceinline__ static float from_w2(float a2, const MlGainParams& gp, int col) {
+    const float P = fmaf(a2, gp.inv_s2, __ldg(gp.lam_m + col));
+    return P > 1e-30f ? __fdividef(gp.invJ, P) : 0.0f;
+  }
+  // modes k and -k (w = 1), or one self-conjugate mode passed as both (w = 1/2)
+  __device__ __forceinline__ void apply(float2& zk, float2& zm, const float* ta, const float* tb, float2 e1,
+                                        const MlGainParams& gp, int p, float w) {
+    float2 Wa, Wb;
+    if constexpr (NT > 0) {
+      // both columns share the powers of e1
+      float2 ep[NT];
+      ep[0] = make_float2(1.0f, 0.0f);
+      if constexpr (NT > 1) ep[1] = e1;
+#pragma unroll
+      for (int q = 2; q < NT; ++q) ep[q] = cmul(ep[q / 2], ep[q - q / 2]);
+      Wa = make_float2(ta[0], 0.0f);
+      Wb = make_float2(tb[0], 0.0f);
+#pragma unroll
+      for (int q = 1; q < NT; ++q) {
+        Wa.x = fmaf(ta[q], ep[q].x, Wa.x);
+        Wa.y = fmaf(ta[q], ep[q].y, Wa.y);
+        Wb.x = fmaf(tb[q], ep[q].x, Wb.x);
+        Wb.y = fmaf(tb[q], ep[q].y, Wb.y);
+      }
+    } else {
+      Wa = make_float2(0.0f, 0.0f);
+      Wb = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int t = kMaxTaps - 1; t >= 0; --t) {
+        if (t < gp.ntap) {
+          Wa = cmul(Wa, e1);
+          Wa.x += ta[t];
+          Wb = cmul(Wb, e1);
+          Wb.x += tb[t];
+        }
+      }
+    }
+    const float ga = from_w2(fmaf(Wa.x, Wa.x, Wa.y * Wa.y), gp, 2 * p);
+    const float gb = from_w2(fmaf(Wb.x, Wb.x, Wb.y * Wb.y), gp, 2 * p + 1);
+    // real gains: Z'_k = ga A + i gb B, Z'_-k = conj(ga A) + i conj(gb B) with
+    // A = (Z_k + conj Z_-k)/2 = sv/2 and B = (Z_k - conj Z_-k)/(2i) = dv/(2i)
+    const float2 sv = make_float2(zk.x + zm.x, zk.y - zm.y);
+    const float2 dv = make_float2(zk.x - zm.x, zk.y + zm.y);
+    const float2 P = cscale(sv, 0.5f * ga), Q = cscale(dv, 0.5f * gb);
+    zk = cadd(P, Q);
+    zm = make_float2(P.x - Q.x, Q.y - P.y);
+    // modes k and -k add 2 g |A|^2 = g |sv|^2 / 2 (half that for a self-conjugate mode)
+    acc_a = fmaf(0.5f * w * ga, fmaf(sv.x, sv.x, sv.y * sv.y), acc_a);
+    acc_b = fmaf(0.5f * w * gb, fmaf(dv.x, dv.x, dv.y * dv.y), acc_b);
+  }
+  __device__ __forceinline__ void pair(float2& zk, float2& zm, const float* ta, const float* tb, int k, float2 e1,
+                                       const MlGainParams& gp, int p) {
+    (void)k;
+    apply(zk, zm, ta, tb, e1, gp, p, 1.0f);
+  }
+  __device__ __forceinline__ void single(float2& a, float2& b, const float* ta, const float* tb, int k, float2 e1,
+                                         const MlGainParams& gp, int p, bool self) {
+    (void)k;
+    apply(a, b, ta, tb, e1, gp, p, self ? 0.5f : 1.0f);
+  }
+  // the CTA's r.z of both columns to rz_out[2 slot + c] (FP32 within a warp, FP64 across)
+  __device__ __forceinline__ void finish(const MlGainParams& gp, int slot) {
+    if (!gp.rz_out) return;
+    __shared__ float red[2][32];
+    float a = acc_a, b = acc_b;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = a;
+      red[1][threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sa = 0.0, sb = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        sa += (double)red[0][w];
+        sb += (double)red[1][w];
+      }
+      gp.rz_out[2 * slot] = sa;
+      gp.rz_out[2 * slot + 1] = sb;
+    }
+  }
+};
+
 // ----------------------------------------------------------------------------
 // K3: per column pair: FFT_J along frames -> gain -> inverse FFT_J, in place on d2.
 // A cluster of C CTAs handles one pair; CTA r owns z[C m + r], m < S.
@@ -289,12 +409,11 @@ __device__ __forceinline__ void pair_gain(float2& zk, float2& zm, const float* t
 //      thread owns both and nothing crosses CTAs between 2 and 4
 //   4. inverse cross stage, pushed back to the owners, then local inverse FFT.
 // ----------------------------------------------------------------------------
-template <int C, int S, int T, int NT>
-__global__ void __launch_bounds__(T, (S >= 4096 ? 2 : 1))
-k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int N, GainParams gp) {
+template <int C, int S, int T, int NT, class GAIN, class GP>
+__device__ __forceinline__ void k3_pair(float2* __restrict__ d2, const float* __restrict__ window, int N, GP gp,
+                                        const int p) {
   extern __shared__ float2 sm[];
   const int tid = threadIdx.x;
-  const int p = blockIdx.x / C;
   int r = 0;
   if constexpr (C > 1) r = (int)cg::this_cluster().block_rank();
   float2* base = d2 + ((size_t)p * C + r) * S;
@@ -325,6 +444,7 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
   };
 
   // 2-4. tasks: t = 0 (kb = 0), t = S/2 (kb = S/2), else the pair (t, S - t)
+  GAIN gn;
   for (int t = r * T + tid; t <= S / 2; t += C * T) {
     const bool pairtask = (t != 0) && (2 * t != S);
     const int kb0 = t, kb1 = S - t;
@@ -358,12 +478,7 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
       for (int ka = 0; ka < C; ++ka) {
         const int k = kb0 + S * ka;
         const float2 e1 = rotq<C, false>(e0, ka);
-        if constexpr (NT > 0) {
-          pair_gain<NT>(z0[ka], z1[C - 1 - ka], ta, tb, k, e1, gp);
-        } else {
-          const float2 ga = filter_gain<NT>(ta, k, e1, gp, 2 * p), gb = filter_gain<NT>(tb, k, e1, gp, 2 * p + 1);
-          split_gain(z0[ka], z1[C - 1 - ka], ga, gb);
-        }
+        gn.pair(z0[ka], z1[C - 1 - ka], ta, tb, k, e1, gp, p);
       }
     } else if (t == 0) {
       // modes S*ka; -k is S*((C-ka) mod C)
@@ -372,9 +487,8 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
         const int km = (C - ka) % C;
         const int k = S * ka;
         const float2 e1 = rotq<C, false>(make_float2(1.0f, 0.0f), ka);
-        const float2 ga = filter_gain<NT>(ta, k, e1, gp, 2 * p), gb = filter_gain<NT>(tb, k, e1, gp, 2 * p + 1);
         float2 a = z0[ka], b = z0[km];
-        split_gain(a, b, ga, gb);
+        gn.single(a, b, ta, tb, k, e1, gp, p, km == ka);
         z0[ka] = a;
         if (km != ka) z0[km] = b;
       }
@@ -385,9 +499,8 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
         const int km = C - 1 - ka;
         const int k = kb0 + S * ka;
         const float2 e1 = rotq<C, false>(e0, ka);
-        const float2 ga = filter_gain<NT>(ta, k, e1, gp, 2 * p), gb = filter_gain<NT>(tb, k, e1, gp, 2 * p + 1);
         float2 a = z0[ka], b = z0[km];
-        split_gain(a, b, ga, gb);
+        gn.single(a, b, ta, tb, k, e1, gp, p, km == ka);
         z0[ka] = a;
         if (km != ka) z0[km] = b;
       }
@@ -413,6 +526,7 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
   } else {
     __syncthreads();
   }
+  gn.finish(gp, p * C + r);
   // 4. inverse local FFT: smem -> global, in place over this CTA's input run, or (for
   // the up-channelizer) in place over the pair's J frames in block-major order: frame
   // j at 64 (j >> 6) + 8 (j & 7) + ((j >> 3) & 7), i.e. each 64-frame block contiguous
@@ -428,6 +542,27 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
       base[m] = v;
     }
   }));
+}
+
+template <int C, int S, int T, int NT>
+__global__ void __launch_bounds__(T, (S >= 4096 ? 2 : 1))
+k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int N, GainParams gp) {
+  k3_pair<C, S, T, NT, WienerGain<NT>, GainParams>(d2, window, N, gp, blockIdx.x / C);
+}
+
+// The ML solve's preconditioner.  With a pair list (the solve's active pairs, ascending)
+// cluster c transforms pair pair_list[c] if c < *pair_count and exits otherwise; every
+// CTA of a cluster takes the same branch, before any cluster barrier.  (A persistent
+// loop over the list keeps the transform's state live across trips and spills.)
+template <int C, int S, int T, int NT>
+__global__ void __launch_bounds__(T, (S >= 4096 ? 2 : 1))
+k3_column_ml(float2* __restrict__ d2, const float* __restrict__ window, int N, MlGainParams gp) {
+  int p = blockIdx.x / C;
+  if (gp.pair_list) {
+    if (p >= __ldg(gp.pair_count)) return;
+    p = __ldg(gp.pair_list + p);
+  }
+  k3_pair<C, S, T, NT, MlGain<NT>, MlGainParams>(d2, window, N, gp, p);
 }
 
 // ----------------------------------------------------------------------------

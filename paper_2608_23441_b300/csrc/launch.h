@@ -22,6 +22,17 @@ struct GainParams {
   const float2* gains = nullptr;
 };
 
+// K3 with the ML solve's preconditioner gain (k3_column_ml): 1 / sigma^2, lam times the
+// mask fraction of each column, and an optional list of the pairs to transform
+// (*pair_count entries)
+struct MlGainParams : GainParams {
+  float inv_s2 = 0.0f;
+  const float* lam_m = nullptr;
+  const int* pair_list = nullptr;
+  const int* pair_count = nullptr;
+  double* rz_out = nullptr;  // [P][C][2]: each CTA's r.z of both columns (Parseval), or nullptr
+};
+
 struct UpchanSrc {
   const float* x;    // time order, or nullptr
   const float2* d2;  // column-pair scratch, or nullptr
@@ -45,6 +56,9 @@ cudaError_t launch_quantize(int H, long long nspec, const float2* spec, const fl
 cudaError_t launch_k2(int H, const uint8_t* codes, const float* scale, float2* d2, int C, int S,
                       cudaStream_t st);
 cudaError_t launch_k3(int C, int S, float2* d2, const float* window, int N, GainParams gp, cudaStream_t st);
+// K3 with the ML preconditioner gain on the residue splits C = 2, 4, 8 with S = 512 or 8192
+cudaError_t launch_k3_ml(int C, int S, float2* z2, const float* window, int N, const MlGainParams& gp,
+                         cudaStream_t st);
 cudaError_t launch_pairs_to_time(const float2* d2, float* x, int N, int C, int S, cudaStream_t st);
 struct MLParams {
   float inv_s2;  // 1 / sigma^2
@@ -75,6 +89,56 @@ bool upchan2_supported(int N, int C, int U);
 cudaError_t launch_k4a(const float2* d2, int N, int J, long long nblocks, float2* W, float* x_out,
                        cudaStream_t st);
 cudaError_t launch_k4b(const float2* W, int N, long long nblocks, float2* out, cudaStream_t st);
+
+// ---- ML solve with the CG vectors in HBM (columns longer than the on-chip run)
+// Every vector is [P C][S] in the column transform's residue layout: frame j = C m + r
+// of pair p at v[(p C + r) S + m], columns 2p and 2p+1 as the real and imaginary parts.
+struct MlbPair {
+  double rz[2];  // r.z of each column's current residual
+  float bn[2];   // |b| (1 where b = 0)
+  float beta[2];
+  float rel[2];  // recursive relative residual at the last test
+  int act;       // bit c: column 2p + c still iterating
+  int it[2];
+  int pad;
+};
+struct MlbBufs {
+  float2 *B, *X, *R, *Q, *Z;  // Q holds d until the right-hand side is built; Z = R without a preconditioner
+  float2* Pv[2];              // search direction, read from one and written to the other
+  uint8_t* mk;                // mask bits per pair-frame (bit c: column 2p + c saved)
+  float2* acoef;              // [P][16] stencil taps a_s / sigma^2 of both columns
+  double* part;               // [P][NT][8] per-tile partial sums
+  double* rzk;                // [P][8][2] r.z of both columns from each CTA of the preconditioner
+  MlbPair* ps;                // [P]
+  float* lam_m;               // [N] lam * mask fraction of each column
+  int* list;                  // [P] active pairs, ascending
+  int* ctl;                   // [0] active pairs, [1] iterations done, [2] block ticket
+};
+struct MlbGeom {
+  int N, C, S, logC;
+  int TM, logTM, NT;  // tile: TM positions of all C residues (TF = C TM frames), NT tiles per pair
+};
+MlbGeom mlb_geom(int N, int C, int S);
+size_t mlb_workspace(int N, int C, int S);
+MlbBufs mlb_carve(void* ws, int N, int C, int S);
+// mask, prior, initial guess (time order [J][N]) -> mask bits, lam m prior (in B), X
+cudaError_t launch_mlb_transpose(const uint8_t* mask, const float* prior, const float* x0, float lam,
+                                 const MlbGeom& g, const MlbBufs& b, cudaStream_t st);
+// b = C^T d / sigma^2 + lam m prior, r0 = b - A x0, [Z = r0]; per-tile |b|^2, mask counts, r.r
+cudaError_t launch_mlb_rhs(const float* window, const MLParams& mp, const MlbGeom& g, const MlbBufs& b,
+                           cudaStream_t st);
+// |b|, lam mbar, all pairs listed, counters cleared
+cudaError_t launch_mlb_init(const MLParams& mp, const MlbGeom& g, const MlbBufs& b, cudaStream_t st);
+// p' = z + beta p (Pv[src] -> Pv[src ^ 1]), q = A p', per-tile p'.q (listed pairs)
+cudaError_t launch_mlb_ap(int src, const MLParams& mp, const MlbGeom& g, const MlbBufs& b, cudaStream_t st);
+// x += alpha p', r -= alpha q, [Z = r], per-tile r.r (listed pairs)
+cudaError_t launch_mlb_xr(int dst, const MLParams& mp, const MlbGeom& g, const MlbBufs& b, cudaStream_t st);
+// stopping test, beta, iteration counts, the next list; sets h (if set_cond) to "a pair is listed"
+cudaError_t launch_mlb_ctl(int first, int set_cond, cudaGraphConditionalHandle h, const MLParams& mp,
+                           const MlbGeom& g, const MlbBufs& b, cudaStream_t st);
+// true residual b - A x, iterations and residuals out
+cudaError_t launch_mlb_finish(const MLParams& mp, const MlbGeom& g, const MlbBufs& b, int* iters, float* resid,
+                              cudaStream_t st);
 
 // ---- learned preconditioner: flexible CG state and the net
 struct FcgCol;

@@ -62,6 +62,29 @@ def test_learned_workspace_sizes():
     assert grad - fwd == 16 * ((8192 + 223) // 224) * (ipfb.NET_NPARAMS + 1) * 4
 
 
+def test_ml_workspace_beyond_the_on_chip_run():
+    g = ipfb.geom(2048, 4, 65536)
+    ml = ipfb.workspace_size(g, ipfb.OP_ML)
+    vec = 1024 * 65536 * 8  # one pair-packed vector
+    # seven vectors, the mask bits, per-tile partial sums and small state
+    assert 7 * vec + 1024 * 65536 <= ml <= 7 * vec + 1024 * 65536 + (8 << 20)
+    assert ipfb.workspace_size(g, ipfb.OP_ML_STREAM) >= ml + 2048 * 65536 * 4
+    with pytest.raises(ipfb.IpfbError):
+        ipfb.workspace_size(g, ipfb.OP_ML_LEARNED)
+    # the on-chip column run decides the form
+    g2 = ipfb.geom(64, 4, 2048)
+    assert ipfb.workspace_size(g2, ipfb.OP_ML) == 2 * 64 * 2048 * 4
+    assert ipfb.lib().ipfb_set_max_column_run(512) == 0
+    try:
+        assert ipfb.workspace_size(g2, ipfb.OP_ML) >= 7 * 32 * 2048 * 8
+        # 8192 frames would split into 8 runs of 1024: no cluster transform of that length
+        with pytest.raises(ipfb.IpfbError) as e:
+            ipfb.workspace_size(ipfb.geom(64, 4, 8192), ipfb.OP_ML)
+        assert e.value.rc == ipfb.ERR_UNSUPPORTED
+    finally:
+        ipfb.lib().ipfb_set_max_column_run(8192)
+
+
 def test_library_window_matches_oracle_window():
     for N, p in ((64, 4), (256, 4), (4096, 4), (128, 3)):
         w = ipfb.sinc_hamming_window(N, p)

@@ -140,6 +140,12 @@ def test_sampled_column_matches_full_inverse():
     full = ipfb.ipfb_wiener(codes, scale, w, 0.014).reshape(J, N)
     for n in (0, 1, N // 2, N - 1):
         assert np.allclose(ipfb.ipfb_column(codes, scale, w, n, 0.014), full[:, n], atol=1e-12)
+    # the sampled forms evaluate step 1 (the inverse real FFT) at single indices, in
+    # chunks of spectra that do not divide J
+    cols = [0, 3, N // 2, N - 1]
+    d = ipfb.frames_from_spectra(pfb.dequantize(codes, scale), N)
+    assert np.allclose(ipfb.data_columns(codes, scale, N, cols, chunk=20), d[:, cols], atol=1e-12)
+    assert np.allclose(ipfb.ipfb_columns(codes, scale, w, cols, 0.014, chunk=20), full[:, cols], atol=1e-12)
 
 
 def _mc_delta(N, J, w, phi2, noise_level, reps, seed):
