@@ -75,8 +75,10 @@ int ipfb_version(void);
 /*
  * Testing knob (no counterpart in the paper): the longest run of frames one CTA
  * transforms along a column (8192 by default; 512 is also accepted).  Columns
- * longer than the run are split over a thread-block cluster of up to 8 CTAs, so
- * a small run exercises the cluster path on small inputs.  Process-wide.
+ * longer than the run are split over a thread-block cluster of up to 8 CTAs, and
+ * ipfb_ml_solve (precond 0, 1) keeps their CG vectors in HBM instead of on chip, so
+ * a small run exercises both paths on small inputs.  Process-wide; it also decides
+ * ipfb_workspace_size's answer for IPFB_OP_ML and IPFB_OP_ML_STREAM.
  */
 int ipfb_set_max_column_run(int frames);
 
@@ -286,8 +288,16 @@ int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const flo
  * zero is used), the solution on return.  iters: int [N] iterations per column;
  * resid: float [2][N], recursive then true relative residual per column (the
  * true one recomputed from the final x).  Non-convergence is reported through
- * these arrays (the call itself returns 0).  Requires 128 <= J <= 8192.
- * Workspace: ipfb_workspace_size(g, IPFB_OP_ML).
+ * these arrays (the call itself returns 0).  Requires 128 <= J (a power of two);
+ * precond 0 and 1 take J up to 65536, precond 2 up to 8192.  Columns up to the
+ * on-chip run (8192 frames) are solved by one CTA per column pair with the vectors
+ * in shared memory and registers; longer ones keep the CG vectors in HBM in the
+ * column transform's residue layout (J = C S, C = 2, 4, 8), iterate as one CUDA graph
+ * whose loop is ended on the device (no host synchronisation, capturable like
+ * precond 2), take the Wiener step through the cluster column transform and drop
+ * converged column pairs from each iteration's work.
+ * Workspace: ipfb_workspace_size(g, IPFB_OP_ML): 2 J N floats up to the on-chip run,
+ * else about 28 J N bytes (seven pair-packed vectors, the mask bits, small state).
  */
 typedef struct {
   double noise_var;    /* sigma^2 (> 0) in units of d                        */
@@ -310,7 +320,7 @@ int ipfb_ml_solve(const ipfb_geom* g, const uint8_t* codes, const float* scale, 
  * (Sec. 4.2 solved block by block; the solution's dependence on data far away decays
  * along the frame axis, so a chunk solved as if periodic agrees with the solve of the
  * whole run away from the chunk's edges).  g->nframes is the chunk length J
- * (128 <= J <= 8192, a power of two); chunks of J spectra step by J - 2 margin, the
+ * (128 <= J <= 65536, a power of two); chunks of J spectra step by J - 2 margin, the
  * last one aligned to the end of the run; each is solved with its own stretch of
  * prior_mask, prior_values and (when x0 != NULL) initial guess x0, and its frames
  * margin .. J - margin are kept.  codes: uint8 [nspec][N/2] (16-byte aligned; N/2 a

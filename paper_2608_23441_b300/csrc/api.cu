@@ -196,7 +196,7 @@ const char* ipfb_strerror(int status) {
 
 const char* ipfb_last_cuda_error(void) { return g_cuda_err; }
 
-int ipfb_version(void) { return 101; }
+int ipfb_version(void) { return 102; }
 
 int ipfb_stage_timing(int enable) {
   std::lock_guard<std::mutex> lk(g_tmu);
