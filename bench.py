@@ -545,6 +545,65 @@ def run_ml(torch, ipfb, dev, reps=3, theta=None):
         out["learned_net_from"] = pt.NET_FROM
         out["learned_g0_note"] = "the same learned solve with a zero-output net (g = 0: the Wiener term alone)"
     out["paper_protocol"] = run_ml_paper_protocol(torch, ipfb, dev, codes, scale, w, prior, sig2, reps=reps)
+    del codes, scale, w, mask, prior
+    out["paper_size"] = run_ml_long(torch, ipfb, dev, reps=reps)
+    return out
+
+
+def run_ml_long(torch, ipfb, dev, reps=3, seed=11, N=2048, J=65536):
+    """The paper's size (Sec. 4.3: 2048-point 4-tap PFB over 65536 frames, 2^27 samples):
+    one ML solve of the whole run's circulant system to 1e-6 per column (past the
+    on-chip column run the CG vectors stay in HBM), plain CG and Wiener-PCG; 10 % of the
+    samples saved as 256 chunks, prior values = the true stream, sigma^2 measured as in
+    ml_inputs.  The overlap-save solve (chunks of 8192 frames, 512-frame margins) of the
+    same instance is timed beside it."""
+    from paper_2608_23441_b300 import synth
+    x = synth.gaussian_stream_torch(N * J, seed, dev)
+    w = torch.from_numpy(ipfb.sinc_hamming_window(N, NTAP)).to(dev)
+    codes, scale, _ = ipfb.pfb_forward(x, w)
+    xr = ipfb.ipfb_wiener(codes, scale, w, 0.0)
+    e = (xr - x).reshape(J, N).double()
+    wd = w.double()
+    sig2 = float(sum(wd[r][None, :] * torch.roll(e, -r, dims=0) for r in range(NTAP)).var())
+    del e, xr
+    starts, L = synth.prior_chunks(N * J, 256, 0.1, seed)
+    mask = torch.from_numpy(synth.mask_from_chunks(N * J, starts, L)).to(dev)
+    out = {"workload": f"ML CG lblock={N} ntap={NTAP} nframes={J} (2^27 samples), 10% prior in 256 chunks, "
+                       "tol 1e-6 per column", "noise_var": sig2}
+    stream = torch.cuda.current_stream()
+    ws = torch.empty(ipfb.workspace_size(ipfb.geom(N, NTAP, J), ipfb.OP_ML), dtype=torch.uint8, device=dev)
+    xn = float(torch.linalg.norm(x))
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, r
+
+    for pre in ("wiener", "none"):
+        ms, (xm, it, res) = timed(lambda: ipfb.ml_solve(codes, scale, w, sig2, mask, x, precond=pre, tol=1e-6,
+                                                        max_iter=4000, workspace=ws))
+        out[pre] = {"ms": ms, "gsas": N * J / (ms * 1e-3) / 1e9, "iters_max": int(it.max()),
+                    "iters_mean": float(it.float().mean()), "resid_max": float(res[0].max()),
+                    "resid_true_max": float(res[1].max()),
+                    "rel_error_vs_truth": float(torch.linalg.norm(xm - x)) / xn}
+    del ws
+    chunk, margin = 8192, 512
+    wss = torch.empty(ipfb.workspace_size(ipfb.geom(N, NTAP, chunk), ipfb.OP_ML_STREAM), dtype=torch.uint8,
+                      device=dev)
+    ms, (xs, its, rs) = timed(lambda: ipfb.ml_solve_stream(codes, scale, w, sig2, mask, x, chunk, margin,
+                                                           precond="wiener", tol=1e-6, max_iter=4000, workspace=wss))
+    ref = x[margin * N:(J - margin) * N]
+    out["overlap_save_wiener"] = {"chunk": chunk, "margin": margin, "ms": ms, "iters_max": int(its.max()),
+                                  "rel_error_vs_truth": float(torch.linalg.norm(xs - ref) / torch.linalg.norm(ref)),
+                                  "note": "solves each 8192-frame chunk as a periodic system; "
+                                          "the run's first and last 512 frames are not produced"}
+    del wss, x, codes, mask
     return out
 
 

@@ -17,11 +17,13 @@ quoted figures beside the measured ones.
 
 Every transform, inverse and solve runs in libipfb; torch only holds the arrays and
 forms the averages.  The default run is the paper's: 2048 x 65536 = 2^27 samples,
-delta(f) averaged over its 1024 re-channelized blocks.  A single ML solve holds up to
-8192 frames, so beyond that the ML reconstruction is the overlap-save solve
-(ipfb_ml_solve_stream: chunks of 8192 frames stepping by 8192 - 2 x 512, each solved
-with its own stretch of the mask, the prior and the Wiener start); the run's first
-and last 512 frames, which no chunk covers from both sides, keep the Wiener start.
+delta(f) averaged over its 1024 re-channelized blocks.  The ML reconstruction is one
+solve of the whole run's circulant system (up to 65536 frames; past the on-chip column
+run its CG vectors stay in HBM).  With ml_chunk set, it is the overlap-save solve
+instead (ipfb_ml_solve_stream: chunks of ml_chunk frames stepping by ml_chunk - 2
+ml_margin, each solved with its own stretch of the mask, the prior and the Wiener
+start; the run's first and last ml_margin frames, which no chunk covers from both
+sides, keep the Wiener start).
 """
 from __future__ import annotations
 
@@ -50,11 +52,8 @@ def _delta_stats(delta: np.ndarray, upfactor: int) -> dict:
             "median": float(np.median(interior))}
 
 
-ML_CHUNK, ML_MARGIN = 8192, 512
-
-
 def run(torch, dev, nframes: int = 65536, seed: int = 11, betas=(0.01, 0.03, 0.10), iters: int = 25,
-        prior_weights=("1", "1/sigma2")) -> dict:
+        prior_weights=("1", "1/sigma2"), ml_chunk: int | None = None, ml_margin: int = 512) -> dict:
     N, J = LBLOCK, nframes
     T = N * J
     x = synth.gaussian_stream_torch(T, seed, dev)
@@ -73,8 +72,8 @@ def run(torch, dev, nframes: int = 65536, seed: int = 11, betas=(0.01, 0.03, 0.1
     wd = w.double()
     ce = sum(wd[r][None, :] * torch.roll(e, -r, dims=0) for r in range(NTAP))
     sig2 = float(ce.var())
-    chunked = J > ML_CHUNK
-    g = ipfb.geom(N, NTAP, ML_CHUNK if chunked else J)
+    chunked = ml_chunk is not None and J > ml_chunk
+    g = ipfb.geom(N, NTAP, ml_chunk if chunked else J)
     ws = torch.empty(ipfb.workspace_size(g, ipfb.OP_ML_STREAM if chunked else ipfb.OP_ML), dtype=torch.uint8,
                      device=dev)
     for beta in betas:
@@ -84,8 +83,8 @@ def run(torch, dev, nframes: int = 65536, seed: int = 11, betas=(0.01, 0.03, 0.1
             lam = 1.0 if pw == "1" else 1.0 / sig2
             if chunked:
                 xm = recon["wiener"].clone()
-                ipfb.ml_solve_stream(codes, scale, w, sig2, mask, x, ML_CHUNK, ML_MARGIN, prior_weight=lam, tol=0.0,
-                                     max_iter=iters, x0=recon["wiener"], out=xm[ML_MARGIN * N:(J - ML_MARGIN) * N],
+                ipfb.ml_solve_stream(codes, scale, w, sig2, mask, x, ml_chunk, ml_margin, prior_weight=lam, tol=0.0,
+                                     max_iter=iters, x0=recon["wiener"], out=xm[ml_margin * N:(J - ml_margin) * N],
                                      workspace=ws)
             else:
                 xm, _, _ = ipfb.ml_solve(codes, scale, w, sig2, mask, x, prior_weight=lam, tol=0.0, max_iter=iters,
@@ -104,7 +103,8 @@ def run(torch, dev, nframes: int = 65536, seed: int = 11, betas=(0.01, 0.03, 0.1
            "phi2": phi2, "sigma2_d": sig2,
            "ml": f"every 4th frame of L central paths, Wiener start, {iters} CG steps; data term weight 1/sigma2_d, "
                  "prior weight 1 or 1/sigma2_d (the latter = unit weights on both terms)"
-                 + (f"; overlap-save solves of {ML_CHUNK} frames, {ML_MARGIN}-frame margins" if chunked else ""),
+                 + (f"; overlap-save solves of {ml_chunk} frames, {ml_margin}-frame margins" if chunked
+                    else f"; one solve of all {J} frames"),
            "paper": {"delta_channel_centre": "~1.1 % (-19 dB)", "wiener_max": "~10 %", "no_filter_max": "> 100 %",
                      "ml_beta_0.03_max": "< half of the Wiener maximum", "ml_beta_0.10_max": "~2 %",
                      "timestream_error": "~10 % for most frame samples"},
@@ -125,9 +125,12 @@ def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--nframes", type=int, default=65536)
     ap.add_argument("--seed", type=int, default=11)
+    ap.add_argument("--ml-chunk", type=int, default=None,
+                    help="overlap-save ML solves of this many frames instead of one solve of the run")
+    ap.add_argument("--ml-margin", type=int, default=512)
     args = ap.parse_args(argv)
     dev = torch.device("cuda", 0)
-    print(json.dumps(run(torch, dev, args.nframes, args.seed)))
+    print(json.dumps(run(torch, dev, args.nframes, args.seed, ml_chunk=args.ml_chunk, ml_margin=args.ml_margin)))
     return 0
 
 
