@@ -782,9 +782,11 @@ int ml_solve_learned(const ipfb_geom* g, const uint8_t* codes, const float* scal
 //   k2 (d in the residue layout), transpose of mask / prior / initial guess, right-hand
 //   side and r0, init, [K3 on z with r.z], control, WHILE { two CG iterations }, true
 //   residual and report, back to time order.
-// Each iteration is mlb_ap, mlb_xr, [K3 (ML gain, listed pairs, r.z)], mlb_ctl; the
+// Each iteration is mlb_ap, then K3 with the ML gain fused with the residual update
+// (listed pairs; r.r and r.z) or, without a preconditioner, mlb_xr, then mlb_ctl; the
 // two iterations of the body alternate the search-direction buffers, and the second
-// control sets the loop condition (a pair still listed and iterations left).
+// control sets the loop condition (a pair still listed and iterations left).  The
+// finish applies each pair's last step and writes the solution through Q.
 int ml_solve_big(const ipfb_geom* g, const uint8_t* codes, const float* scale, const float* window,
                  const MLParams& mp, const uint8_t* mask, const float* prior, float* x_inout, int* iters,
                  float* resid, void* ws, int C, int S, cudaStream_t st) {
@@ -802,9 +804,16 @@ int ml_solve_big(const ipfb_geom* g, const uint8_t* codes, const float* scale, c
   gp.inv_s2 = mp.inv_s2;
   gp.lam_m = b.lam_m;
   gp.rz_out = b.rzk;
+  // in the loop the transform also forms r -= alpha q on its way in
   MlGainParams gl = gp;
   gl.pair_list = b.list;
   gl.pair_count = b.ctl;
+  gl.r_io = b.R;
+  gl.q_in = b.Q;
+  gl.pq_part = b.part;
+  gl.nt = G.NT;
+  gl.ps = b.ps;
+  gl.rr_out = b.rrk;
   int rc;
   Stage t("k5_mlbig_solve", st);
   Capture c;
@@ -823,14 +832,17 @@ int ml_solve_big(const ipfb_geom* g, const uint8_t* codes, const float* scale, c
     cudaStream_t bs = c.body;
     for (int half = 0; half < 2; ++half) {
       CK(launch_mlb_ap(half, mp, G, b, bs), "k_mlb_ap");
-      CK(launch_mlb_xr(half ^ 1, mp, G, b, bs), "k_mlb_xr");
-      if (mp.precond == 1) CK(launch_k3_ml(C, S, b.Z, window, N, gl, bs), "k3_column_ml");
+      if (mp.precond == 1) {
+        CK(launch_k3_ml(C, S, b.Z, window, N, gl, bs), "k3_column_ml");
+      } else {
+        CK(launch_mlb_xr(mp, G, b, bs), "k_mlb_xr");
+      }
       CK(launch_mlb_ctl(0, half, h, mp, G, b, bs), "k_mlb_ctl");
     }
   }
   if ((rc = capture_end_body(c))) return rc;
   CK(launch_mlb_finish(mp, G, b, iters, resid, s), "k_mlb_finish");
-  CK(launch_pairs_to_time(b.X, x_inout, N, C, S, s), "k_pairs_to_time");
+  CK(launch_pairs_to_time(b.Q, x_inout, N, C, S, s), "k_pairs_to_time");
   if ((rc = capture_finish(c))) return rc;
   t.done();
   return IPFB_OK;

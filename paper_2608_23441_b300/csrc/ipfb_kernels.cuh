@@ -303,13 +303,43 @@ struct WienerGain {
     split_gain(a, b, ga, gb);
   }
   __device__ __forceinline__ static void finish(const GainParams&, int) {}
+  // step 1's forward local FFT: this CTA's run of the pair, global -> smem
+  template <int S, int T>
+  __device__ __forceinline__ static void load(float2* sm, int tid, float2* base, const GainParams&, int, size_t) {
+    block_fft<S, T, false>(sm, tid, GMem{base}, SPad{sm});
+  }
 };
 
-template <int NT>
+// First-pass accessor of the fused CG update: element i of the CTA's run is
+// r_i - alpha q_i, written back to r and added to the CTA's r.r (each element is read
+// once by the first pass)
+struct MlResidLoad {
+  float2* rp;
+  const float2* qp;
+  float aa, ab;
+  float* rr;
+  template <int R, int NB>
+  __device__ __forceinline__ int lbase(int b) const { return b; }
+  template <int R, int NB>
+  __device__ __forceinline__ float2 ld(int base, int r) const {
+    const int i = base + r * NB;
+    float2 v = rp[i];
+    const float2 q = __ldg(qp + i);
+    v.x = fmaf(-aa, q.x, v.x);
+    v.y = fmaf(-ab, q.y, v.y);
+    rp[i] = v;
+    rr[0] = fmaf(v.x, v.x, rr[0]);
+    rr[1] = fmaf(v.y, v.y, rr[1]);
+    return v;
+  }
+};
+
+template <int NT, bool FUSED>
 struct MlGain {
   // With the real gain g, z = M r has r.z = sum_k g(k) |R(k)|^2 (Parseval for the
   // unnormalised transform pair), accumulated here per column while the gains are applied
   float acc_a = 0.0f, acc_b = 0.0f;
+  float rr[2] = {0.0f, 0.0f};  // FUSED: the CTA's r.r of the updated residual
 
   // 1 / (|W|^2 inv_s2 + lam_m) / J from |W|^2; a preconditioner only needs a fixed
   // positive gain, so the fast division serves (denominators below 1e-30 give 0)
@@ -373,29 +403,67 @@ struct MlGain {
     (void)k;
     apply(a, b, ta, tb, e1, gp, p, self ? 0.5f : 1.0f);
   }
-  // the CTA's r.z of both columns to rz_out[2 slot + c] (FP32 within a warp, FP64 across)
+  // step 1.  FUSED: alpha = r.z / p.q per active column (the pair's per-tile p.q
+  // summed by one warp in a fixed order, FP64; the ratio in FP32), then the first pass
+  // forms r - alpha q on the fly
+  template <int S, int T>
+  __device__ __forceinline__ void load(float2* sm, int tid, float2* base, const MlGainParams& gp, int p,
+                                       size_t off) {
+    if constexpr (!FUSED) {
+      block_fft<S, T, false>(sm, tid, GMem{base}, SPad{sm});
+    } else {
+      __shared__ float al[2];
+      if (tid < 32) {
+        double a = 0.0, b = 0.0;
+        if (tid < gp.nt) {
+          const double* q = gp.pq_part + ((size_t)p * gp.nt + tid) * 8;
+          a = __ldcg(q);
+          b = __ldcg(q + 1);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (tid == 0) {
+          const int act = __ldcg(&gp.ps[p].act);
+          const double rz0 = __ldcg(&gp.ps[p].rz[0]), rz1 = __ldcg(&gp.ps[p].rz[1]);
+          al[0] = ((act & 1) && a != 0.0) ? (float)rz0 / (float)a : 0.0f;
+          al[1] = ((act & 2) && b != 0.0) ? (float)rz1 / (float)b : 0.0f;
+        }
+      }
+      __syncthreads();
+      block_fft<S, T, false>(sm, tid, MlResidLoad{gp.r_io + off, gp.q_in + off, al[0], al[1], rr}, SPad{sm});
+    }
+  }
+  // the CTA's r.z (and, FUSED, r.r) of both columns to rz_out / rr_out[2 slot + c]
+  // (FP32 within a warp, FP64 across)
   __device__ __forceinline__ void finish(const MlGainParams& gp, int slot) {
     if (!gp.rz_out) return;
-    __shared__ float red[2][32];
-    float a = acc_a, b = acc_b;
+    __shared__ float red[4][32];
+    float v[4] = {acc_a, acc_b, rr[0], rr[1]};
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      b += __shfl_xor_sync(0xffffffffu, b, o);
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
     }
     if ((threadIdx.x & 31) == 0) {
-      red[0][threadIdx.x >> 5] = a;
-      red[1][threadIdx.x >> 5] = b;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) red[k][threadIdx.x >> 5] = v[k];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double sa = 0.0, sb = 0.0;
+      double sum[4] = {0.0, 0.0, 0.0, 0.0};
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        sa += (double)red[0][w];
-        sb += (double)red[1][w];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sum[k] += (double)red[k][w];
       }
-      gp.rz_out[2 * slot] = sa;
-      gp.rz_out[2 * slot + 1] = sb;
+      gp.rz_out[2 * slot] = sum[0];
+      gp.rz_out[2 * slot + 1] = sum[1];
+      if constexpr (FUSED) {
+        gp.rr_out[2 * slot] = sum[2];
+        gp.rr_out[2 * slot + 1] = sum[3];
+      }
     }
   }
 };
@@ -428,7 +496,8 @@ __device__ __forceinline__ void k3_pair(float2* __restrict__ d2, const float* __
   }
 
   // 1. forward local FFT: global -> smem
-  block_fft<S, T, false>(sm, tid, GMem{base}, SPad{sm});
+  GAIN gn;
+  gn.template load<S, T>(sm, tid, base, gp, p, ((size_t)p * C + r) * S);
   if constexpr (C > 1) {
     cg::this_cluster().sync();
   } else {
@@ -444,7 +513,6 @@ __device__ __forceinline__ void k3_pair(float2* __restrict__ d2, const float* __
   };
 
   // 2-4. tasks: t = 0 (kb = 0), t = S/2 (kb = S/2), else the pair (t, S - t)
-  GAIN gn;
   for (int t = r * T + tid; t <= S / 2; t += C * T) {
     const bool pairtask = (t != 0) && (2 * t != S);
     const int kb0 = t, kb1 = S - t;
@@ -550,11 +618,13 @@ k3_column_wiener(float2* __restrict__ d2, const float* __restrict__ window, int 
   k3_pair<C, S, T, NT, WienerGain<NT>, GainParams>(d2, window, N, gp, blockIdx.x / C);
 }
 
-// The ML solve's preconditioner.  With a pair list (the solve's active pairs, ascending)
-// cluster c transforms pair pair_list[c] if c < *pair_count and exits otherwise; every
-// CTA of a cluster takes the same branch, before any cluster barrier.  (A persistent
-// loop over the list keeps the transform's state live across trips and spills.)
-template <int C, int S, int T, int NT>
+// The ML solve's preconditioner (FUSED: with the residual update r -= alpha q in its
+// load, so the transform's input is the new residual).  With a pair list (the solve's
+// active pairs, ascending) cluster c transforms pair pair_list[c] if c < *pair_count
+// and exits otherwise; every CTA of a cluster takes the same branch, before any cluster
+// barrier.  (A persistent loop over the list keeps the transform's state live across
+// trips and spills.)
+template <int C, int S, int T, int NT, bool FUSED>
 __global__ void __launch_bounds__(T, (S >= 4096 ? 2 : 1))
 k3_column_ml(float2* __restrict__ d2, const float* __restrict__ window, int N, MlGainParams gp) {
   int p = blockIdx.x / C;
@@ -562,7 +632,7 @@ k3_column_ml(float2* __restrict__ d2, const float* __restrict__ window, int N, M
     if (p >= __ldg(gp.pair_count)) return;
     p = __ldg(gp.pair_list + p);
   }
-  k3_pair<C, S, T, NT, MlGain<NT>, MlGainParams>(d2, window, N, gp, p);
+  k3_pair<C, S, T, NT, MlGain<NT, FUSED>, MlGainParams>(d2, window, N, gp, p);
 }
 
 // ----------------------------------------------------------------------------

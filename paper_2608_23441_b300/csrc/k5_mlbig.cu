@@ -8,10 +8,14 @@
 // so that the Wiener preconditioner
 //     z = F^dagger[ F r / (|W_n|^2 / sigma^2 + lam mbar_n) ]
 // is the cluster transform K3 with its ML gain.  One CG iteration is
-//     mlb_ap   p' = z + beta p, q = A p'            tiles with a stencil halo
-//     mlb_xr   x += alpha p', r -= alpha q, z = r   alpha from the tiles' p'.q
-//     k3       z = M_W z and r.z                    listed pairs only; r.z by Parseval
-//     mlb_ctl  stopping test, beta, the next list of active pairs
+//     mlb_ap   x += alpha_prev p, p' = z + beta p, q = A p'    tiles with a stencil halo
+//     k3       r -= alpha q (alpha from the tiles' p'.q), r.r,  listed pairs only;
+//              z = M_W r, r.z                                    r.z by Parseval
+//     mlb_ctl  stopping test, beta, alpha, the next list of active pairs
+// (without a preconditioner mlb_xr forms alpha, r -= alpha q and r.r, and z = r).
+// The step x += alpha p of an iteration is applied by the next iteration's mlb_ap,
+// which reads that p anyway; a pair's last step is applied when the solution is
+// written out.
 // A pair leaves the list once both its columns have converged, so the work follows the
 // columns still iterating.  p' goes to the other of two buffers: neighbouring tiles read
 // the old p in their halos.  Each tile writes its partial sums to a slot of its own and a
@@ -323,7 +327,8 @@ __global__ void __launch_bounds__(kT) k_mlb_init(MLParams mp, MlbGeom g, MlbBufs
 }
 
 // ---- iteration ----------------------------------------------------------------------
-// p' = z + beta p (beta = 0: p' = z, the old p unread), q = A p'; slots [0,1] p'.q
+// x += apend p (the previous iteration's step), p' = z + beta p (beta = 0: p' = z, the old
+// p unread), q = A p'; slots [0,1] p'.q
 template <int RMAX>
 __global__ void __launch_bounds__(kT, RMAX <= 3 ? 4 : 2)
 k_mlb_ap(const float2* __restrict__ Po, float2* __restrict__ Pn, MLParams mp, MlbGeom g, MlbBufs b) {
@@ -336,7 +341,8 @@ k_mlb_ap(const float2* __restrict__ Po, float2* __restrict__ Pn, MLParams mp, Ml
     const int li = w / g.NT, t = w - li * g.NT;
     const int p = __ldg(b.list + li);
     const float ba = b.ps[p].beta[0], bb = b.ps[p].beta[1];
-    const bool rd = ba != 0.0f || bb != 0.0f;
+    const float xa = b.ps[p].apend[0], xb = b.ps[p].apend[1];
+    const bool rd = ba != 0.0f || bb != 0.0f, xs = xa != 0.0f || xb != 0.0f;
     float2 a[RMAX + 1];
     load_coef<RMAX>(b, p, a);
     uint8_t mb[kEPT];
@@ -366,6 +372,14 @@ k_mlb_ap(const float2* __restrict__ Po, float2* __restrict__ Pn, MLParams mp, Ml
                                      fmaf((bits & 2) ? mp.lam : 0.0f, pv.y, ap.y));
         Pn[v] = pv;
         b.Q[v] = q;
+        if (xs) {
+          // the previous iteration's step (its p is the old direction, just read through L2)
+          const float2 po = Po[v];
+          float2 x = b.X[v];
+          x.x = fmaf(xa, po.x, x.x);
+          x.y = fmaf(xb, po.y, x.y);
+          b.X[v] = x;
+        }
         acc[0] = fmaf(pv.x, q.x, acc[0]);
         acc[1] = fmaf(pv.y, q.y, acc[1]);
       }
@@ -393,30 +407,25 @@ __device__ __forceinline__ int off4(const MlbGeom& g, int t, int e) {
 }
 constexpr int kE4 = kEPT / 2;  // float4 per thread per tile, at most
 
-// alpha = r.z / p'.q per active column; x += alpha p', r -= alpha q, [z = r]; slots [4,5] r.r
-__global__ void __launch_bounds__(kT, 2)
-k_mlb_xr(float2* __restrict__ Pn, MLParams mp, MlbGeom g, MlbBufs b) {
+// without a preconditioner: alpha = r.r / p'.q per active column, r -= alpha q;
+// slots [4,5] r.r (z is r itself)
+__global__ void __launch_bounds__(kT, 4)
+k_mlb_xr(MLParams mp, MlbGeom g, MlbBufs b) {
   __shared__ double red[kW * 2];
   __shared__ float al[2];
   const int cnt = b.ctl[0];
-  const bool zcopy = mp.precond == 1;
   for (int w = blockIdx.x; w < cnt * g.NT; w += gridDim.x) {
     const int li = w / g.NT, t = w - li * g.NT;
     const int p = __ldg(b.list + li);
-    const float4* __restrict__ P4 = pair4(Pn, g, p);
     const float4* __restrict__ Q4 = pair4(b.Q, g, p);
-    float4* __restrict__ X4 = pair4(b.X, g, p);
     float4* __restrict__ R4 = pair4(b.R, g, p);
-    float4* __restrict__ Z4 = pair4(b.Z, g, p);
     int o[kE4];
-    float4 pv[kE4], q[kE4], xv[kE4], rv[kE4];
+    float4 q[kE4], rv[kE4];
 #pragma unroll
     for (int e = 0; e < kE4; ++e) {
       o[e] = off4(g, t, e);
       if (o[e] >= 0) {
-        pv[e] = P4[o[e]];
         q[e] = Q4[o[e]];
-        xv[e] = X4[o[e]];
         rv[e] = R4[o[e]];
       }
     }
@@ -436,18 +445,12 @@ k_mlb_xr(float2* __restrict__ Pn, MLParams mp, MlbGeom g, MlbBufs b) {
 #pragma unroll
     for (int e = 0; e < kE4; ++e) {
       if (o[e] >= 0) {
-        float4 x = xv[e], r = rv[e];
-        x.x = fmaf(aa, pv[e].x, x.x);
-        x.y = fmaf(ab, pv[e].y, x.y);
-        x.z = fmaf(aa, pv[e].z, x.z);
-        x.w = fmaf(ab, pv[e].w, x.w);
+        float4 r = rv[e];
         r.x = fmaf(-aa, q[e].x, r.x);
         r.y = fmaf(-ab, q[e].y, r.y);
         r.z = fmaf(-aa, q[e].z, r.z);
         r.w = fmaf(-ab, q[e].w, r.w);
-        X4[o[e]] = x;
         R4[o[e]] = r;
-        if (zcopy) Z4[o[e]] = r;
         acc[0] = fmaf(r.x, r.x, fmaf(r.z, r.z, acc[0]));
         acc[1] = fmaf(r.y, r.y, fmaf(r.w, r.w, acc[1]));
       }
@@ -476,8 +479,15 @@ k_mlb_ctl(int first, int set_cond, cudaGraphConditionalHandle h, MLParams mp, Ml
   if (cnt0 > 0 && p < P) {
     const int act0 = first ? 3 : b.ps[p].act;
     if (act0) {
-      double rz0, rz1, rr0, rr1;
-      pair_sums(b.part, p, g.NT, 4, rr0, rr1);
+      double rz0, rz1, rr0, rr1, pq0 = 0.0, pq1 = 0.0;
+      if (mp.precond == 1 && !first) {
+        // the fused update's per-CTA r.r, in CTA order
+        const double* q = b.rrk + (size_t)p * g.C * 2;
+        rr0 = warp_sum(lane < g.C ? __ldcg(q + 2 * lane) : 0.0);
+        rr1 = warp_sum(lane < g.C ? __ldcg(q + 2 * lane + 1) : 0.0);
+      } else {
+        pair_sums(b.part, p, g.NT, 4, rr0, rr1);
+      }
       if (mp.precond == 1) {
         // the preconditioner's per-CTA r.z, in CTA order
         const double* q = b.rzk + (size_t)p * g.C * 2;
@@ -487,9 +497,18 @@ k_mlb_ctl(int first, int set_cond, cudaGraphConditionalHandle h, MLParams mp, Ml
         rz0 = rr0;
         rz1 = rr1;
       }
+      if (!first) pair_sums(b.part, p, g.NT, 0, pq0, pq1);
       if (lane == 0) {
         MlbPair s = b.ps[p];
-        const double rz[2] = {rz0, rz1}, rr[2] = {rr0, rr1};
+        const double rz[2] = {rz0, rz1}, rr[2] = {rr0, rr1}, pq[2] = {pq0, pq1};
+        // the step this iteration took (the same alpha as the update kernels formed)
+        // is applied to x by the next stencil pass, or when the solution is written
+        if (!first) {
+#pragma unroll
+          for (int c = 0; c < 2; ++c)
+            s.apend[c] = ((act0 & (1 << c)) && pq[c] != 0.0) ? (float)s.rz[c] / (float)pq[c] : 0.0f;
+          s.pbuf = (b.ctl[1] + 1) & 1;
+        }
         int nac = 0;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -542,7 +561,8 @@ k_mlb_ctl(int first, int set_cond, cudaGraphConditionalHandle h, MLParams mp, Ml
   }
 }
 
-// true residual b - A x per tile: slots [6,7]
+// x = X + apend p (each pair's last step, p in Pv[pbuf]) written to Q; its true
+// residual b - A x per tile: slots [6,7]
 template <int RMAX>
 __global__ void __launch_bounds__(kT, RMAX <= 3 ? 4 : 2) k_mlb_true_resid(MLParams mp, MlbGeom g, MlbBufs b) {
   __shared__ float2 sv[kSv];
@@ -564,7 +584,17 @@ __global__ void __launch_bounds__(kT, RMAX <= 3 ? 4 : 2) k_mlb_true_resid(MLPara
         mb[e] = b.mk[v];
       }
     }
-    load_halo(sv, g, p, t, h, [&](size_t i) { return b.X[i]; });
+    const float xa = b.ps[p].apend[0], xb = b.ps[p].apend[1];
+    const float2* __restrict__ Pl = (b.ps[p].pbuf & 1) ? b.Pv[1] : b.Pv[0];
+    load_halo(sv, g, p, t, h, [&](size_t i) {
+      float2 x = b.X[i];
+      if (xa != 0.0f || xb != 0.0f) {
+        const float2 pv = Pl[i];
+        x.x = fmaf(xa, pv.x, x.x);
+        x.y = fmaf(xb, pv.y, x.y);
+      }
+      return x;
+    });
     __syncthreads();
     float acc[2] = {0.0f, 0.0f};
 #pragma unroll
@@ -573,6 +603,7 @@ __global__ void __launch_bounds__(kT, RMAX <= 3 ? 4 : 2) k_mlb_true_resid(MLPara
       if (i < items) {
         const int r = i >> g.logTM, m = i & (g.TM - 1);
         const float2 xv = sv[r * TMP + h + m];
+        b.Q[vidx(g, p, 0, 0) + loc(g, t, i)] = xv;
         const float2 ax = stencil<RMAX>(sv, TMP, h, g.logC, r, m, a);
         const uint8_t bits = mb[e];
         const float2 bv = bq[e];
@@ -648,7 +679,7 @@ size_t mlb_workspace(int N, int C, int S) {
   const MlbGeom g = mlb_geom(N, C, S);
   const size_t P = (size_t)N / 2, J = (size_t)C * S;
   return 7 * al256(P * J * sizeof(float2)) + al256(P * J) + al256(P * 16 * sizeof(float2)) +
-         al256(P * g.NT * 8 * sizeof(double)) + al256(P * 16 * sizeof(double)) + al256(P * sizeof(MlbPair)) +
+         al256(P * g.NT * 8 * sizeof(double)) + 2 * al256(P * 16 * sizeof(double)) + al256(P * sizeof(MlbPair)) +
          al256((size_t)N * sizeof(float)) + al256(P * sizeof(int)) + al256(16 * sizeof(int));
 }
 
@@ -669,6 +700,8 @@ MlbBufs mlb_carve(void* ws, int N, int C, int S) {
   b.part = reinterpret_cast<double*>(w);
   w += al256(P * g.NT * 8 * sizeof(double));
   b.rzk = reinterpret_cast<double*>(w);
+  w += al256(P * 16 * sizeof(double));
+  b.rrk = reinterpret_cast<double*>(w);
   w += al256(P * 16 * sizeof(double));
   b.ps = reinterpret_cast<MlbPair*>(w);
   w += al256(P * sizeof(MlbPair));
@@ -711,8 +744,8 @@ cudaError_t launch_mlb_ap(int src, const MLParams& mp, const MlbGeom& g, const M
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlb_xr(int dst, const MLParams& mp, const MlbGeom& g, const MlbBufs& b, cudaStream_t st) {
-  k_mlb_xr<<<persistent_grid((const void*)k_mlb_xr), kT, 0, st>>>(b.Pv[dst], mp, g, b);
+cudaError_t launch_mlb_xr(const MLParams& mp, const MlbGeom& g, const MlbBufs& b, cudaStream_t st) {
+  k_mlb_xr<<<persistent_grid((const void*)k_mlb_xr), kT, 0, st>>>(mp, g, b);
   return cudaGetLastError();
 }
 

@@ -25,12 +25,23 @@ struct GainParams {
 // K3 with the ML solve's preconditioner gain (k3_column_ml): 1 / sigma^2, lam times the
 // mask fraction of each column, and an optional list of the pairs to transform
 // (*pair_count entries)
+struct MlbPair;
 struct MlGainParams : GainParams {
   float inv_s2 = 0.0f;
   const float* lam_m = nullptr;
   const int* pair_list = nullptr;
   const int* pair_count = nullptr;
   double* rz_out = nullptr;  // [P][C][2]: each CTA's r.z of both columns (Parseval), or nullptr
+  // the CG residual update fused into the transform's load (r_io != nullptr): alpha of
+  // each active column from the stencil's per-tile p.q (pq_part [P][nt][8], slots 0, 1)
+  // and the pair state, r = r - alpha q written back to r_io, and each CTA's r.r to
+  // rr_out [P][C][2]; the transform then runs on r and writes z to d2
+  float2* r_io = nullptr;
+  const float2* q_in = nullptr;
+  const double* pq_part = nullptr;
+  int nt = 0;
+  const MlbPair* ps = nullptr;
+  double* rr_out = nullptr;
 };
 
 struct UpchanSrc {
@@ -56,7 +67,8 @@ cudaError_t launch_quantize(int H, long long nspec, const float2* spec, const fl
 cudaError_t launch_k2(int H, const uint8_t* codes, const float* scale, float2* d2, int C, int S,
                       cudaStream_t st);
 cudaError_t launch_k3(int C, int S, float2* d2, const float* window, int N, GainParams gp, cudaStream_t st);
-// K3 with the ML preconditioner gain on the residue splits C = 2, 4, 8 with S = 512 or 8192
+// K3 with the ML preconditioner gain on the residue splits C = 2, 4, 8 with S = 512 or
+// 8192; fused with the CG residual update when gp.r_io is set
 cudaError_t launch_k3_ml(int C, int S, float2* z2, const float* window, int N, const MlGainParams& gp,
                          cudaStream_t st);
 cudaError_t launch_pairs_to_time(const float2* d2, float* x, int N, int C, int S, cudaStream_t st);
@@ -94,13 +106,14 @@ cudaError_t launch_k4b(const float2* W, int N, long long nblocks, float2* out, c
 // Every vector is [P C][S] in the column transform's residue layout: frame j = C m + r
 // of pair p at v[(p C + r) S + m], columns 2p and 2p+1 as the real and imaginary parts.
 struct MlbPair {
-  double rz[2];  // r.z of each column's current residual
-  float bn[2];   // |b| (1 where b = 0)
+  double rz[2];    // r.z of each column's current residual
+  float bn[2];     // |b| (1 where b = 0)
   float beta[2];
-  float rel[2];  // recursive relative residual at the last test
-  int act;       // bit c: column 2p + c still iterating
+  float rel[2];    // recursive relative residual at the last test
+  float apend[2];  // alpha of the last iteration, whose x += alpha p is still to be applied
+  int act;         // bit c: column 2p + c still iterating
   int it[2];
-  int pad;
+  int pbuf;        // the search-direction buffer that holds that p
 };
 struct MlbBufs {
   float2 *B, *X, *R, *Q, *Z;  // Q holds d until the right-hand side is built; Z = R without a preconditioner
@@ -109,6 +122,7 @@ struct MlbBufs {
   float2* acoef;              // [P][16] stencil taps a_s / sigma^2 of both columns
   double* part;               // [P][NT][8] per-tile partial sums
   double* rzk;                // [P][8][2] r.z of both columns from each CTA of the preconditioner
+  double* rrk;                // [P][8][2] r.r of both columns from each CTA of the fused update
   MlbPair* ps;                // [P]
   float* lam_m;               // [N] lam * mask fraction of each column
   int* list;                  // [P] active pairs, ascending
@@ -129,14 +143,16 @@ cudaError_t launch_mlb_rhs(const float* window, const MLParams& mp, const MlbGeo
                            cudaStream_t st);
 // |b|, lam mbar, all pairs listed, counters cleared
 cudaError_t launch_mlb_init(const MLParams& mp, const MlbGeom& g, const MlbBufs& b, cudaStream_t st);
-// p' = z + beta p (Pv[src] -> Pv[src ^ 1]), q = A p', per-tile p'.q (listed pairs)
+// x += apend p (the previous iteration's step, p in Pv[src]), p' = z + beta p
+// (Pv[src] -> Pv[src ^ 1]), q = A p', per-tile p'.q (listed pairs)
 cudaError_t launch_mlb_ap(int src, const MLParams& mp, const MlbGeom& g, const MlbBufs& b, cudaStream_t st);
-// x += alpha p', r -= alpha q, [Z = r], per-tile r.r (listed pairs)
-cudaError_t launch_mlb_xr(int dst, const MLParams& mp, const MlbGeom& g, const MlbBufs& b, cudaStream_t st);
+// without a preconditioner: alpha, r -= alpha q, per-tile r.r (listed pairs)
+cudaError_t launch_mlb_xr(const MLParams& mp, const MlbGeom& g, const MlbBufs& b, cudaStream_t st);
 // stopping test, beta, iteration counts, the next list; sets h (if set_cond) to "a pair is listed"
 cudaError_t launch_mlb_ctl(int first, int set_cond, cudaGraphConditionalHandle h, const MLParams& mp,
                            const MlbGeom& g, const MlbBufs& b, cudaStream_t st);
-// true residual b - A x, iterations and residuals out
+// x = X + apend p (each pair's last step) written to Q, its true residual b - A x,
+// iterations and residuals out
 cudaError_t launch_mlb_finish(const MLParams& mp, const MlbGeom& g, const MlbBufs& b, int* iters, float* resid,
                               cudaStream_t st);
 
