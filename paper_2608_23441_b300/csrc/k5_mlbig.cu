@@ -535,9 +535,15 @@ k_mlb_ctl(int first, int set_cond, cudaGraphConditionalHandle h, MLParams mp, Ml
   int total = 0;
   if (cnt0 > 0) {
     // contiguous chunks per thread, an exclusive scan of their counts, then the list
-    const int per = (P + kT - 1) / kT, lo = threadIdx.x * per, hi = min(P, lo + per);
-    int n = 0;
-    for (int q = lo; q < hi; ++q) n += __ldcg(&b.ps[q].act) != 0;
+    // (P <= 8192 = 32 kT: a thread's flags fit one 32-bit mask, loaded all at once)
+    const int per = (P + kT - 1) / kT, lo = threadIdx.x * per;
+    unsigned bits = 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const int q = lo + k;
+      if (k < per && q < P && __ldcg(&b.ps[q].act) != 0) bits |= 1u << k;
+    }
+    const int n = __popc(bits);
     s_scan[threadIdx.x] = n;
     __syncthreads();
     for (int o = 1; o < kT; o <<= 1) {
@@ -548,8 +554,7 @@ k_mlb_ctl(int first, int set_cond, cudaGraphConditionalHandle h, MLParams mp, Ml
     }
     total = s_scan[kT - 1];
     int pos = s_scan[threadIdx.x] - n;
-    for (int q = lo; q < hi; ++q)
-      if (__ldcg(&b.ps[q].act) != 0) b.list[pos++] = q;
+    for (; bits; bits &= bits - 1) b.list[pos++] = lo + __ffs(bits) - 1;
   }
   if (threadIdx.x == 0) {
     const int it = b.ctl[1] + ((first || cnt0 == 0) ? 0 : 1);
