@@ -206,14 +206,15 @@ def test_mlbig_stream_chunks_beyond_the_on_chip_run(short_run):
     assert int(it.max()) == 25
 
 
-@pytest.mark.parametrize("precond", ["wiener", "none"])
-def test_mlbig_paper_size_sampled_columns(precond):
-    """The paper's size: lblock 2048, ntap 4, 65536 frames (2^27 samples), 10 % of the
-    samples saved as 256 chunks; random 4-bit codes and channel steps, a Gaussian prior
-    of the data's scale, sigma^2 = 0.0141 var(d).  Every column's own stopping test and
-    true residual; sampled columns (the edges, the worst-conditioned column N/2 and its
-    neighbours, seeded ones) against the oracle's column-wise solve."""
-    N, J = 2048, 65536
+@pytest.mark.parametrize("N,precond", [(2048, "wiener"), (2048, "none"), (4096, "wiener")])
+def test_mlbig_paper_size_sampled_columns(N, precond):
+    """The paper's size (lblock 2048, ntap 4, 65536 frames: 2^27 samples) and the
+    benchmark's pipeline geometry (lblock 4096: 2^28 samples), 10 % of the samples saved
+    as 256 chunks; random 4-bit codes and channel steps, a Gaussian prior of the data's
+    scale, sigma^2 = 0.0141 var(d).  Every column's own stopping test and true residual;
+    sampled columns (the edges, the worst-conditioned column N/2 and its neighbours,
+    seeded ones) against the oracle's column-wise solve."""
+    J = 65536
     ipfb.set_max_column_run(8192)
     dev = torch.device("cuda", 0)
     codes = synth.random_code_bytes(J, N // 2, 71)
