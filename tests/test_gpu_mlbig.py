@@ -206,6 +206,53 @@ def test_mlbig_stream_chunks_beyond_the_on_chip_run(short_run):
     assert int(it.max()) == 25
 
 
+def _check_sampled_columns(dcols, w64, sig2, M, P, G, it_cols, tol, precond):
+    """Sampled columns of a long solve against the oracle's column-wise solve.
+    In FP32 the true residual exceeds the recursive one (the stopping test) by the
+    rounding gap of finite-precision CG, about k u ||A|| max_j ||x_j|| after k steps
+    (Greenbaum 1997), u = 2^-24, ||A|| <= max_k |W_n(k)|^2 / sigma^2 + lam; near column
+    N/2 that floor is ~1e-6 of ||b|| at 65536 frames.  The distance to the exact solution
+    is bounded by ||A^-1|| ||b - A x||, ||A^-1|| from inverse iteration with the oracle's
+    PCG (a lower estimate, hence the factor 2)."""
+    J = dcols.shape[0]
+    X, _, _ = oml.ml_solve_d(dcols, w64, sig2, M, P, 1.0, "wiener", 1e-11, 5000)
+    B = oml.rhs(w64, dcols, sig2, M, P, 1.0)
+    bn, xn = np.linalg.norm(B, axis=0), np.linalg.norm(X, axis=0)
+    tr = oml.true_relative_residual(dcols, w64, sig2, M, P, 1.0, G)
+    Anorm = (np.abs(oipfb.eigenvalues(w64, J)) ** 2).max(axis=0) / sig2 + 1.0
+    gap = 2.0 * np.maximum(it_cols, 1) * 2.0 ** -24 * Anorm * xn / bn
+    assert np.all(tr <= tol + gap), (tr, gap)
+    V = np.random.default_rng(76).standard_normal(dcols.shape)
+    for _ in range(8):
+        V /= np.linalg.norm(V, axis=0)
+        V = oml.cg(lambda U: oml.normal_operator_fft(w64, U, sig2, M, 1.0), V, np.zeros_like(V), 1e-10, 5000,
+                   lambda R: oml.wiener_precond(w64, R, sig2, M, 1.0))[0]
+    inv_norm = np.linalg.norm(V, axis=0)
+    rel = np.linalg.norm(G - X, axis=0) / xn
+    assert np.all(rel <= 2.0 * inv_norm * tr * bn / xn + 1e-6), (rel, inv_norm * tr * bn / xn)
+    _, oit, _ = oml.ml_solve_d(dcols, w64, sig2, M, P, 1.0, precond, tol, 20000)
+    assert np.all(np.abs(it_cols - oit) <= np.maximum(3, 0.15 * oit)), (it_cols, oit)
+    return rel
+
+
+@pytest.mark.parametrize("J", [16384, 32768])
+def test_mlbig_two_and_four_cta_runs_of_8192(J):
+    """16384 and 32768 frames: residue splits C = 2, 4 with S = 8192 (the default on-chip
+    run), 8 and 16 tiles per pair; lblock 256, 10 % prior; sampled columns against the
+    oracle, the stopping test and true residuals on every column."""
+    N = 256
+    x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 26, nchunks=32)
+    ipfb.set_max_column_run(8192)
+    xg, it, res = _solve(codes, scale, w, sig2, mask, prior, precond="wiener", tol=1e-6, max_iter=500)
+    assert np.all(res[0] <= 1e-6) and np.all(res[1] <= 1e-5)
+    cols = np.array([0, 1, N // 2 - 1, N // 2, N // 2 + 1, N - 1, 77, 190])
+    M = mask.reshape(J, N)[:, cols].astype(np.float64)
+    P = prior.reshape(J, N)[:, cols].astype(np.float64)
+    G = xg.reshape(J, N)[:, cols]
+    rel = _check_sampled_columns(d[:, cols], w[:, cols], sig2, M, P, G, it[cols], 1e-6, "wiener")
+    assert np.all(rel[[0, 1, 5, 6, 7]] < 1e-5), rel   # the well-conditioned columns
+
+
 @pytest.mark.parametrize("N,precond", [(2048, "wiener"), (2048, "none"), (4096, "wiener")])
 def test_mlbig_paper_size_sampled_columns(N, precond):
     """The paper's size (lblock 2048, ntap 4, 65536 frames: 2^27 samples) and the
@@ -240,27 +287,5 @@ def test_mlbig_paper_size_sampled_columns(N, precond):
     P = prior.reshape(J, N)[:, cols].double().cpu().numpy()
     w64 = w.astype(np.float64)[:, cols]
     G = xg.reshape(J, N)[:, cols].double().cpu().numpy()
-    X, _, _ = oml.ml_solve_d(dcols, w64, sig2, M, P, 1.0, "wiener", 1e-11, 5000)
-    B = oml.rhs(w64, dcols, sig2, M, P, 1.0)
-    bn, xn = np.linalg.norm(B, axis=0), np.linalg.norm(X, axis=0)
-    # In FP32 the true residual exceeds the recursive one (the stopping test) by the
-    # rounding gap of finite-precision CG, about k u ||A|| max_j ||x_j|| after k steps
-    # (Greenbaum 1997), u = 2^-24, ||A|| <= max_k |W_n(k)|^2 / sigma^2 + lam.  Near
-    # column N/2 that floor is ~1e-6 of ||b|| (x* itself rounded to FP32 leaves ~2e-7).
-    tr = oml.true_relative_residual(dcols, w64, sig2, M, P, 1.0, G)
-    Anorm = (np.abs(oipfb.eigenvalues(w64, J)) ** 2).max(axis=0) / sig2 + 1.0
-    gap = 2.0 * np.maximum(it[cols], 1) * 2.0 ** -24 * Anorm * xn / bn
-    assert np.all(tr <= tol + gap), (tr, gap)
-    # the distance to the exact solution is bounded by ||A^-1|| ||b - A x||; ||A^-1|| from
-    # inverse iteration with the oracle's PCG (a lower estimate, hence the factor 2)
-    V = np.random.default_rng(76).standard_normal(dcols.shape)
-    for _ in range(8):
-        V /= np.linalg.norm(V, axis=0)
-        V = oml.cg(lambda U: oml.normal_operator_fft(w64, U, sig2, M, 1.0), V, np.zeros_like(V), 1e-10, 5000,
-                   lambda R: oml.wiener_precond(w64, R, sig2, M, 1.0))[0]
-    inv_norm = np.linalg.norm(V, axis=0)
-    rel = np.linalg.norm(G - X, axis=0) / xn
-    assert np.all(rel <= 2.0 * inv_norm * tr * bn / xn + 1e-6), (rel, inv_norm * tr * bn / xn)
+    rel = _check_sampled_columns(dcols, w64, sig2, M, P, G, it[cols], tol, precond)
     assert np.all(rel[[0, 1, 5]] < 1e-5), rel   # the edge columns are well conditioned
-    _, oit, _ = oml.ml_solve_d(dcols, w64, sig2, M, P, 1.0, precond, tol, 20000)
-    assert np.all(np.abs(it[cols] - oit) <= np.maximum(3, 0.15 * oit)), (it[cols], oit)
