@@ -206,6 +206,37 @@ def test_mlbig_stream_chunks_beyond_the_on_chip_run(short_run):
     assert int(it.max()) == 25
 
 
+@pytest.mark.parametrize("run,J", [(512, 2048), (8192, 16384)])
+def test_mlbig_recorded_inside_a_callers_graph(run, J):
+    """The solve neither synchronises nor reads anything back: recorded inside the
+    caller's torch.cuda.graph (its WHILE node and kernels join the capture) and
+    replayed, it gives the eager answer bit for bit (the sums are fixed-order)."""
+    N = 64
+    ipfb.set_max_column_run(run)
+    try:
+        x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 27)
+        args = (cuda(codes), cuda(scale), cuda(w.astype(np.float32)), sig2, cuda(mask), cuda(prior))
+        ws = torch.empty(ipfb.workspace_size(ipfb.geom(N, 4, J), ipfb.OP_ML), dtype=torch.uint8, device="cuda")
+        for precond in ("wiener", "none"):
+            xe, ite, re = ipfb.ml_solve(*args, precond=precond, tol=1e-6, max_iter=3000, workspace=ws)
+            xe, ite, re = xe.clone(), ite.clone(), re.clone()
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                with torch.cuda.graph(graph, stream=side):
+                    xg, itg, rg = ipfb.ml_solve(*args, precond=precond, tol=1e-6, max_iter=3000, workspace=ws)
+            torch.cuda.current_stream().wait_stream(side)
+            for _ in range(2):
+                xg.zero_()
+                graph.replay()
+                torch.cuda.synchronize()
+                assert torch.equal(xg, xe) and torch.equal(itg, ite) and torch.equal(rg, re), precond
+    finally:
+        ipfb.set_max_column_run(8192)
+
+
 def _check_sampled_columns(dcols, w64, sig2, M, P, G, it_cols, tol, precond):
     """Sampled columns of a long solve against the oracle's column-wise solve.
     In FP32 the true residual exceeds the recursive one (the stopping test) by the
