@@ -922,6 +922,28 @@ def run_profile_case(lblock: int, nframes: int, reps: int):
     return 0
 
 
+def run_profile_ml_long(lblock: int, nframes: int, reps: int):
+    """A smaller case of the long-column ML solve for ncu (whole-graph captures): the
+    run_ml_long instance at lblock x nframes, `reps` Wiener-PCG solves to 1e-6."""
+    import torch
+    from paper_2608_23441_b300 import ipfb, synth
+    dev = torch.device("cuda", 0)
+    N, J = lblock, nframes
+    x = synth.gaussian_stream_torch(N * J, 11, dev)
+    w = torch.from_numpy(ipfb.sinc_hamming_window(N, NTAP)).to(dev)
+    codes, scale, _ = ipfb.pfb_forward(x, w)
+    starts, L = synth.prior_chunks(N * J, 256, 0.1, 11)
+    mask = torch.from_numpy(synth.mask_from_chunks(N * J, starts, L)).to(dev)
+    ws = torch.empty(ipfb.workspace_size(ipfb.geom(N, NTAP, J), ipfb.OP_ML), dtype=torch.uint8, device=dev)
+    for _ in range(reps):
+        xm, it, res = ipfb.ml_solve(codes, scale, w, 0.0114, mask, x, precond="wiener", tol=1e-6, max_iter=4000,
+                                    workspace=ws)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_ml_long": {"lblock": N, "nframes": J, "reps": reps, "iters_max": int(it.max()),
+                                          "iters_sum": int(it.sum())}}))
+    return 0
+
+
 def run_profile_batched(nstreams: int):
     """The batched-streams configuration (first `nstreams` streams of the seeded
     256-stream recipe) planned with the default variants and run once, for ncu
@@ -975,6 +997,8 @@ def main():
                     help="skip training the learned preconditioner and its ML timing")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-streams timing")
     ap.add_argument("--no-cufft", action="store_true", help="skip the torch.fft (cuFFT) comparison")
+    ap.add_argument("--profile-ml-long", nargs=3, type=int, metavar=("LBLOCK", "NFRAMES", "REPS"),
+                    help="run only a smaller long-column ML solve (for ncu captures)")
     ap.add_argument("--profile-case", nargs=3, type=int, metavar=("LBLOCK", "NFRAMES", "REPS"),
                     help="run a smaller case of the pipeline (for ncu captures) and exit")
     ap.add_argument("--profile-batched", type=int, metavar="NSTREAMS",
@@ -986,6 +1010,8 @@ def main():
         return run_profile_net(args.profile_net)
     if args.profile_case:
         return run_profile_case(*args.profile_case)
+    if args.profile_ml_long:
+        return run_profile_ml_long(*args.profile_ml_long)
     if args.profile_batched:
         return run_profile_batched(args.profile_batched)
     if args.impl == "reference":
