@@ -354,35 +354,44 @@ __device__ __forceinline__ void k3_pair(float2* __restrict__ d2, const float* __
       return sm;
   };
 
-  // 2-4. tasks: t = 0 (kb = 0), t = S/2 (kb = S/2), else the pair (t, S - t)
-  for (int t = r * T + tid; t <= S / 2; t += C * T) {
-    const bool pairtask = (t != 0) && (2 * t != S);
-    const int kb0 = t, kb1 = S - t;
+  // 2-4. tasks t < S/2: the pair (t, S - t); t = 0 takes the two self-paired groups
+  // kb = 0 and kb = S/2 together (each holds C modes whose partners lie in the same
+  // group, so together they weigh one pair task, and the S/2 tasks fill the C T
+  // threads' slots evenly instead of leaving one thread a third task)
+  for (int t = r * T + tid; t < S / 2; t += C * T) {
+    const bool pairtask = t != 0;
+    const int kb0 = t, kb1 = pairtask ? S - t : S / 2;
     float2 z0[C], z1[C];
     float2 w0[C];
     // gather + cross-stage twiddle + C-point DFT over r.  The twiddle of kb1 = S - kb0
-    // is e^{-2 pi i q (S - kb0)/J} = e^{-2 pi i q / C} conj(w0[q]).
-    if constexpr (C > 1) twiddle_powers<C>(twiddle<false>(kb0, J), w0);
+    // is e^{-2 pi i q (S - kb0)/J} = e^{-2 pi i q / C} conj(w0[q]); for kb0 = 0 it is 1,
+    // and kb1 = S/2 takes its own.
+    if constexpr (C > 1) twiddle_powers<C>(twiddle<false>(pairtask ? kb0 : S / 2, J), w0);
 #pragma unroll
     for (int q = 0; q < C; ++q) {
       z0[q] = peer(q)[pidx(kb0)];
-      if (pairtask) z1[q] = peer(q)[pidx(kb1)];
+      z1[q] = peer(q)[pidx(kb1)];
     }
     if constexpr (C > 1) {
 #pragma unroll
       for (int q = 1; q < C; ++q) {
-        z0[q] = cmul(z0[q], w0[q]);
-        if (pairtask) z1[q] = rotq<C, false>(cmul(z1[q], cconj(w0[q])), q);
+        if (pairtask) {
+          z0[q] = cmul(z0[q], w0[q]);
+          z1[q] = rotq<C, false>(cmul(z1[q], cconj(w0[q])), q);
+        } else {
+          z1[q] = cmul(z1[q], w0[q]);
+        }
       }
       DFT<C, false>::run(z0);
-      if (pairtask) DFT<C, false>::run(z1);
+      DFT<C, false>::run(z1);
     }
-    // gains: z0[ka] is mode k = kb0 + S*ka, e^{-2 pi i k/J} = e0 e^{-2 pi i ka/C}
+    // gains: z0[ka] is mode k = kb0 + S*ka, e^{-2 pi i k/J} = e0 e^{-2 pi i ka/C} (e0 of
+    // kb = S/2 in the t = 0 task)
     float2 e0;
     if constexpr (C > 1)
       e0 = w0[1];
     else
-      e0 = twiddle<false>(kb0, J);
+      e0 = twiddle<false>(pairtask ? kb0 : S / 2, J);
     if (pairtask) {
 #pragma unroll
       for (int ka = 0; ka < C; ++ka) {
@@ -390,8 +399,8 @@ __device__ __forceinline__ void k3_pair(float2* __restrict__ d2, const float* __
         const float2 e1 = rotq<C, false>(e0, ka);
         gn.pair(z0[ka], z1[C - 1 - ka], ta, tb, k, e1, gp, p);
       }
-    } else if (t == 0) {
-      // modes S*ka; -k is S*((C-ka) mod C)
+    } else {
+      // kb = 0 in z0: modes S*ka; -k is S*((C-ka) mod C)
 #pragma unroll
       for (int ka = 0; ka <= C / 2; ++ka) {
         const int km = (C - ka) % C;
@@ -402,33 +411,36 @@ __device__ __forceinline__ void k3_pair(float2* __restrict__ d2, const float* __
         z0[ka] = a;
         if (km != ka) z0[km] = b;
       }
-    } else {
-      // kb = S/2: modes S/2 + S*ka; -k is S/2 + S*(C-1-ka)
+      // kb = S/2 in z1: modes S/2 + S*ka; -k is S/2 + S*(C-1-ka)
 #pragma unroll
       for (int ka = 0; ka < (C + 1) / 2; ++ka) {
         const int km = C - 1 - ka;
-        const int k = kb0 + S * ka;
+        const int k = S / 2 + S * ka;
         const float2 e1 = rotq<C, false>(e0, ka);
-        float2 a = z0[ka], b = z0[km];
+        float2 a = z1[ka], b = z1[km];
         gn.single(a, b, ta, tb, k, e1, gp, p, km == ka);
-        z0[ka] = a;
-        if (km != ka) z0[km] = b;
+        z1[ka] = a;
+        if (km != ka) z1[km] = b;
       }
     }
     // inverse C-point DFT over ka, conj twiddle, push back to owner q
     if constexpr (C > 1) {
       DFT<C, true>::run(z0);
-      if (pairtask) DFT<C, true>::run(z1);
+      DFT<C, true>::run(z1);
 #pragma unroll
       for (int q = 1; q < C; ++q) {
-        z0[q] = cmul(z0[q], cconj(w0[q]));
-        if (pairtask) z1[q] = rotq<C, true>(cmul(z1[q], w0[q]), q);
+        if (pairtask) {
+          z0[q] = cmul(z0[q], cconj(w0[q]));
+          z1[q] = rotq<C, true>(cmul(z1[q], w0[q]), q);
+        } else {
+          z1[q] = cmul(z1[q], cconj(w0[q]));
+        }
       }
     }
 #pragma unroll
     for (int q = 0; q < C; ++q) {
       peer(q)[pidx(kb0)] = z0[q];
-      if (pairtask) peer(q)[pidx(kb1)] = z1[q];
+      peer(q)[pidx(kb1)] = z1[q];
     }
   }
   if constexpr (C > 1) {
