@@ -266,17 +266,18 @@ def _check_sampled_columns(dcols, w64, sig2, M, P, G, it_cols, tol, precond):
     return rel
 
 
-@pytest.mark.parametrize("J", [16384, 32768])
-def test_mlbig_two_and_four_cta_runs_of_8192(J):
+@pytest.mark.parametrize("J,ntap", [(16384, 4), (32768, 4), (16384, 8)])
+def test_mlbig_two_and_four_cta_runs_of_8192(J, ntap):
     """16384 and 32768 frames: residue splits C = 2, 4 with S = 8192 (the default on-chip
-    run), 8 and 16 tiles per pair; lblock 256, 10 % prior; sampled columns against the
-    oracle, the stopping test and true residuals on every column."""
-    N = 256
-    x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 26, nchunks=32)
+    run), 8 and 16 tiles per pair; an 8-tap window takes the generic-tap transform and the
+    15-tap stencil; lblock 256 (128 at 32768 frames), 10 % prior; sampled columns against
+    the oracle, the stopping test and true residuals on every column."""
+    N = 256 if J <= 16384 else 128
+    x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 26, nchunks=32, ntap=ntap)
     ipfb.set_max_column_run(8192)
     xg, it, res = _solve(codes, scale, w, sig2, mask, prior, precond="wiener", tol=1e-6, max_iter=500)
     assert np.all(res[0] <= 1e-6) and np.all(res[1] <= 1e-5)
-    cols = np.array([0, 1, N // 2 - 1, N // 2, N // 2 + 1, N - 1, 77, 190])
+    cols = np.array([0, 1, N // 2 - 1, N // 2, N // 2 + 1, N - 1, N // 3, 3 * N // 4])
     M = mask.reshape(J, N)[:, cols].astype(np.float64)
     P = prior.reshape(J, N)[:, cols].astype(np.float64)
     G = xg.reshape(J, N)[:, cols]
