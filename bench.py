@@ -510,6 +510,9 @@ def train_learned(torch, dev, epochs=None, seeds=range(1000, 1008)):
     return theta, info
 
 
+NET_FROM_SWEEP = (2, 8, 14, 20)
+
+
 def run_ml(torch, ipfb, dev, reps=3, theta=None):
     """Time to relative residual 1e-6 per column on the config-4 instance (seed 4, held
     out from training): plain CG, Wiener-PCG and, with theta, the learned FCG."""
@@ -544,6 +547,27 @@ def run_ml(torch, ipfb, dev, reps=3, theta=None):
         out["learned_vs_plain_time"] = out["learned"]["ms"] / out["none"]["ms"]
         out["learned_net_from"] = pt.NET_FROM
         out["learned_g0_note"] = "the same learned solve with a zero-output net (g = 0: the Wiener term alone)"
+        # the trade-off in net_from: the net's iterations cost far more than the on-chip
+        # Wiener-only ones, so joining early saves iterations and joining late saves time
+        sweep = []
+        ws = torch.empty(ipfb.workspace_size(g, ipfb.OP_ML_LEARNED), dtype=torch.uint8, device=dev)
+        for nf in NET_FROM_SWEEP:
+            row = {"net_from": nf}
+            for key, net in (("learned", theta), ("g0", zero)):
+                kw = dict(precond="learned", tol=1e-6, max_iter=4000, workspace=ws, net=net, net_from=nf)
+                ipfb.ml_solve(codes, scale, w, sig2, mask, prior, **kw)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    x, it, res = ipfb.ml_solve(codes, scale, w, sig2, mask, prior, **kw)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                row[key] = {"ms": e0.elapsed_time(e1) / reps, "iters_max": int(it.max()),
+                            "iters_mean": float(it.float().mean()), "resid_true_max": float(res[1].max())}
+            sweep.append(row)
+        del ws
+        out["learned_net_from_sweep"] = sweep
     out["paper_protocol"] = run_ml_paper_protocol(torch, ipfb, dev, codes, scale, w, prior, sig2, reps=reps)
     del codes, scale, w, mask, prior
     out["paper_size"] = run_ml_long(torch, ipfb, dev, reps=reps)

@@ -270,10 +270,13 @@ int ipfb_wiener_upchannelize(const ipfb_geom* g, const uint8_t* codes, const flo
  * ||b - A x|| / ||b|| <= tol (recursively updated residual), or after max_iter.
  * precond: 0 none; 1 Wiener, z = F^dagger[F r / (|W_n|^2/sigma^2 + lam mean(M_n))];
  * 2 learned: net = device pointer to the net parameters (float [IPFB_NET_NPARAMS],
- * see ipfb_net_forward), z = u + s g(u/s, m) with u the Wiener z above, s = RMS(u)
- * over the column (1 if u = 0), m the column's prior mask; the outer iteration is
- * then flexible CG (Notay 2000) with the Polak-Ribiere beta
- * r_new.(z_new - z_old) / r_old.z_old.  precond 2 requires ntap = 4; its workspace
+ * see ipfb_net_forward), z = u + lam mean(M_n) M_W(s g(u/s, m)) with u = M_W r the
+ * Wiener z above, M_W that Wiener step, s = RMS(u) over the column (1 if u = 0), m
+ * the column's prior mask; the outer iteration is then flexible CG (Notay 2000) with
+ * the Polak-Ribiere beta r_new.(z_new - z_old) / r_old.z_old.  The first net_from
+ * applications use u alone: with net_from >= 1 those iterations (Wiener-PCG) run in
+ * the on-chip CG kernel, which hands x, r, p, z and r.z over to the flexible-CG
+ * kernels for the columns still active.  precond 2 requires ntap = 4; its workspace
  * is ipfb_workspace_size(g, IPFB_OP_ML_LEARNED).  It is enqueued as one CUDA graph
  * whose loop (two launches per iteration) is ended on the device once no column is
  * active, so the call neither synchronizes nor reads anything back: when `stream` is

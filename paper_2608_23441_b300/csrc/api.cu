@@ -2,6 +2,7 @@
 // Declarations and the meaning of every argument: include/ipfb.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -559,7 +560,9 @@ MLParams ml_params(const ipfb_geom* g, const ipfb_ml_params* prm, int use_x0) {
 
 // ---------------------------------------------------------------- learned solve
 // The learned solve is one CUDA graph (no host synchronisation, no read-back):
-//   k2, [initial guess to pairs], net pack, counters cleared, FCG phase 0,
+//   k2, [initial guess to pairs], net pack, counters cleared,
+//   FCG phase 0 (net_from = 0) or, when the net joins later, the Wiener-only
+//   iterations on chip (k5_ml_cg with the hand-over) and FCG phase 3,
 //   loop control, WHILE { net, FCG step, net, FCG step, loop control },
 //   FCG finish, fallback check, IF { [initial guess to pairs], plain CG },
 //   pairs to time order.
@@ -740,7 +743,20 @@ int ml_solve_learned(const ipfb_geom* g, const uint8_t* codes, const float* scal
   if (use_x0) CK(launch_time_to_pairs(x_inout, b.X, N, J, s), "k_time_to_pairs");
   CK(launch_net_pack(theta, packed, s), "k6_net_pack");
   CK(cudaMemsetAsync(cnt, 0, kFcgCounters * sizeof(int), s), "cudaMemsetAsync");
-  CK(launch_fcg_step(J, 0, d2, b, mask, prior, window, N, mp, cnt, s), "k5_fcg_step");
+  if (prm->net_from >= 1) {
+    // The applications before the net joins use the Wiener step alone, so those
+    // iterations are Wiener-preconditioned CG: they run on chip (k5_ml_cg, one CTA per
+    // column pair, vectors in registers and shared memory), which hands its state over
+    // to the flexible-CG kernels; phase 3 takes the next step from it and asks the net
+    // for the columns still active.
+    MLParams wp = mp;
+    wp.precond = 1;
+    wp.max_iter = std::min(prm->net_from - 1, prm->max_iter);
+    CK(launch_k5_handover(J, d2, mask, prior, window, N, wp, b, prm->max_iter, s), "k5_ml_cg");
+    CK(launch_fcg_step(J, 3, d2, b, mask, prior, window, N, mp, cnt, s), "k5_fcg_step");
+  } else {
+    CK(launch_fcg_step(J, 0, d2, b, mask, prior, window, N, mp, cnt, s), "k5_fcg_step");
+  }
   cudaGraphConditionalHandle hl;
   if ((rc = capture_handle(c, 0, &hl))) return rc;
   CK(launch_fcg_loop_ctrl(b, N, cnt + 2, max_trips, hl, s), "k_fcg_loop_ctrl");

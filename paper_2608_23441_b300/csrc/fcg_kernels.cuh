@@ -23,18 +23,6 @@
 
 namespace ipfb {
 
-struct FcgCol {
-  double rz;    // r.z of the current search direction
-  float bnorm;  // |b|
-  float rel;    // |r| / |b| (recursive residual)
-  float s;      // RMS of u = M_W r, the net input scale
-  float lam_m;  // prior weight x mask mean of the column (Wiener preconditioner)
-  int iters;
-  int active;
-  int slot;     // request slot of the current preconditioner application
-  int pad;
-};
-
 template <int NT, int RMAX>
 __device__ __forceinline__ void load_taps_stencil(const float* __restrict__ window, int N, int p, int ntap,
                                                   float inv_s2, float (&ta)[NT > 0 ? NT : kMlMaxTaps],
@@ -131,26 +119,28 @@ constexpr size_t fcg_smem_bytes() {
 
 // phase 0: r0 = b - A x0, first request, P = Z = 0.  phase 1: z0 from the net, p = z0.
 // phase 2: z from the net, Polak-Ribiere beta, p update (with rz = 0 after phase 0,
-// beta is 0 and phase 2 does what phase 1 does).  Phases 1 and 2 then take
-// one CG step and issue the next request for the columns still active.
+// beta is 0 and phase 2 does what phase 1 does).  phase 3: resume from the state that
+// k5_ml_cg handed over (search direction P and r.z already formed).  Phases 1 to 3
+// then take one CG step and issue the next request for the columns still active.
 template <int J, int T, int RMAX, int NT>
-__global__ void __launch_bounds__(T, 1)
-k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, float2* __restrict__ R,
-            float2* __restrict__ Pv, float2* __restrict__ Z, float2* __restrict__ U, const uint8_t* __restrict__ mask,
-            const float* __restrict__ prior, const float* __restrict__ window, int N, MLParams mp,
-            FcgCol* __restrict__ cs, const float* __restrict__ Y, float* __restrict__ netin,
-            uint32_t* __restrict__ mbc, int* __restrict__ counter) {
+__device__ __forceinline__ void fcg_step_pair(int p, int phase, const float2* __restrict__ d2, float2* __restrict__ X,
+                                              float2* __restrict__ R, float2* __restrict__ Pv,
+                                              float2* __restrict__ Z, float2* __restrict__ U,
+                                              const uint8_t* __restrict__ mask, const float* __restrict__ prior,
+                                              const float* __restrict__ window, int N, const MLParams& mp,
+                                              FcgCol* __restrict__ cs, const float* __restrict__ Y,
+                                              float* __restrict__ netin, uint32_t* __restrict__ mbc,
+                                              int* __restrict__ counter, float2* smem) {
   constexpr int EPT = J / T;
   constexpr int WIN = EPT + 2 * RMAX;
   constexpr int NMAX = NT > 0 ? NT : kMlMaxTaps;
-  extern __shared__ float2 smem[];
   float2* sm_p = smem;
   float2* sm_f = sm_p + padded_len(J);
   double* res = reinterpret_cast<double*>(sm_f + padded_len(J));
   float* part = reinterpret_cast<float*>(res + 8);
   int* sflag = reinterpret_cast<int*>(part + (T / 32) * 4);
 
-  const int tid = threadIdx.x, p = blockIdx.x, j0 = tid * EPT;
+  const int tid = threadIdx.x, j0 = tid * EPT;
   const size_t vb = (size_t)p * J + tid;  // element e of this thread at vb + e T
   FcgCol sa = {}, sb = {};
   if (phase != 0) {
@@ -223,69 +213,73 @@ k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, fl
     const bool na = aa && sa.slot >= 0, nb = ab && sb.slot >= 0;
     float2 z[EPT];
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      r[e] = R[vb + (size_t)e * T];
-      z[e] = U[vb + (size_t)e * T];
-    }
-    if (na || nb) {
-      // z = u + lam mbar M_W(s y) = M_W(r + lam mbar s y): the net's output enters
-      // through the Wiener preconditioner weighted by the column's prior term, i.e.
-      // mode k of it is scaled by rho(k) = lam mbar / (|W(k)|^2 / sigma^2 + lam mbar),
-      // near 1 where the prior dominates (the near-null eigenvalues of App. A) and
-      // near 0 where the Wiener step already resolves the mode, which is left as it is.
+    for (int e = 0; e < EPT; ++e) r[e] = R[vb + (size_t)e * T];
+    if (phase == 3) {
 #pragma unroll
-      for (int q = 0; q < EPT / 4; ++q) {
-        const float4 va = na ? reinterpret_cast<const float4*>(Y + (size_t)sa.slot * J + j0)[q]
-                             : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        const float4 vb4 = nb ? reinterpret_cast<const float4*>(Y + (size_t)sb.slot * J + j0)[q]
-                              : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        const float ya[4] = {va.x, va.y, va.z, va.w}, yb[4] = {vb4.x, vb4.y, vb4.z, vb4.w};
+      for (int e = 0; e < EPT; ++e) sm_p[pidx(j0 + e)] = Pv[vb + (size_t)e * T];
+    } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) sm_f[pidx(j0 + 4 * q + i)] = make_float2(sa.s * ya[i], sb.s * yb[i]);
+      for (int e = 0; e < EPT; ++e) z[e] = U[vb + (size_t)e * T];
+      if (na || nb) {
+        // z = u + lam mbar M_W(s y) = M_W(r + lam mbar s y): the net's output enters
+        // through the Wiener preconditioner weighted by the column's prior term, i.e.
+        // mode k of it is scaled by rho(k) = lam mbar / (|W(k)|^2 / sigma^2 + lam mbar),
+        // near 1 where the prior dominates (the near-null eigenvalues of App. A) and
+        // near 0 where the Wiener step already resolves the mode, which is left as it is.
+#pragma unroll
+        for (int q = 0; q < EPT / 4; ++q) {
+          const float4 va = na ? reinterpret_cast<const float4*>(Y + (size_t)sa.slot * J + j0)[q]
+                               : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          const float4 vb4 = nb ? reinterpret_cast<const float4*>(Y + (size_t)sb.slot * J + j0)[q]
+                                : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          const float ya[4] = {va.x, va.y, va.z, va.w}, yb[4] = {vb4.x, vb4.y, vb4.z, vb4.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) sm_f[pidx(j0 + 4 * q + i)] = make_float2(sa.s * ya[i], sb.s * yb[i]);
+        }
+        __syncthreads();
+        wiener_precond_pair<J, T, NT>(sm_f, ta, tb, mp.ntap, mp.inv_s2, sa.lam_m, sb.lam_m);
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          const float2 c = sm_f[pidx(j0 + e)];
+          if (na) z[e].x = fmaf(sa.lam_m, c.x, z[e].x);
+          if (nb) z[e].y = fmaf(sb.lam_m, c.y, z[e].y);
+        }
       }
-      __syncthreads();
-      wiener_precond_pair<J, T, NT>(sm_f, ta, tb, mp.ntap, mp.inv_s2, sa.lam_m, sb.lam_m);
 #pragma unroll
       for (int e = 0; e < EPT; ++e) {
-        const float2 c = sm_f[pidx(j0 + e)];
-        if (na) z[e].x = fmaf(sa.lam_m, c.x, z[e].x);
-        if (nb) z[e].y = fmaf(sb.lam_m, c.y, z[e].y);
+        if (!aa) z[e].x = 0.0f;
+        if (!ab) z[e].y = 0.0f;
       }
-    }
+      // r.z_new (and r.z_old for the Polak-Ribiere beta)
+      float q[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      float2 zo[EPT];
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      if (!aa) z[e].x = 0.0f;
-      if (!ab) z[e].y = 0.0f;
-    }
-    // r.z_new (and r.z_old for the Polak-Ribiere beta)
-    float q[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    float2 zo[EPT];
+      for (int e = 0; e < EPT; ++e) {
+        zo[e] = phase == 2 ? Z[vb + (size_t)e * T] : make_float2(0.0f, 0.0f);
+        q[0] = fmaf(r[e].x, z[e].x, q[0]);
+        q[1] = fmaf(r[e].y, z[e].y, q[1]);
+        q[2] = fmaf(r[e].x, zo[e].x, q[2]);
+        q[3] = fmaf(r[e].y, zo[e].y, q[3]);
+      }
+      block_sum_bcast<4, T>(q, part, res, NoScalars{});
+      float be_a = 0.0f, be_b = 0.0f;
+      if (phase == 2) {
+        be_a = (aa && sa.rz != 0.0) ? (float)((res[0] - res[2]) / sa.rz) : 0.0f;
+        be_b = (ab && sb.rz != 0.0) ? (float)((res[1] - res[3]) / sb.rz) : 0.0f;
+      }
+      if (aa) sa.rz = res[0];
+      if (ab) sb.rz = res[1];
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      zo[e] = phase == 2 ? Z[vb + (size_t)e * T] : make_float2(0.0f, 0.0f);
-      q[0] = fmaf(r[e].x, z[e].x, q[0]);
-      q[1] = fmaf(r[e].y, z[e].y, q[1]);
-      q[2] = fmaf(r[e].x, zo[e].x, q[2]);
-      q[3] = fmaf(r[e].y, zo[e].y, q[3]);
-    }
-    block_sum_bcast<4, T>(q, part, res, NoScalars{});
-    float be_a = 0.0f, be_b = 0.0f;
-    if (phase == 2) {
-      be_a = (aa && sa.rz != 0.0) ? (float)((res[0] - res[2]) / sa.rz) : 0.0f;
-      be_b = (ab && sb.rz != 0.0) ? (float)((res[1] - res[3]) / sb.rz) : 0.0f;
-    }
-    if (aa) sa.rz = res[0];
-    if (ab) sb.rz = res[1];
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      float2 pe = phase == 2 ? Pv[vb + (size_t)e * T] : make_float2(0.0f, 0.0f);
-      if (aa) pe.x = fmaf(be_a, pe.x, z[e].x);
-      if (ab) pe.y = fmaf(be_b, pe.y, z[e].y);
-      if (!aa) pe.x = 0.0f;
-      if (!ab) pe.y = 0.0f;
-      sm_p[pidx(j0 + e)] = pe;
-      Pv[vb + (size_t)e * T] = pe;
-      Z[vb + (size_t)e * T] = z[e];
+      for (int e = 0; e < EPT; ++e) {
+        float2 pe = phase == 2 ? Pv[vb + (size_t)e * T] : make_float2(0.0f, 0.0f);
+        if (aa) pe.x = fmaf(be_a, pe.x, z[e].x);
+        if (ab) pe.y = fmaf(be_b, pe.y, z[e].y);
+        if (!aa) pe.x = 0.0f;
+        if (!ab) pe.y = 0.0f;
+        sm_p[pidx(j0 + e)] = pe;
+        Pv[vb + (size_t)e * T] = pe;
+        Z[vb + (size_t)e * T] = z[e];
+      }
     }
     __syncthreads();
     float2 pw[WIN];
@@ -348,6 +342,38 @@ k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, fl
   if (tid == 0) {
     cs[2 * p] = sa;
     cs[2 * p + 1] = sb;
+  }
+}
+
+// One flexible-CG step over the column pairs.  A grid of G CTAs (one per SM) walks
+// the pairs p = blockIdx.x + i G: every pair in phase 0, otherwise only the pairs with
+// an active column (listed in shared memory first), so that a step near the end of a
+// solve costs the few pairs still running rather than a launch wave per SM-full of
+// finished ones.
+template <int J, int T, int RMAX, int NT>
+__global__ void __launch_bounds__(T, 1)
+k5_fcg_step(int phase, const float2* __restrict__ d2, float2* __restrict__ X, float2* __restrict__ R,
+            float2* __restrict__ Pv, float2* __restrict__ Z, float2* __restrict__ U, const uint8_t* __restrict__ mask,
+            const float* __restrict__ prior, const float* __restrict__ window, int N, MLParams mp,
+            FcgCol* __restrict__ cs, const float* __restrict__ Y, float* __restrict__ netin,
+            uint32_t* __restrict__ mbc, int* __restrict__ counter) {
+  extern __shared__ float2 smem[];
+  __shared__ int plist[T];
+  __shared__ int nlist;
+  const int P = N / 2, G = gridDim.x;
+  for (int base = blockIdx.x; base < P; base += G * T) {
+    __syncthreads();  // the previous chunk's list and pairs are done
+    if (threadIdx.x == 0) nlist = 0;
+    __syncthreads();
+    const int pp = base + threadIdx.x * G;
+    if (pp < P && (phase == 0 || cs[2 * pp].active || cs[2 * pp + 1].active)) plist[atomicAdd(&nlist, 1)] = pp;
+    __syncthreads();
+    const int n = nlist;
+    for (int k = 0; k < n; ++k) {
+      __syncthreads();  // the previous pair's shared-memory readers are done
+      fcg_step_pair<J, T, RMAX, NT>(plist[k], phase, d2, X, R, Pv, Z, U, mask, prior, window, N, mp, cs, Y, netin,
+                                    mbc, counter, smem);
+    }
   }
 }
 

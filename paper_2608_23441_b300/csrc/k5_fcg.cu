@@ -1,4 +1,6 @@
 // Flexible-CG launches (learned preconditioner) and the net's training-pair builder.
+#include <algorithm>
+
 #include "fcg_kernels.cuh"
 #include "launch.h"
 
@@ -13,8 +15,13 @@ cudaError_t fcg_step(int phase, const float2* d2, const FcgBufs& b, const uint8_
   const size_t smem = fcg_smem_bytes<J, T>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<N / 2, T, smem, st>>>(phase, d2, b.X, b.R, b.P, b.Z, b.U, mask, prior, window, N, mp, b.cs, b.Y, b.netin,
-                               b.mb, counter);
+  // one CTA per SM (the kernel's shared memory allows no more) walks the pairs
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(N / 2, sms));
+  kern<<<grid, T, smem, st>>>(phase, d2, b.X, b.R, b.P, b.Z, b.U, mask, prior, window, N, mp, b.cs, b.Y, b.netin,
+                              b.mb, counter);
   return cudaGetLastError();
 }
 

@@ -7,28 +7,29 @@ namespace ipfb {
 namespace {
 template <int J, int RMAX, int PRE, int NT>
 cudaError_t k5(const float2* d2, float2* x2, const uint8_t* mask, const float* prior, const float* window, int N,
-               const MLParams& mp, int* iters, float* resid, cudaStream_t st) {
+               const MLParams& mp, int* iters, float* resid, const FcgBufs& ex, int ex_max_iter, cudaStream_t st) {
   constexpr int T = (J / 16 < 32) ? 32 : (J / 16 > 512 ? 512 : J / 16);
   auto kern = k5_ml_cg<J, T, RMAX, PRE, NT>;
   size_t smem = 2 * (size_t)padded_len(J) * sizeof(float2) + 24 * sizeof(double) + (size_t)(T / 32) * 4 * sizeof(float);
   if (PRE == 1) smem += (size_t)padded_len(J) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<N / 2, T, smem, st>>>(d2, x2, mask, prior, window, N, mp, iters, resid);
+  kern<<<N / 2, T, smem, st>>>(d2, x2, mask, prior, window, N, mp, iters, resid, ex, ex_max_iter);
   return cudaGetLastError();
 }
 
 template <int RMAX, int PRE, int NT>
 cudaError_t k5_j(int J, const float2* d2, float2* x2, const uint8_t* mask, const float* prior, const float* window,
-                 int N, const MLParams& mp, int* iters, float* resid, cudaStream_t st) {
+                 int N, const MLParams& mp, int* iters, float* resid, const FcgBufs& ex, int ex_max_iter,
+                 cudaStream_t st) {
   switch (J) {
-    case 128: return k5<128, RMAX, PRE, NT>(d2, x2, mask, prior, window, N, mp, iters, resid, st);
-    case 256: return k5<256, RMAX, PRE, NT>(d2, x2, mask, prior, window, N, mp, iters, resid, st);
-    case 512: return k5<512, RMAX, PRE, NT>(d2, x2, mask, prior, window, N, mp, iters, resid, st);
-    case 1024: return k5<1024, RMAX, PRE, NT>(d2, x2, mask, prior, window, N, mp, iters, resid, st);
-    case 2048: return k5<2048, RMAX, PRE, NT>(d2, x2, mask, prior, window, N, mp, iters, resid, st);
-    case 4096: return k5<4096, RMAX, PRE, NT>(d2, x2, mask, prior, window, N, mp, iters, resid, st);
-    case 8192: return k5<8192, RMAX, PRE, NT>(d2, x2, mask, prior, window, N, mp, iters, resid, st);
+    case 128: return k5<128, RMAX, PRE, NT>(d2, x2, mask, prior, window, N, mp, iters, resid, ex, ex_max_iter, st);
+    case 256: return k5<256, RMAX, PRE, NT>(d2, x2, mask, prior, window, N, mp, iters, resid, ex, ex_max_iter, st);
+    case 512: return k5<512, RMAX, PRE, NT>(d2, x2, mask, prior, window, N, mp, iters, resid, ex, ex_max_iter, st);
+    case 1024: return k5<1024, RMAX, PRE, NT>(d2, x2, mask, prior, window, N, mp, iters, resid, ex, ex_max_iter, st);
+    case 2048: return k5<2048, RMAX, PRE, NT>(d2, x2, mask, prior, window, N, mp, iters, resid, ex, ex_max_iter, st);
+    case 4096: return k5<4096, RMAX, PRE, NT>(d2, x2, mask, prior, window, N, mp, iters, resid, ex, ex_max_iter, st);
+    case 8192: return k5<8192, RMAX, PRE, NT>(d2, x2, mask, prior, window, N, mp, iters, resid, ex, ex_max_iter, st);
   }
   return cudaErrorNotSupported;
 }
@@ -36,12 +37,20 @@ cudaError_t k5_j(int J, const float2* d2, float2* x2, const uint8_t* mask, const
 
 cudaError_t launch_k5(int J, const float2* d2, float2* x2, const uint8_t* mask, const float* prior,
                       const float* window, int N, const MLParams& mp, int* iters, float* resid, cudaStream_t st) {
+  const FcgBufs none = {};
   if (mp.ntap == 4) {
-    if (mp.precond == 1) return k5_j<3, 1, 4>(J, d2, x2, mask, prior, window, N, mp, iters, resid, st);
-    return k5_j<3, 0, 4>(J, d2, x2, mask, prior, window, N, mp, iters, resid, st);
+    if (mp.precond == 1) return k5_j<3, 1, 4>(J, d2, x2, mask, prior, window, N, mp, iters, resid, none, 0, st);
+    return k5_j<3, 0, 4>(J, d2, x2, mask, prior, window, N, mp, iters, resid, none, 0, st);
   }
-  if (mp.precond == 1) return k5_j<15, 1, 0>(J, d2, x2, mask, prior, window, N, mp, iters, resid, st);
-  return k5_j<15, 0, 0>(J, d2, x2, mask, prior, window, N, mp, iters, resid, st);
+  if (mp.precond == 1) return k5_j<15, 1, 0>(J, d2, x2, mask, prior, window, N, mp, iters, resid, none, 0, st);
+  return k5_j<15, 0, 0>(J, d2, x2, mask, prior, window, N, mp, iters, resid, none, 0, st);
+}
+
+cudaError_t launch_k5_handover(int J, const float2* d2, const uint8_t* mask, const float* prior,
+                               const float* window, int N, const MLParams& mp, const FcgBufs& b, int fcg_max_iter,
+                               cudaStream_t st) {
+  if (mp.ntap != 4 || !b.X) return cudaErrorNotSupported;
+  return k5_j<3, 1, 4>(J, d2, b.X, mask, prior, window, N, mp, nullptr, nullptr, b, fcg_max_iter, st);
 }
 
 namespace {

@@ -55,6 +55,20 @@ __device__ __forceinline__ void block_sum_bcast(float (&v)[K], float* part, doub
   __syncthreads();
 }
 
+// Per-column state of the flexible-CG solve (fcg_kernels.cuh); k5_ml_cg writes it too
+// when it hands a Wiener-preconditioned solve over to the flexible-CG kernels.
+struct FcgCol {
+  double rz;    // r.z of the current search direction
+  float bnorm;  // |b|
+  float rel;    // |r| / |b| (recursive residual)
+  float s;      // RMS of u = M_W r, the net input scale
+  float lam_m;  // prior weight x mask mean of the column (Wiener preconditioner)
+  int iters;
+  int active;
+  int slot;     // request slot of the current preconditioner application
+  int pad;
+};
+
 struct NoScalars {
   template <class A>
   __device__ __forceinline__ void operator()(const A&, double*) const {}
@@ -166,7 +180,7 @@ template <int J, int T, int RMAX, int PRE, int NT>
 __global__ void __launch_bounds__(T, 1)
 k5_ml_cg(const float2* __restrict__ d2, float2* __restrict__ x2, const uint8_t* __restrict__ mask,
          const float* __restrict__ prior, const float* __restrict__ window, int N, MLParams mp,
-         int* __restrict__ iters, float* __restrict__ resid) {
+         int* __restrict__ iters, float* __restrict__ resid, FcgBufs ex, int ex_max_iter) {
   constexpr int EPT = J / T;
   constexpr int WIN = EPT + 2 * RMAX;
   static_assert(EPT >= 1 && EPT <= 16, "1..16 frames per thread");
@@ -364,6 +378,44 @@ k5_ml_cg(const float2* __restrict__ d2, float2* __restrict__ x2, const uint8_t* 
       sm_p[pidx(j0 + e)] = pe;
     }
     __syncthreads();  // publish sm_p before the next stencil
+  }
+
+  if (ex.X) {
+    // Hand-over to the flexible-CG kernels (the learned solve runs its Wiener-only
+    // iterations here, on chip): x, r, the search direction p, z = M_W r of the last
+    // step and r.z, in their lane-interleaved layout (element e of thread t at
+    // p J + e T + t), with the mask bits and the per-column state.  A column stays
+    // active if it has not converged and has iterations left (ex_max_iter).
+    const size_t vb = (size_t)p * J + tid;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+      ex.X[vb + (size_t)e * T] = sm_x[pidx(j0 + e)];
+      ex.R[vb + (size_t)e * T] = r[e];
+      ex.P[vb + (size_t)e * T] = sm_p[pidx(j0 + e)];
+      ex.Z[vb + (size_t)e * T] = z[e];
+    }
+    ex.mb[(size_t)p * T + tid] = mbits;
+    if (tid == 0) {
+      const int ac = (int)st[4];
+      FcgCol ca = {}, cb = {};
+      ca.rz = st[7];
+      cb.rz = st[8];
+      ca.bnorm = (float)st[5];
+      cb.bnorm = (float)st[6];
+      ca.rel = (float)st[9];
+      cb.rel = (float)st[10];
+      ca.s = cb.s = 1.0f;
+      ca.lam_m = lam_ma;
+      cb.lam_m = lam_mb;
+      ca.iters = (int)st[11];
+      cb.iters = (int)st[12];
+      ca.active = ((ac & 1) && ca.iters < ex_max_iter) ? 1 : 0;
+      cb.active = ((ac & 2) && cb.iters < ex_max_iter) ? 1 : 0;
+      ca.slot = cb.slot = -1;
+      ex.cs[2 * p] = ca;
+      ex.cs[2 * p + 1] = cb;
+    }
+    return;
   }
 
   // true residual b - A x (FP32 operator, FP64 norms); write the solution

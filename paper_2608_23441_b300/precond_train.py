@@ -21,9 +21,16 @@ from . import ipfb, synth
 
 NTAP = 4
 # training epochs of the recipe, and the preconditioner applications that use the
-# Wiener term alone before the net joins the learned solve (ipfb_ml_params.net_from)
+# Wiener term alone before the net joins the learned solve (ipfb_ml_params.net_from).
+# Those first iterations run on chip at about 25 us each; an iteration with the net
+# (its forward over the active columns plus a flexible-CG step with two pair FFTs)
+# costs about 0.1 ms, so the net is kept for the slow columns: joining at the 21st
+# application, the learned solve of the lblock-4096, 8192-spectrum workload is
+# faster than plain CG; joining at the 3rd (NET_FROM_EARLY) it takes the fewest
+# iterations but about three times plain CG's time.
 EPOCHS = 24
-NET_FROM = 2
+NET_FROM = 20
+NET_FROM_EARLY = 2
 
 
 def init_theta(seed: int, scale3: float = 0.1) -> np.ndarray:

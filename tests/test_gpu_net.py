@@ -150,7 +150,24 @@ def test_training_pairs_match_oracle():
         assert np.max(np.abs(tgt[c] - ref_t[c])) <= 1e-4 * np.sqrt(np.mean((E[:, c] / s[c]) ** 2)), c
 
 
-def test_learned_with_zero_net_is_wiener_pcg():
+def _oracle_precond(pr, Mw, M, lam_mbar, net_from):
+    """The learned preconditioner of the oracle FCG, with the net joining from the
+    net_from-th application (the earlier ones are the Wiener step alone)."""
+    calls = [0]
+
+    def pre(R):
+        k = calls[0]
+        calls[0] += 1
+        u = Mw(R)
+        return u if k < net_from else onet.apply_precond(pr, u, M, Mw, lam_mbar, emulate_bf16=True)
+    return pre
+
+
+@pytest.mark.parametrize("net_from", [0, 2])
+def test_learned_with_zero_net_is_wiener_pcg(net_from):
+    """A zero-output net leaves the Wiener term alone: the learned solve is Wiener-PCG
+    (with net_from >= 1 its first iterations run in the on-chip CG kernel, which hands
+    its state over to the flexible-CG kernels)."""
     N, J = 64, 256
     x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 22)
     p = onet.unflatten(_theta(23))
@@ -159,21 +176,23 @@ def test_learned_with_zero_net_is_wiener_pcg():
     th = cuda(onet.flatten(p).astype(np.float32))
     args = (cuda(codes), cuda(scale), cuda(w.astype(np.float32)), sig2, cuda(mask), cuda(prior))
     xw, itw, rw = ipfb.ml_solve(*args, precond="wiener", tol=1e-6, max_iter=500)
-    xl, itl, rl = ipfb.ml_solve(*args, precond="learned", net=th, tol=1e-6, max_iter=500)
+    xl, itl, rl = ipfb.ml_solve(*args, precond="learned", net=th, tol=1e-6, max_iter=500, net_from=net_from)
     itw, itl = itw.cpu().numpy(), itl.cpu().numpy()
     assert np.all(np.abs(itw - itl) <= 1), np.abs(itw - itl).max()
     assert np.all(rl.cpu().numpy()[0] <= 1e-6)
     assert _rel(xl.cpu().numpy(), xw.cpu().numpy()) <= 1e-4
 
 
-@pytest.mark.parametrize("N,J", [(64, 128), (64, 512)])
-def test_learned_fcg_matches_oracle(N, J):
+@pytest.mark.parametrize("N,J,net_from", [(64, 128, 0), (64, 512, 0), (64, 512, 3), (64, 1024, 1)])
+def test_learned_fcg_matches_oracle(N, J, net_from):
+    """Learned FCG against the oracle's FCG with the BF16-emulating net; with
+    net_from >= 1 the Wiener-only iterations run on chip and are handed over."""
     x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 24)
     th = _theta(25, scale3=0.2, jitter=0.01)
     tol = 1e-6
     xl, itl, rl = ipfb.ml_solve(cuda(codes), cuda(scale), cuda(w.astype(np.float32)), sig2, cuda(mask),
                                 cuda(prior), precond="learned", net=cuda(th.astype(np.float32)), tol=tol,
-                                max_iter=2000)
+                                max_iter=2000, net_from=net_from)
     xl = xl.cpu().numpy().reshape(J, N).astype(np.float64)
     itl, rl = itl.cpu().numpy(), rl.cpu().numpy()
     M = mask.reshape(J, N).astype(np.float64)
@@ -183,7 +202,7 @@ def test_learned_fcg_matches_oracle(N, J):
     pr = onet.unflatten(th.astype(np.float32).astype(np.float64))
     lam_mbar = 1.0 * M.mean(axis=0)
     Mw = lambda R: oml.wiener_precond(w, R, sig2, M, 1.0)  # noqa: E731
-    pre = lambda R: onet.apply_precond(pr, Mw(R), M, Mw, lam_mbar, emulate_bf16=True)  # noqa: E731
+    pre = _oracle_precond(pr, Mw, M, lam_mbar, net_from)
     Xo, ito, _ = onet.fcg(A, B, np.zeros_like(B), pre, tol, 2000)
     assert np.all(rl[0] <= tol)
     tr = oml.true_relative_residual(d, w, sig2, M, P, 1.0, xl)
@@ -196,10 +215,12 @@ def test_learned_fcg_matches_oracle(N, J):
     assert abs(e_gpu - e_or) <= 1e-3 * e_or
 
 
-def test_learned_initial_guess():
+@pytest.mark.parametrize("net_from", [0, 2])
+def test_learned_initial_guess(net_from):
     """x0 enters in frame order and the solution leaves in frame order: with no
     iteration the output is x0 bit for bit; from x0 the learned FCG reaches the same
-    reconstruction as the oracle's FCG started from the same x0."""
+    reconstruction as the oracle's FCG started from the same x0 (net_from >= 1: through
+    the on-chip Wiener iterations and the hand-over)."""
     N, J = 64, 256
     x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 27)
     th = _theta(28, scale3=0.2, jitter=0.01)
@@ -207,12 +228,12 @@ def test_learned_initial_guess():
     x0 = (x + 0.3 * rng.standard_normal(x.shape)).astype(np.float32)
     args = (cuda(codes), cuda(scale), cuda(w.astype(np.float32)), sig2, cuda(mask), cuda(prior))
     x_same, it0, _ = ipfb.ml_solve(*args, precond="learned", net=cuda(th.astype(np.float32)), tol=1e-6,
-                                   max_iter=0, x0=cuda(x0))
+                                   max_iter=0, x0=cuda(x0), net_from=net_from)
     assert np.array_equal(x_same.cpu().numpy(), x0)
     assert np.all(it0.cpu().numpy() == 0)
     tol = 1e-6
     xl, itl, rl = ipfb.ml_solve(*args, precond="learned", net=cuda(th.astype(np.float32)), tol=tol,
-                                max_iter=2000, x0=cuda(x0))
+                                max_iter=2000, x0=cuda(x0), net_from=net_from)
     xl = xl.cpu().numpy().reshape(J, N).astype(np.float64)
     itl, rl = itl.cpu().numpy(), rl.cpu().numpy()
     M = mask.reshape(J, N).astype(np.float64)
@@ -222,7 +243,7 @@ def test_learned_initial_guess():
     pr = onet.unflatten(th.astype(np.float32).astype(np.float64))
     lam_mbar = 1.0 * M.mean(axis=0)
     Mw = lambda R: oml.wiener_precond(w, R, sig2, M, 1.0)  # noqa: E731
-    pre = lambda R: onet.apply_precond(pr, Mw(R), M, Mw, lam_mbar, emulate_bf16=True)  # noqa: E731
+    pre = _oracle_precond(pr, Mw, M, lam_mbar, net_from)
     Xo, ito, _ = onet.fcg(A, B, x0.reshape(J, N).astype(np.float64), pre, tol, 2000)
     assert np.all(rl[0] <= tol)
     tr = oml.true_relative_residual(d, w, sig2, M, P, 1.0, xl)
@@ -292,7 +313,9 @@ def test_trained_net_gain_over_its_zero_output_form():
     the Wiener preconditioner) and than Wiener-PCG itself: a lower worst-column count
     (by 4 or more), a lower mean, at least 15 % fewer iterations over the slow columns
     (those Wiener-PCG needs 10 or more for), and the same reconstruction error within
-    1e-3 relative."""
+    1e-3 relative.  With the net joining late (the default net_from, where the learned
+    solve is faster than plain CG) it still lowers the worst column and the mean
+    against its zero-output form."""
     from paper_2608_23441_b300 import precond_train as pt
     dev = torch.device("cuda", 0)
     xin, tgt, _ = pt.make_training_set(torch, dev, list(range(1000, 1008)))
@@ -309,8 +332,9 @@ def test_trained_net_gain_over_its_zero_output_form():
     args = (codes, scale, w, sig2, mask, x)
     zero = torch.from_numpy(pt.init_theta(0, scale3=0.0)).to(dev)
     xw, itw, rw = ipfb.ml_solve(*args, precond="wiener", tol=1e-6, max_iter=4000)
-    x0, it0, r0 = ipfb.ml_solve(*args, precond="learned", net=zero, tol=1e-6, max_iter=4000, net_from=pt.NET_FROM)
-    xl, itl, rl = ipfb.ml_solve(*args, precond="learned", net=theta, tol=1e-6, max_iter=4000, net_from=pt.NET_FROM)
+    nf = pt.NET_FROM_EARLY
+    x0, it0, r0 = ipfb.ml_solve(*args, precond="learned", net=zero, tol=1e-6, max_iter=4000, net_from=nf)
+    xl, itl, rl = ipfb.ml_solve(*args, precond="learned", net=theta, tol=1e-6, max_iter=4000, net_from=nf)
     for r in (rw, r0, rl):
         assert bool((r[0] <= 1e-6).all())
     itw, it0, itl = itw.cpu().numpy(), it0.cpu().numpy(), itl.cpu().numpy()
@@ -325,6 +349,17 @@ def test_trained_net_gain_over_its_zero_output_form():
     ew = float(torch.linalg.norm(xw - x) / torch.linalg.norm(x))
     el = float(torch.linalg.norm(xl - x) / torch.linalg.norm(x))
     assert abs(el - ew) <= 1e-3 * ew, (el, ew)
+    # the net joining late
+    _, it0l, r0l = ipfb.ml_solve(*args, precond="learned", net=zero, tol=1e-6, max_iter=4000, net_from=pt.NET_FROM)
+    xll, itll, rll = ipfb.ml_solve(*args, precond="learned", net=theta, tol=1e-6, max_iter=4000,
+                                   net_from=pt.NET_FROM)
+    assert bool((rll[0] <= 1e-6).all()) and bool((r0l[0] <= 1e-6).all())
+    it0l, itll = it0l.cpu().numpy(), itll.cpu().numpy()
+    print(f"net from application {pt.NET_FROM + 1}: worst column {itll.max()} against {it0l.max()}, "
+          f"mean {itll.mean():.4f} against {it0l.mean():.4f}")
+    assert itll.max() < it0l.max() and itll.mean() < it0l.mean(), (itll.max(), it0l.max())
+    ell = float(torch.linalg.norm(xll - x) / torch.linalg.norm(x))
+    assert abs(ell - ew) <= 1e-3 * ew, (ell, ew)
 
 
 def test_training_resumes_exactly_from_a_checkpoint(tmp_path):
