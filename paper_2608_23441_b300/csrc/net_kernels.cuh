@@ -205,9 +205,17 @@ __device__ __forceinline__ void load_pack(const uint8_t* __restrict__ packed, __
 
 // x0 rows: x0s[i] = (bf16 ch0, bf16 ch1) at position (q0 + i) mod J, i < nrows
 __device__ __forceinline__ void load_x0(const float* __restrict__ in, int J, int q0, int nrows, uint32_t* x0s) {
+  // positions q0 .. q0 + nrows - 1 lie in [-J, 2J) when -J <= q0 and q0 + nrows <= 2J
+  // (every tile of a column with J >= nrows): one conditional wrap, no division
+  const bool one_wrap = q0 >= -J && q0 + nrows <= 2 * J;
   for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
-    int q = (q0 + i) % J;
-    if (q < 0) q += J;
+    int q = q0 + i;
+    if (one_wrap) {
+      q = q < 0 ? q + J : (q >= J ? q - J : q);
+    } else {
+      q %= J;
+      if (q < 0) q += J;
+    }
     x0s[i] = pack_bf2(__ldg(in + q), __ldg(in + J + q));
   }
 }
@@ -251,6 +259,56 @@ __device__ __forceinline__ void conv_layer_warp(const __nv_bfloat16* A, int astr
   for (int n = 0; n < 4; ++n) {
     epi(m0 + g, n * 8 + 2 * c, acc[n][0], acc[n][1]);
     epi(m0 + g + 8, n * 8 + 2 * c, acc[n][2], acc[n][3]);
+  }
+}
+
+// Layer 1 (2 -> 32 channels, 9 taps, K = 2t + ci padded to 32) for one m-tile, its A
+// fragments read straight from the packed input rows: in the m16n8k16 layout lane
+// (g = lane / 4, c = lane % 4) holds rows g and g + 8 at k = 2c, 2c + 1 (tap c, both
+// channels: one packed row x0s[row + c]) and at k = 2c + 8, 2c + 9 (tap c + 4); the
+// second k-step holds tap 8 (lanes with c = 0) and zeros.  bw holds the B fragments
+// of W1 (two k-steps x four n-tiles), loaded once per warp.
+template <class EPI>
+__device__ __forceinline__ void conv1_warp(const uint32_t* x0s, const uint32_t (&bw)[16], int m0, int lane,
+                                           EPI epi) {
+  float acc[4][4];
+#pragma unroll
+  for (int n = 0; n < 4; ++n)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[n][q] = 0.0f;
+  const int g = lane >> 2, c = lane & 3;
+  const uint32_t* x = x0s + m0 + g;
+  const uint32_t a0[4] = {x[c], x[8 + c], x[4 + c], x[12 + c]};
+  const uint32_t t8a = x[8], t8b = x[16];
+  const uint32_t a1[4] = {c == 0 ? t8a : 0u, c == 0 ? t8b : 0u, 0u, 0u};
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    mma_bf16(acc[n], a0, bw[2 * n], bw[2 * n + 1]);
+    mma_bf16(acc[n], a1, bw[8 + 2 * n], bw[8 + 2 * n + 1]);
+  }
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    epi(m0 + g, n * 8 + 2 * c, acc[n][0], acc[n][1]);
+    epi(m0 + g + 8, n * 8 + 2 * c, acc[n][2], acc[n][3]);
+  }
+}
+
+// B fragments of W1 for conv1_warp: bw[2n], bw[2n + 1] the n-tile n of k-step 0,
+// bw[8 + 2n], bw[8 + 2n + 1] those of k-step 1
+__device__ __forceinline__ void load_w1_frags(const __nv_bfloat16* W1, int lane, uint32_t (&bw)[16]) {
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks) {
+    uint32_t b01[4], b23[4];
+    ldsm_x4(b01, b_pair_addr(W1, S32, 0, ks * 16, lane));
+    ldsm_x4(b23, b_pair_addr(W1, S32, 16, ks * 16, lane));
+    bw[8 * ks + 0] = b01[0];
+    bw[8 * ks + 1] = b01[1];
+    bw[8 * ks + 2] = b01[2];
+    bw[8 * ks + 3] = b01[3];
+    bw[8 * ks + 4] = b23[0];
+    bw[8 * ks + 5] = b23[1];
+    bw[8 * ks + 6] = b23[2];
+    bw[8 * ks + 7] = b23[3];
   }
 }
 
@@ -358,19 +416,37 @@ k6_net_forward(const uint8_t* __restrict__ packed, const float* __restrict__ in,
   tc::fence_after();
   const uint32_t tbase = tmem_slot;
   uint32_t phase = 0;
+  uint32_t bw1[16];
+  load_w1_frags(W1, lane, bw1);
+  // layer-2 operand descriptors: the start address sits in the low 14 bits (16-byte
+  // units, shared memory < 256 KB), so each MMA's descriptor is a base plus a constant
+  const uint64_t adesc0 = tc::desc(smem_u32(a1c), A1R * 16, 128);
+  const uint64_t bdesc0 = tc::desc(smem_u32(w2c), 32 * 16, 128);
 
-  for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const int slot = (int)(item / ntile), tile = (int)(item % ntile);
-    const int p0 = tile * FT;
-    __syncthreads();  // previous item's readers are done
-    load_x0(in + (size_t)slot * 2 * J, J, p0 - 12, F_X0, x0s);
-    __syncthreads();
-    build_a1col(x0s, F_A1, a2s);
-    __syncthreads();
-    // layer 1 (mma.sync): m-tiles warp, warp + 8, into the chunked a1
+  // Tile loop, software-pipelined: while the tensor cores run layer 2 of tile i, the
+  // warps run layer 3 of tile i - 1 (from a2s) and load the input rows of tile i + 1
+  // (into x0s, free once layer 1 of tile i is done).
+  const float b3 = bsm[64];
+  auto layer3 = [&](int s3, int q3) {
+    float* yo = y + (size_t)s3 * J;
+#pragma unroll 1
+    for (int mt = warp; mt < FT / 16; mt += 8)
+      conv_out_warp(a2s, W3, mt * 16, lane, [&](int r, float v) {
+        if (q3 + r < J) yo[q3 + r] = v + b3;
+      });
+  };
+  long long item = blockIdx.x;
+  int slot = (int)(item / ntile), p0 = (int)(item % ntile) * FT;
+  int prev_slot = -1, prev_p0 = 0;
+  bool stopped = false;
+  load_x0(in + (size_t)slot * 2 * J, J, p0 - 12, F_X0, x0s);
+  for (; item < nitems; item += gridDim.x) {
+    __syncthreads();  // x0s holds this tile's rows; a2s, a1c and TMEM are free
+    // layer 1 (mma.sync, A fragments from the packed input rows): m-tiles warp,
+    // warp + 8, into the chunked a1
 #pragma unroll 1
     for (int mt = warp; mt < F_A1 / 16; mt += 8)
-      conv_layer_warp<2, false>(a2s, S32, W1, S32, mt * 16, lane, [&](int r, int cc, float v0, float v1) {
+      conv1_warp(x0s, bw1, mt * 16, lane, [&](int r, int cc, float v0, float v1) {
         v0 += bsm[cc];
         v1 += bsm[cc + 1];
         gelu2(v0, v1);
@@ -382,19 +458,22 @@ k6_net_forward(const uint8_t* __restrict__ packed, const float* __restrict__ in,
     // layer 2 (tcgen05): one thread issues the 36 MMAs and commits them to mma_bar
     if (threadIdx.x == 0) {
       tc::fence_after();
-      const uint32_t a0 = smem_u32(a1c), b0 = smem_u32(w2c);
       constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
-#pragma unroll 1
+#pragma unroll
       for (int mb = 0; mb < 2; ++mb)
-#pragma unroll 1
+#pragma unroll
         for (int ks = 0; ks < 2 * KW; ++ks) {
           const int t = ks >> 1, h = ks & 1;
-          const uint64_t ad = tc::desc(a0 + (uint32_t)((2 * h) * A1R + 128 * mb + t) * 16, A1R * 16, 128);
-          const uint64_t bd = tc::desc(b0 + (uint32_t)(2 * ks) * 32 * 16, 32 * 16, 128);
+          const uint64_t ad = adesc0 + (uint64_t)((2 * h) * A1R + 128 * mb + t);
+          const uint64_t bd = bdesc0 + (uint64_t)(2 * ks * 32);
           tc::mma(tbase + 32 * mb, ad, bd, idesc, ks > 0 ? 1u : 0u);
         }
       tc::commit(smem_u32(&mma_bar));
     }
+    if (prev_slot >= 0) layer3(prev_slot, prev_p0);
+    const long long next = item + gridDim.x;
+    const int nslot = (int)(next / ntile), np0 = (int)(next % ntile) * FT;
+    if (next < nitems) load_x0(in + (size_t)nslot * 2 * J, J, np0 - 12, F_X0, x0s);
     // one thread waits on the barrier; the others sleep in the block barrier below
     bool late = false;
     if (threadIdx.x == 0) late = !tc::mbar_wait(smem_u32(&mma_bar), phase, wait_limit);
@@ -405,6 +484,7 @@ k6_net_forward(const uint8_t* __restrict__ packed, const float* __restrict__ in,
         (void)tc::mbar_wait(smem_u32(&mma_bar), phase, kNetMmaWait);
       }
       __syncthreads();
+      stopped = true;
       break;
     }
     phase ^= 1;
@@ -426,15 +506,14 @@ k6_net_forward(const uint8_t* __restrict__ packed, const float* __restrict__ in,
       for (int c = 0; c < 4; ++c) dst[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
     }
     tc::fence_before();
+    prev_slot = slot;
+    prev_p0 = p0;
+    slot = nslot;
+    p0 = np0;
+  }
+  if (!stopped && prev_slot >= 0) {
     __syncthreads();
-    // layer 3
-    float* yo = y + (size_t)slot * J;
-    const float b3 = bsm[64];
-#pragma unroll 1
-    for (int mt = warp; mt < FT / 16; mt += 8)
-      conv_out_warp(a2s, W3, mt * 16, lane, [&](int r, float v) {
-        if (p0 + r < J) yo[p0 + r] = v + b3;
-      });
+    layer3(prev_slot, prev_p0);
   }
   tc::fence_before();
   __syncthreads();
