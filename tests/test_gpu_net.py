@@ -183,6 +183,23 @@ def test_learned_with_zero_net_is_wiener_pcg(net_from):
     assert _rel(xl.cpu().numpy(), xw.cpu().numpy()) <= 1e-4
 
 
+@pytest.mark.parametrize("max_iter", [0, 3, 500])
+def test_learned_net_never_joining_is_wiener_pcg_bit_for_bit(max_iter):
+    """With net_from beyond the iterations any column takes (or beyond max_iter), the
+    learned solve never asks the net: every iteration runs in the on-chip CG kernel,
+    whose state goes through the hand-over, the flexible-CG finish and back to time
+    order.  Solution, iterations and both residuals equal Wiener-PCG's bit for bit."""
+    N, J = 64, 256
+    x, w, codes, scale, d, sig2, mask, prior = _instance(N, J, 32)
+    th = cuda(_theta(33, scale3=0.2, jitter=0.01).astype(np.float32))
+    args = (cuda(codes), cuda(scale), cuda(w.astype(np.float32)), sig2, cuda(mask), cuda(prior))
+    xw, itw, rw = ipfb.ml_solve(*args, precond="wiener", tol=1e-6, max_iter=max_iter)
+    xl, itl, rl = ipfb.ml_solve(*args, precond="learned", net=th, tol=1e-6, max_iter=max_iter, net_from=1000)
+    assert torch.equal(itl, itw), (itl.max(), itw.max())
+    assert torch.equal(xl, xw)
+    assert torch.equal(rl, rw)
+
+
 @pytest.mark.parametrize("N,J,net_from", [(64, 128, 0), (64, 512, 0), (64, 512, 3), (64, 1024, 1)])
 def test_learned_fcg_matches_oracle(N, J, net_from):
     """Learned FCG against the oracle's FCG with the BF16-emulating net; with
