@@ -752,7 +752,7 @@ int ml_solve_learned(const ipfb_geom* g, const uint8_t* codes, const float* scal
     MLParams wp = mp;
     wp.precond = 1;
     wp.max_iter = std::min(prm->net_from - 1, prm->max_iter);
-    CK(launch_k5_handover(J, d2, mask, prior, window, N, wp, b, prm->max_iter, s), "k5_ml_cg");
+    CK(launch_k5_handover(J, d2, mask, prior, window, N, wp, b, prm->max_iter, iters, resid, s), "k5_ml_cg");
     CK(launch_fcg_step(J, 3, d2, b, mask, prior, window, N, mp, cnt, s), "k5_fcg_step");
   } else {
     CK(launch_fcg_step(J, 0, d2, b, mask, prior, window, N, mp, cnt, s), "k5_fcg_step");

@@ -391,6 +391,7 @@ k5_fcg_finish(const float2* __restrict__ d2, float2* __restrict__ X, const uint8
   double* res = reinterpret_cast<double*>(sm_p + 2 * padded_len(J));
   float* part = reinterpret_cast<float*>(res + 8);
   const int tid = threadIdx.x, p = blockIdx.x, j0 = tid * EPT;
+  if (cs[2 * p].pad) return;  // finished in the on-chip CG kernel (solution and outputs written)
   float ta[NMAX], tb[NMAX];
   float2 a[RMAX + 1];
   load_taps_stencil<NT, RMAX>(window, N, p, mp.ntap, mp.inv_s2, ta, tb, a);

@@ -48,9 +48,9 @@ cudaError_t launch_k5(int J, const float2* d2, float2* x2, const uint8_t* mask, 
 
 cudaError_t launch_k5_handover(int J, const float2* d2, const uint8_t* mask, const float* prior,
                                const float* window, int N, const MLParams& mp, const FcgBufs& b, int fcg_max_iter,
-                               cudaStream_t st) {
+                               int* iters, float* resid, cudaStream_t st) {
   if (mp.ntap != 4 || !b.X) return cudaErrorNotSupported;
-  return k5_j<3, 1, 4>(J, d2, b.X, mask, prior, window, N, mp, nullptr, nullptr, b, fcg_max_iter, st);
+  return k5_j<3, 1, 4>(J, d2, b.X, mask, prior, window, N, mp, iters, resid, b, fcg_max_iter, st);
 }
 
 namespace {

@@ -175,9 +175,11 @@ cudaError_t launch_fcg_step(int J, int phase, const float2* d2, const FcgBufs& b
 // b.X in frame order when mp.use_x0) whose state is handed over to the flexible-CG
 // kernels: X, R, P, Z and the mask bits lane-interleaved, the per-column state in b.cs
 // (a column stays active below fcg_max_iter iterations); resumed by fcg step phase 3.
+// A pair with no active column is finished in the kernel instead: its solution in
+// frame order in b.X, its iters / resid entries written, b.cs marked done (pad = 1).
 cudaError_t launch_k5_handover(int J, const float2* d2, const uint8_t* mask, const float* prior,
                                const float* window, int N, const MLParams& mp, const FcgBufs& b, int fcg_max_iter,
-                               cudaStream_t st);
+                               int* iters, float* resid, cudaStream_t st);
 // device-side control of the learned solve's graph: the loop condition (a column still
 // active and fewer than max_trips trips) and the plain-CG fallback condition (a
 // non-finite residual among the 2 N values, or a net that gave up waiting)

@@ -66,7 +66,7 @@ struct FcgCol {
   int iters;
   int active;
   int slot;     // request slot of the current preconditioner application
-  int pad;
+  int pad;      // 1: the pair was finished in the on-chip CG kernel (hand-over)
 };
 
 struct NoScalars {
@@ -380,12 +380,26 @@ k5_ml_cg(const float2* __restrict__ d2, float2* __restrict__ x2, const uint8_t* 
     __syncthreads();  // publish sm_p before the next stencil
   }
 
-  if (ex.X) {
-    // Hand-over to the flexible-CG kernels (the learned solve runs its Wiener-only
-    // iterations here, on chip): x, r, the search direction p, z = M_W r of the last
-    // step and r.z, in their lane-interleaved layout (element e of thread t at
-    // p J + e T + t), with the mask bits and the per-column state.  A column stays
-    // active if it has not converged and has iterations left (ex_max_iter).
+  // Hand-over to the flexible-CG kernels (the learned solve runs its Wiener-only
+  // iterations here, on chip).  A column stays active there if it has not converged
+  // and has iterations left (ex_max_iter).  A pair with an active column hands over
+  // x, r, the search direction p, z = M_W r of the last step and r.z, in their
+  // lane-interleaved layout (element e of thread t at p J + e T + t), with the mask
+  // bits and the per-column state; a pair with none is finished here (solution in
+  // frame order, iterations and residuals written below) and marked done, so the
+  // flexible-CG kernels skip it.
+  const bool ex_done = ex.X && !((((int)st[4] & 1) && (int)st[11] < ex_max_iter) ||
+                                 (((int)st[4] & 2) && (int)st[12] < ex_max_iter));
+  if (ex.X && tid == 0 && ex_done) {
+    FcgCol ca = {}, cb = {};
+    ca.iters = (int)st[11];
+    cb.iters = (int)st[12];
+    ca.slot = cb.slot = -1;
+    ca.pad = cb.pad = 1;
+    ex.cs[2 * p] = ca;
+    ex.cs[2 * p + 1] = cb;
+  }
+  if (ex.X && !ex_done) {
     const size_t vb = (size_t)p * J + tid;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
