@@ -27,9 +27,14 @@ struct Variant {
 constexpr Variant kVariants[] = {{4, 256, 32, "c4_t256_r32"}, {4, 256, 16, "c4_t256_r16"}, {2, 256, 32, "c2_t256_r32"},
                                  {8, 256, 32, "c8_t256_r32"}, {1, 512, 32, "c1_t512_r32"}};
 constexpr int kNumVariants = 5;
-constexpr int kNumMClass = 5;  // M = 2048 .. 32768
+constexpr int kNumMClass = 5;   // power-of-two M = 2048 .. 32768, tuned among the variants
+constexpr int kNumOddClass = 2; // M = 5, 6 x 4096, one kernel each (kb3_v5.cu)
+constexpr int kNumClass = kNumMClass + kNumOddClass;
 
+bool odd_len(int M) { return M == 5 * 4096 || M == 6 * 4096; }
+int class_len(int c) { return c < kNumMClass ? (2048 << c) : (c - kNumMClass + 5) * 4096; }
 int mclass(int M) {
+  if (odd_len(M)) return kNumMClass + M / 4096 - 5;
   int c = 0;
   while ((2048 << c) < M) ++c;
   return c;
@@ -46,16 +51,16 @@ struct Plan {
   std::vector<ipfb_stream_desc> in;
   std::vector<BStream> st;
   std::vector<BItem> items2, items4;
-  std::vector<BItem> items3[kNumMClass];
+  std::vector<BItem> items3[kNumClass];
   std::vector<int> Js, Ms;
   std::vector<int> jidx;  // stream -> distinct J index
-  size_t off_streams = 0, off_items2 = 0, off_items4 = 0, off_items3[kNumMClass] = {}, off_counters = 0;
+  size_t off_streams = 0, off_items2 = 0, off_items4 = 0, off_items3[kNumClass] = {}, off_counters = 0;
   size_t off_Js = 0, off_Ms = 0, off_chirp_ptr = 0, off_bhat_ptr = 0;
   std::vector<size_t> off_chirp, off_bhat, off_d2;
   std::vector<float2*> chirp_ptr, bhat_ptr;  // device addresses of the tables, uploaded by prepare
   size_t total = 0;
   // defaults = the autotuner's choice on the 256-stream batch (M = 2048 .. 32768)
-  int variant[kNumMClass] = {0, 2, 2, 0, 3};
+  int variant[kNumMClass] = {0, 2, 2, 4, 3};
   const void* prepared_ws = nullptr;
   int normalize = 1;
 };
@@ -78,6 +83,17 @@ int next_pow2(int v) {
   return p;
 }
 
+// Bluestein convolution length of a J-point DFT: the smallest supported M >= 2J - 1,
+// a power of two or, above 16384, 5 or 6 x 4096 (a 7-CTA cluster for 28672 measured
+// twice the time per point of the 8-CTA one at 32768, so J > 12288 keeps 32768)
+int bluestein_len(int J) {
+  const int need = 2 * J - 1, p = next_pow2(need);
+  if (p > 16384)
+    for (int c = 5; c <= 6; ++c)
+      if (c * 4096 >= need && c * 4096 < p) return c * 4096;
+  return p;
+}
+
 void layout(Plan& P) {
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -88,7 +104,7 @@ void layout(Plan& P) {
   P.off_streams = take(P.st.size() * sizeof(BStream));
   P.off_items2 = take(P.items2.size() * sizeof(BItem));
   P.off_items4 = take(P.items4.size() * sizeof(BItem));
-  for (int c = 0; c < kNumMClass; ++c) P.off_items3[c] = take(std::max<size_t>(1, P.items3[c].size()) * sizeof(BItem));
+  for (int c = 0; c < kNumClass; ++c) P.off_items3[c] = take(std::max<size_t>(1, P.items3[c].size()) * sizeof(BItem));
   P.off_counters = take(16 * sizeof(int));
   P.off_Js = take(P.Js.size() * sizeof(int));
   P.off_Ms = take(P.Ms.size() * sizeof(int));
@@ -113,6 +129,8 @@ cudaError_t kb3_launch_v1(int, const BStream*, const BItem*, int, int*, cudaStre
 cudaError_t kb3_launch_v2(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb3_launch_v3(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb3_launch_v4(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb3_launch_odd(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb_bhat_odd_launch(const int*, const int*, const float2* const*, float2* const*, int, cudaStream_t);
 }  // namespace ipfb
 
 namespace {
@@ -125,6 +143,11 @@ int launch_kb3(const Plan& P, char* ws, int cls, int v, cudaStream_t stream) {
   int* ctr = reinterpret_cast<int*>(ws + P.off_counters) + 2 + cls;
   int nclusters = 0;
   cudaError_t e = cudaErrorInvalidValue;
+  if (cls >= kNumMClass) {
+    e = kb3_launch_odd(class_len(cls), s, it, (int)n, ctr, stream, &nclusters);
+    if (e != cudaSuccess) return fail(e, "kb3_columns");
+    return IPFB_OK;
+  }
   switch (v) {
     case 0: e = kb3_launch_v0(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
     case 1: e = kb3_launch_v1(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
@@ -160,7 +183,7 @@ int prepare(Plan& P, char* ws, cudaStream_t stream) {
   BCK(up(P.off_streams, P.st.data(), P.st.size() * sizeof(BStream)), "upload streams");
   BCK(up(P.off_items2, P.items2.data(), P.items2.size() * sizeof(BItem)), "upload items");
   BCK(up(P.off_items4, P.items4.data(), P.items4.size() * sizeof(BItem)), "upload items");
-  for (int c = 0; c < kNumMClass; ++c)
+  for (int c = 0; c < kNumClass; ++c)
     BCK(up(P.off_items3[c], P.items3[c].data(), P.items3[c].size() * sizeof(BItem)), "upload items");
   BCK(up(P.off_Js, P.Js.data(), P.Js.size() * sizeof(int)), "upload J");
   BCK(up(P.off_Ms, P.Ms.data(), P.Ms.size() * sizeof(int)), "upload M");
@@ -191,6 +214,10 @@ int prepare(Plan& P, char* ws, cudaStream_t stream) {
                            reinterpret_cast<float2* const*>(ws + P.off_bhat_ptr), nJ),
         "kb_bhat");
   }
+  if (std::any_of(P.Ms.begin(), P.Ms.end(), odd_len))
+    BCK(kb_bhat_odd_launch(dJ, dM, reinterpret_cast<const float2* const*>(ws + P.off_chirp_ptr),
+                           reinterpret_cast<float2* const*>(ws + P.off_bhat_ptr), nJ, stream),
+        "kb_bhat_s");
   P.prepared_ws = ws;
   return IPFB_OK;
 }
@@ -219,9 +246,9 @@ int run_all(Plan& P, char* ws, cudaStream_t stream, bool columns_only = false, i
                                                     (int)P.items2.size(), ctr + 0);
     BCK(cudaGetLastError(), "kb2_unpack");
   }
-  for (int c = 0; c < kNumMClass; ++c) {
+  for (int c = 0; c < kNumClass; ++c) {
     if (only_cls >= 0 && c != only_cls) continue;
-    const int v = only_v >= 0 ? only_v : P.variant[c];
+    const int v = c >= kNumMClass ? 0 : (only_v >= 0 ? only_v : P.variant[c]);
     int rc = launch_kb3(P, ws, c, v, stream);
     if (rc) return rc;
   }
@@ -268,7 +295,7 @@ extern "C" int ipfb_batched_plan(const ipfb_stream_desc* streams, int nstreams, 
     double c;
     BItem it;
   };
-  std::vector<Cost> c2, c3[kNumMClass], c4;
+  std::vector<Cost> c2, c3[kNumClass], c4;
   for (int s = 0; s < nstreams; ++s) {
     const ipfb_stream_desc& d = streams[s];
     if (!d.codes || !d.scale || !d.window || !d.x_out || (reinterpret_cast<uintptr_t>(d.codes) & 15)) {
@@ -284,7 +311,7 @@ extern "C" int ipfb_batched_plan(const ipfb_stream_desc* streams, int nstreams, 
     BStream b = {};
     b.N = d.lblock;
     b.J = d.nframes;
-    b.M = next_pow2(2 * d.nframes - 1);
+    b.M = bluestein_len(d.nframes);
     b.ntap = d.ntap;
     b.phi2 = (float)d.noise_level;
     b.gnorm = (d.noise_level > 0.0 && normalize) ? (float)(1.0 + d.noise_level) : 1.0f;
@@ -320,7 +347,7 @@ extern "C" int ipfb_batched_plan(const ipfb_stream_desc* streams, int nstreams, 
     return out;
   };
   P->items2 = sorted(c2);
-  for (int c = 0; c < kNumMClass; ++c) P->items3[c] = sorted(c3[c]);
+  for (int c = 0; c < kNumClass; ++c) P->items3[c] = sorted(c3[c]);
   P->items4 = sorted(c4);
   for (int c = 0; c < kNumMClass; ++c)
     if (!variant_ok(P->variant[c], 2048 << c)) P->variant[c] = 0;
@@ -404,6 +431,11 @@ extern "C" int ipfb_batched_autotune(void* plan, void* ws, size_t ws_bytes, void
 extern "C" int ipfb_batched_variant(void* plan, int M, char* name, size_t cap) {
   Plan* P = static_cast<Plan*>(plan);
   if (!P || !name || cap < 16 || M < 2048 || M > 32768) return IPFB_ERR_INVALID;
+  if (odd_len(M)) {
+    std::snprintf(name, cap, "c%d_t256_r32", M / 4096);
+    return IPFB_OK;
+  }
+  if (M & (M - 1)) return IPFB_ERR_INVALID;
   std::snprintf(name, cap, "%s", kVariants[P->variant[mclass(M)]].name);
   return IPFB_OK;
 }

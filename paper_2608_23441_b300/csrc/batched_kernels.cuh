@@ -367,6 +367,20 @@ struct Kb3Launch {
   }
 };
 
+// FFT_M(b) for the distinct J whose Bluestein length is exactly M = C * S (the odd
+// cluster lengths; the other J are left to kb_bhat)
+template <int C, int S, int T, int MAXR>
+__global__ void __launch_bounds__(T, 1)
+kb_bhat_s(const int* __restrict__ Js, const int* __restrict__ Ms, const float2* const* __restrict__ chirps,
+          float2* const* __restrict__ bhats, int nJ) {
+  extern __shared__ float2 smem[];
+  int r = 0;
+  if constexpr (C > 1) r = (int)cg::this_cluster().block_rank();
+  const int t = blockIdx.x / C;
+  if (t >= nJ || Ms[t] != C * S) return;  // uniform over the cluster
+  bhat_item<C, S, T, MAXR>(chirps[t], Js[t], bhats[t], smem, r);
+}
+
 template <int C, int T, int MAXR>
 __global__ void __launch_bounds__(T, 1)
 kb_bhat(const int* __restrict__ Js, const int* __restrict__ Ms, const float2* const* __restrict__ chirps,

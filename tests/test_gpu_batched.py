@@ -106,7 +106,7 @@ def test_batched_each_variant_matches_oracle(name):
     # one stream per Bluestein length class M = 4096 .. 32768, every class forced to
     # `name` through a tune cache (classes outside the variant's range, M / C in
     # [512, 8192] for a cluster and up to 16384 for one CTA, keep the default variant)
-    shapes = [(1024, 1031), (2048, 1500), (1024, 2310), (2048, 4099), (1024, 9000)]
+    shapes = [(1024, 1031), (2048, 1500), (1024, 2310), (2048, 4099), (1024, 15000)]
     streams, host = _streams(shapes, 700)
     C = VARIANTS[name]
     with tempfile.TemporaryDirectory() as d:
@@ -124,6 +124,26 @@ def test_batched_each_variant_matches_oracle(name):
     refs = obatched.ipfb_batched(host)
     for (N, J), x, ref in zip(shapes, xs, refs):
         assert relrms(x.cpu().numpy(), ref) < 1e-4, (name, N, J)
+    plan.close()
+
+
+def test_batched_odd_bluestein_lengths_match_oracle():
+    """Above J = 8192 the Bluestein length is the smallest of 5 x 4096, 6 x 4096 and
+    32768 that holds 2J - 1 (clusters of 5 and 6 CTAs with a direct C-point cross
+    stage): each stream still matches the oracle's exact J-point circulant inverse."""
+    shapes = [(1024, 8193), (2048, 10240), (1024, 10241), (1024, 12288), (1024, 12289)]
+    want_M = [20480, 20480, 24576, 24576, 32768]
+    for (_, J), M in zip(shapes, want_M):
+        assert M >= 2 * J - 1 and all(c * 4096 < 2 * J - 1 for c in (5, 6) if c * 4096 < M), (J, M)
+    streams, host = _streams(shapes, 800)
+    plan = ipfb.BatchedPlan(streams)
+    for c in (5, 6):
+        assert plan.variant(c * 4096) == f"c{c}_t256_r32"
+    xs = plan.run()
+    torch.cuda.synchronize()
+    refs = obatched.ipfb_batched(host)
+    for (N, J), x, ref in zip(shapes, xs, refs):
+        assert relrms(x.cpu().numpy(), ref) < 1e-4, (N, J)
     plan.close()
 
 
