@@ -400,7 +400,8 @@ int ipfb_ml_training_pairs(const ipfb_geom* g, const float* window, const ipfb_m
  * {1024, 2048, 4096}, any integer number of frames 1024 <= J <= 16384), each the
  * Wiener inverse of ipfb_wiener (Eq. decorrelation, Eq. wiener weights).  The
  * J-point column DFT for arbitrary J uses Bluestein's chirp-z identity with
- * power-of-two FFTs of length M = next_pow2(2J - 1) on thread-block clusters; the
+ * FFTs of length M on thread-block clusters, M the smallest of the powers of two,
+ * 20480 and 24576 that is >= 2J - 1 (the two non-powers of two only above 16384); the
  * work (spectra groups, column pairs, output tiles) is pulled from counters by
  * persistent kernels, longest items first.
  *
@@ -416,7 +417,8 @@ int ipfb_ml_training_pairs(const ipfb_geom* g, const float* window, const ipfb_m
  * in a CUDA graph and replayed.  ipfb_batched_autotune times every kernel
  * variant per M class on the plan's own work items, keeps the fastest, and
  * writes the choice to cache_path (if not NULL); it overwrites the outputs.
- * ipfb_batched_variant reports the variant chosen for M.  Stream descriptors:
+ * ipfb_batched_variant reports the variant chosen for M (a power of two from 2048
+ * to 32768, or 20480 / 24576, whose kernels are fixed).  Stream descriptors:
  * device pointers codes [J][N/2], scale [N/2+1], window [ntap][N], x_out [J*N].
  */
 typedef struct {
