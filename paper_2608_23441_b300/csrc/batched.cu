@@ -24,11 +24,13 @@ struct Variant {
   int C, T, MAXR;
   const char* name;
 };
+// (T = 0: S / 16 threads, for S = 512 .. 2048 only)
 constexpr Variant kVariants[] = {{4, 256, 32, "c4_t256_r32"}, {4, 256, 16, "c4_t256_r16"}, {2, 256, 32, "c2_t256_r32"},
-                                 {8, 256, 32, "c8_t256_r32"}, {1, 512, 32, "c1_t512_r32"}};
-constexpr int kNumVariants = 5;
+                                 {8, 256, 32, "c8_t256_r32"}, {1, 512, 32, "c1_t512_r32"}, {2, 0, 32, "c2_ts16_r32"},
+                                 {4, 0, 32, "c4_ts16_r32"}};
+constexpr int kNumVariants = 7;
 constexpr int kNumMClass = 5;   // power-of-two M = 2048 .. 32768, tuned among the variants
-constexpr int kNumOddClass = 2; // M = 5, 6 x 4096, one kernel each (kb3_v5.cu)
+constexpr int kNumOddClass = 2; // M = 5, 6 x 4096, one kernel each (kb3_odd.cu)
 constexpr int kNumClass = kNumMClass + kNumOddClass;
 
 bool odd_len(int M) { return M == 5 * 4096 || M == 6 * 4096; }
@@ -42,6 +44,7 @@ int mclass(int M) {
 // a CTA of a cluster holds up to 8192 elements (two buffers); a single CTA up to 16384 (one)
 bool variant_ok(int v, int M) {
   const int S = M / kVariants[v].C;
+  if (kVariants[v].T == 0) return S >= 512 && S <= 2048;
   return S <= (kVariants[v].C == 1 ? 16384 : 8192) && S >= 512;
 }
 
@@ -60,7 +63,7 @@ struct Plan {
   std::vector<float2*> chirp_ptr, bhat_ptr;  // device addresses of the tables, uploaded by prepare
   size_t total = 0;
   // defaults = the autotuner's choice on the 256-stream batch (M = 2048 .. 32768)
-  int variant[kNumMClass] = {0, 2, 2, 4, 3};
+  int variant[kNumMClass] = {0, 5, 2, 4, 0};
   const void* prepared_ws = nullptr;
   int normalize = 1;
 };
@@ -129,6 +132,8 @@ cudaError_t kb3_launch_v1(int, const BStream*, const BItem*, int, int*, cudaStre
 cudaError_t kb3_launch_v2(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb3_launch_v3(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb3_launch_v4(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb3_launch_v5(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb3_launch_v6(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb3_launch_odd(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb_bhat_odd_launch(const int*, const int*, const float2* const*, float2* const*, int, cudaStream_t);
 }  // namespace ipfb
@@ -154,6 +159,8 @@ int launch_kb3(const Plan& P, char* ws, int cls, int v, cudaStream_t stream) {
     case 2: e = kb3_launch_v2(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
     case 3: e = kb3_launch_v3(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
     case 4: e = kb3_launch_v4(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
+    case 5: e = kb3_launch_v5(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
+    case 6: e = kb3_launch_v6(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
   }
   if (e != cudaSuccess) return fail(e, "kb3_columns");
   return IPFB_OK;

@@ -165,10 +165,13 @@ __device__ __forceinline__ void column_item(const BStream& st, int p, float2* sm
   } else {
     __syncthreads();
   }
-  // 3. pair split + gain: partner -k mod J lives in CTA (-k mod J) % C; X'[k] goes to
-  //    the second buffer sm2 so that partners still read unmodified X.  One CTA (C = 1)
-  //    holds both modes of every pair, so one thread splits k and J - k in place.
-  float2* sm2 = sm + padded_len(S);
+  // 3. pair split + gain: partner -k mod J lives in CTA (-k mod J) % C, so X'[k] may
+  //    overwrite X only once every partner read is done.  S >= 4096: X'[k] stays in
+  //    registers across a cluster barrier, then goes in place (one buffer, two CTAs per
+  //    SM at S = 8192); smaller S: it goes to a second buffer sm2 (holding 8 or more
+  //    values per thread across the rare out-of-line FP64 gain call spills there).  One
+  //    CTA (C = 1) holds both modes of every pair, so one thread splits k and J - k in
+  //    place.
   float ta[4], tb[4];
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
@@ -197,33 +200,61 @@ __device__ __forceinline__ void column_item(const BStream& st, int p, float2* sm
 #pragma unroll 1
     for (int k = J + threadIdx.x; k < S; k += T) sm[pidx(k)] = make_float2(0.0f, 0.0f);  // zero padding
     __syncthreads();
-  } else {
+  } else if constexpr (S < 4096) {
+    float2* sm2 = sm + padded_len(S);
 #pragma unroll 1
-  for (int m = threadIdx.x; m < S; m += T) {
-    const int k = C * m + r;
-    float2 xk = make_float2(0.0f, 0.0f);
-    if (k < J) {
-      const int km = (k == 0) ? 0 : J - k;
-      const float2* src = sm;
-      if constexpr (C > 1) src = cg::this_cluster().map_shared_rank(sm, km % C);
-      float2 zm = src[pidx(km / C)];
-      xk = sm[pidx(m)];
-      const float2 e1 = twiddle<false>(k, J);
-      const float2 ga = gain_at<4>(ta, k, e1, gp), gb = gain_at<4>(tb, k, e1, gp);
-      split_gain(xk, zm, ga, gb);
-      // 4. the inverse transform's input: a'[k] = conj(X'[k]) w[k]
-      xk = cmul(cconj(xk), __ldg(w + k));
+    for (int m = threadIdx.x; m < S; m += T) {
+      const int k = C * m + r;
+      float2 xk = make_float2(0.0f, 0.0f);
+      if (k < J) {
+        const int km = (k == 0) ? 0 : J - k;
+        const float2* src = cg::this_cluster().map_shared_rank(sm, km % C);
+        float2 zm = src[pidx(km / C)];
+        xk = sm[pidx(m)];
+        const float2 e1 = twiddle<false>(k, J);
+        const float2 ga = gain_at<4>(ta, k, e1, gp), gb = gain_at<4>(tb, k, e1, gp);
+        split_gain(xk, zm, ga, gb);
+        xk = cmul(cconj(xk), __ldg(w + k));  // 4. a'[k] = conj(X'[k]) w[k]
+      }
+      sm2[pidx(m)] = xk;
     }
-    sm2[pidx(m)] = xk;
-  }
-  if constexpr (C > 1) {
     cg::this_cluster().sync();
-  } else {
-    __syncthreads();
-  }
 #pragma unroll 1
-  for (int m = threadIdx.x; m < S; m += T) sm[pidx(m)] = sm2[pidx(m)];
-  __syncthreads();
+    for (int m = threadIdx.x; m < S; m += T) sm[pidx(m)] = sm2[pidx(m)];
+    __syncthreads();
+  } else {
+    constexpr int PER = (S + T - 1) / T;
+    float2 xo[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int m = threadIdx.x + i * T;
+      const int k = C * m + r;
+      float2 xk = make_float2(0.0f, 0.0f);
+      if (m < S && k < J) {
+        const int km = (k == 0) ? 0 : J - k;
+        const float2* src = sm;
+        if constexpr (C > 1) src = cg::this_cluster().map_shared_rank(sm, km % C);
+        float2 zm = src[pidx(km / C)];
+        xk = sm[pidx(m)];
+        const float2 e1 = twiddle<false>(k, J);
+        const float2 ga = gain_at<4>(ta, k, e1, gp), gb = gain_at<4>(tb, k, e1, gp);
+        split_gain(xk, zm, ga, gb);
+        // 4. the inverse transform's input: a'[k] = conj(X'[k]) w[k]
+        xk = cmul(cconj(xk), __ldg(w + k));
+      }
+      xo[i] = xk;
+    }
+    if constexpr (C > 1) {
+      cg::this_cluster().sync();  // every CTA has read its partners' unmodified X
+    } else {
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int m = threadIdx.x + i * T;
+      if (m < S) sm[pidx(m)] = xo[i];
+    }
+    __syncthreads();
   }
   conv_engine<C, S, T, MAXR, false>(sm, st.bhat, nullptr, r);
   // 5. x[j] = conj(w[j] conv'[j] / M)
@@ -290,7 +321,8 @@ kb2_unpack(const BStream* __restrict__ streams, const BItem* __restrict__ items,
 #endif  // IPFB_BATCHED_HOST_KERNELS
 
 // kb3: columns (4-tap windows); a cluster of C CTAs per item, M = C * S with S
-// picked per item.  Dynamic smem: two padded S = 8192 buffers.
+// picked per item.  Dynamic smem: one padded S-element buffer (two for a cluster
+// with S < 4096).
 // One launch per M class: every item of the class has M = C * S, so each kernel is
 // specialised to its S (one kernel switching over all S was register-allocated for
 // the largest and spilled ~3.7 KB per thread), and limited to 128 registers so two
@@ -318,14 +350,15 @@ kb3_columns(const BStream* __restrict__ streams, const BItem* __restrict__ items
 }
 
 // Launch of the class-M kernel of one variant: a persistent grid of as many clusters
-// as fit, each CTA with 2 S padded elements of shared memory (data + partner buffer).
+// as fit, each CTA with S padded elements of shared memory.
 template <int C, int T, int MAXR>
 struct Kb3Launch {
   template <int S>
   static cudaError_t go(const BStream* s, const BItem* it, int n, int* ctr, cudaStream_t stream, int* nclusters) {
     auto kern = kb3_columns<C, S, T, MAXR>;
-    // one buffer for a single CTA (the pair split runs in place), two for a cluster
-    const size_t smem = (C == 1 ? 1 : 2) * (size_t)padded_len(S) * sizeof(float2);
+    // one buffer (the pair split in place: one CTA, or across a cluster barrier for
+    // S >= 4096), two for a cluster with S < 4096 (the split through a second buffer)
+    const size_t smem = (C > 1 && S < 4096 ? 2 : 1) * (size_t)padded_len(S) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -362,6 +395,22 @@ struct Kb3Launch {
       case 2048: return go<2048>(s, it, n, ctr, stream, nclusters);
       case 4096: return go<4096>(s, it, n, ctr, stream, nclusters);
       case 8192: return go<8192>(s, it, n, ctr, stream, nclusters);
+    }
+    return cudaErrorNotSupported;
+  }
+};
+
+// Variants whose thread count follows S (16 elements per thread, S = 512 .. 2048): with
+// 256 threads those small runs hold 8 or fewer elements per thread and the kernel
+// spills about 900 bytes per thread; with S / 16 threads it does not.
+template <int C, int MAXR>
+struct Kb3LaunchAutoT {
+  static cudaError_t launch(int M, const BStream* s, const BItem* it, int n, int* ctr, cudaStream_t stream,
+                            int* nclusters) {
+    switch (M / C) {
+      case 512: return Kb3Launch<C, 32, MAXR>::template go<512>(s, it, n, ctr, stream, nclusters);
+      case 1024: return Kb3Launch<C, 64, MAXR>::template go<1024>(s, it, n, ctr, stream, nclusters);
+      case 2048: return Kb3Launch<C, 128, MAXR>::template go<2048>(s, it, n, ctr, stream, nclusters);
     }
     return cudaErrorNotSupported;
   }

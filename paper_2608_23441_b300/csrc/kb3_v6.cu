@@ -1,0 +1,10 @@
+// Batched column kernel, variant 6: cluster of 4, S / 16 threads (S = 512 .. 2048),
+// radix <= 32; one kernel per M class.
+#include "batched_kernels.cuh"
+
+namespace ipfb {
+cudaError_t kb3_launch_v6(int M, const BStream* s, const BItem* it, int n, int* ctr, cudaStream_t stream,
+                          int* nclusters) {
+  return Kb3LaunchAutoT<4, 32>::launch(M, s, it, n, ctr, stream, nclusters);
+}
+}  // namespace ipfb

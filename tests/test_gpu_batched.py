@@ -23,11 +23,15 @@ SHAPES = [(1024, 1031), (2048, 1500), (4096, 1024), (1024, 2310), (2048, 4099), 
 
 
 # column-kernel variants (cluster size, threads, largest radix) and their cluster sizes
-VARIANTS = {"c4_t256_r32": 4, "c4_t256_r16": 4, "c2_t256_r32": 2, "c8_t256_r32": 8, "c1_t512_r32": 1}
+VARIANTS = {"c4_t256_r32": 4, "c4_t256_r16": 4, "c2_t256_r32": 2, "c8_t256_r32": 8, "c1_t512_r32": 1,
+            "c2_ts16_r32": 2, "c4_ts16_r32": 4}
 
 
-def _in_range(M, C):
-    # a CTA of a cluster holds up to 8192 elements, a single CTA up to 16384
+def _in_range(M, C, name=""):
+    # a CTA of a cluster holds up to 8192 elements, a single CTA up to 16384; the
+    # "ts16" variants (S / 16 threads) serve S = 512 .. 2048
+    if "ts16" in name:
+        return 512 <= M // C <= 2048
     return 512 <= M // C <= (16384 if C == 1 else 8192)
 
 
@@ -117,7 +121,7 @@ def test_batched_each_variant_matches_oracle(name):
         plan = ipfb.BatchedPlan(streams, tune_cache=cache)
         for c in range(5):
             M = 2048 << c
-            if _in_range(M, C):
+            if _in_range(M, C, name):
                 assert plan.variant(M) == name, M
     xs = plan.run()
     torch.cuda.synchronize()
