@@ -53,11 +53,11 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 struct Plan {
   std::vector<ipfb_stream_desc> in;
   std::vector<BStream> st;
-  std::vector<BItem> items2, items4;
+  std::vector<BItem> items2[6], items4;  // items2: full items by lblock 1024, 2048, 4096, then the short ones
   std::vector<BItem> items3[kNumClass];
   std::vector<int> Js, Ms;
   std::vector<int> jidx;  // stream -> distinct J index
-  size_t off_streams = 0, off_items2 = 0, off_items4 = 0, off_items3[kNumClass] = {}, off_counters = 0;
+  size_t off_streams = 0, off_items2[6] = {}, off_items4 = 0, off_items3[kNumClass] = {}, off_counters = 0;
   size_t off_Js = 0, off_Ms = 0, off_chirp_ptr = 0, off_bhat_ptr = 0;
   std::vector<size_t> off_chirp, off_bhat, off_d2;
   std::vector<float2*> chirp_ptr, bhat_ptr;  // device addresses of the tables, uploaded by prepare
@@ -105,7 +105,7 @@ void layout(Plan& P) {
     return at;
   };
   P.off_streams = take(P.st.size() * sizeof(BStream));
-  P.off_items2 = take(P.items2.size() * sizeof(BItem));
+  for (int q = 0; q < 6; ++q) P.off_items2[q] = take(std::max<size_t>(1, P.items2[q].size()) * sizeof(BItem));
   P.off_items4 = take(P.items4.size() * sizeof(BItem));
   for (int c = 0; c < kNumClass; ++c) P.off_items3[c] = take(std::max<size_t>(1, P.items3[c].size()) * sizeof(BItem));
   P.off_counters = take(16 * sizeof(int));
@@ -188,7 +188,8 @@ int prepare(Plan& P, char* ws, cudaStream_t stream) {
     return cudaMemcpyAsync(ws + off, src, bytes, cudaMemcpyHostToDevice, stream);
   };
   BCK(up(P.off_streams, P.st.data(), P.st.size() * sizeof(BStream)), "upload streams");
-  BCK(up(P.off_items2, P.items2.data(), P.items2.size() * sizeof(BItem)), "upload items");
+  for (int q = 0; q < 6; ++q)
+    BCK(up(P.off_items2[q], P.items2[q].data(), P.items2[q].size() * sizeof(BItem)), "upload items");
   BCK(up(P.off_items4, P.items4.data(), P.items4.size() * sizeof(BItem)), "upload items");
   for (int c = 0; c < kNumClass; ++c)
     BCK(up(P.off_items3[c], P.items3[c].data(), P.items3[c].size() * sizeof(BItem)), "upload items");
@@ -229,29 +230,39 @@ int prepare(Plan& P, char* ws, cudaStream_t stream) {
   return IPFB_OK;
 }
 
-size_t kb2_smem() {
-  auto one = [](size_t F, size_t H) {
-    return ((size_t)F * k2_frame_stride((int)H) + 256) * sizeof(float2) + F * H + (H + 4) * sizeof(float);
-  };
-  return std::max(one(16, 512), std::max(one(8, 1024), one(4, 2048)));
+// kb2 for the streams of lblock 2H: F spectra of TPF threads per CTA, items list q,
+// counter ctr
+template <int H, int TPF, int F, bool FULL>
+int launch_kb2(const Plan& P, char* ws, int q, int* ctr, cudaStream_t stream) {
+  const size_t n = P.items2[q].size();
+  if (n == 0) return IPFB_OK;
+  auto kern = kb2_unpack<H, TPF, F, FULL>;
+  const size_t smem = ((size_t)F * k2_frame_stride(H) + 256) * sizeof(float2) + (size_t)F * H + (H + 4) * sizeof(float);
+  BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "kb2 smem");
+  int per_sm = 0, dev = 0, nsm = 0;
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPF * F, smem), "kb2 occ");
+  BCK(cudaGetDevice(&dev), "device");
+  BCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "sm count");
+  const int grid = (int)std::min<size_t>(n, (size_t)std::max(1, per_sm) * nsm);
+  kern<<<grid, TPF * F, smem, stream>>>(reinterpret_cast<const BStream*>(ws + P.off_streams),
+                                        reinterpret_cast<const BItem*>(ws + P.off_items2[q]), (int)n, ctr);
+  BCK(cudaGetLastError(), "kb2_unpack");
+  return IPFB_OK;
 }
 
 int run_all(Plan& P, char* ws, cudaStream_t stream, bool columns_only = false, int only_cls = -1, int only_v = -1) {
   int* ctr = reinterpret_cast<int*>(ws + P.off_counters);
   BCK(cudaMemsetAsync(ctr, 0, 16 * sizeof(int), stream), "counters");
   const BStream* s = reinterpret_cast<const BStream*>(ws + P.off_streams);
-  if (!columns_only && !P.items2.empty()) {
-    const size_t smem = kb2_smem();
-    BCK(cudaFuncSetAttribute(kb2_unpack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "kb2 smem");
-    int per_sm = 0;
-    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb2_unpack, kKb2Threads, smem), "kb2 occ");
-    int dev = 0, nsm = 0;
-    BCK(cudaGetDevice(&dev), "device");
-    BCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "sm count");
-    const int grid = (int)std::min<size_t>(P.items2.size(), (size_t)std::max(1, per_sm) * nsm);
-    kb2_unpack<<<grid, kKb2Threads, smem, stream>>>(s, reinterpret_cast<const BItem*>(ws + P.off_items2),
-                                                    (int)P.items2.size(), ctr + 0);
-    BCK(cudaGetLastError(), "kb2_unpack");
+  if (!columns_only) {
+    // counters: 1 kb4, 2 + class kb3, 10 .. 15 kb2 (full items by lblock, then short)
+    int rc = launch_kb2<512, 32, 16, true>(P, ws, 0, ctr + 10, stream);
+    if (!rc) rc = launch_kb2<1024, 64, 8, true>(P, ws, 1, ctr + 11, stream);
+    if (!rc) rc = launch_kb2<2048, 128, 4, true>(P, ws, 2, ctr + 12, stream);
+    if (!rc) rc = launch_kb2<512, 32, 16, false>(P, ws, 3, ctr + 13, stream);
+    if (!rc) rc = launch_kb2<1024, 64, 8, false>(P, ws, 4, ctr + 14, stream);
+    if (!rc) rc = launch_kb2<2048, 128, 4, false>(P, ws, 5, ctr + 15, stream);
+    if (rc) return rc;
   }
   for (int c = 0; c < kNumClass; ++c) {
     if (only_cls >= 0 && c != only_cls) continue;
@@ -302,7 +313,7 @@ extern "C" int ipfb_batched_plan(const ipfb_stream_desc* streams, int nstreams, 
     double c;
     BItem it;
   };
-  std::vector<Cost> c2, c3[kNumClass], c4;
+  std::vector<Cost> c2[6], c3[kNumClass], c4;
   for (int s = 0; s < nstreams; ++s) {
     const ipfb_stream_desc& d = streams[s];
     if (!d.codes || !d.scale || !d.window || !d.x_out || (reinterpret_cast<uintptr_t>(d.codes) & 15)) {
@@ -340,7 +351,8 @@ extern "C" int ipfb_batched_plan(const ipfb_stream_desc* streams, int nstreams, 
     P->jidx.push_back(ji);
     P->st.push_back(b);
     const int F = 8192 / (b.N / 2) >= 16 ? 16 : 8192 / (b.N / 2);
-    for (int j0 = 0; j0 < b.J; j0 += F) c2.push_back({(double)b.N, {s, j0}});
+    const int q = b.N == 1024 ? 0 : (b.N == 2048 ? 1 : 2);
+    for (int j0 = 0; j0 < b.J; j0 += F) c2[j0 + F <= b.J ? q : q + 3].push_back({(double)b.N, {s, j0}});
     const int cls = mclass(b.M);
     for (int p = 0; p < b.N / 2; ++p) c3[cls].push_back({(double)b.M, {s, p}});
     const int ntp = (b.N / 2 + 31) / 32, ntj = (b.J + 63) / 64;
@@ -353,7 +365,7 @@ extern "C" int ipfb_batched_plan(const ipfb_stream_desc* streams, int nstreams, 
     for (auto& c : v) out.push_back(c.it);
     return out;
   };
-  P->items2 = sorted(c2);
+  for (int q = 0; q < 6; ++q) P->items2[q] = sorted(c2[q]);
   for (int c = 0; c < kNumClass; ++c) P->items3[c] = sorted(c3[c]);
   P->items4 = sorted(c4);
   for (int c = 0; c < kNumMClass; ++c)

@@ -289,11 +289,17 @@ __device__ __forceinline__ int fetch_item_cluster(int* counter, int* slot, int r
   }
 }
 
-// kb2: unpack + per-frame inverse real FFT for every stream (lblock 1024/2048/4096)
+// kb2: unpack + per-frame inverse real FFT, one kernel per lblock N = 2H (the items of
+// the streams of that lblock; F spectra of TPF threads each per item, as k2), so each
+// is register-allocated for its own shape (one kernel switching over the three took
+// 128 registers and spilled).  FULL: items of exactly F spectra (the group size is a
+// compile-time constant, as in k2); otherwise the last, shorter item of each stream.
 constexpr int kKb2Threads = 512;
 #ifdef IPFB_BATCHED_HOST_KERNELS
-__global__ void __launch_bounds__(kKb2Threads)
+template <int H, int TPF, int F, bool FULL>
+__global__ void __launch_bounds__(TPF* F, (H == 512 ? 1 : 2))
 kb2_unpack(const BStream* __restrict__ streams, const BItem* __restrict__ items, int nitems, int* counter) {
+  static_assert(TPF * F == kKb2Threads, "512 threads");
   extern __shared__ float2 smem[];
   __shared__ int slot;
   for (int guard = 0; guard < nitems + 1; ++guard) {
@@ -301,19 +307,8 @@ kb2_unpack(const BStream* __restrict__ streams, const BItem* __restrict__ items,
     if (it >= nitems) break;
     const BItem item = items[it];
     const BStream& st = streams[item.s];
-    switch (st.N) {
-      case 1024:
-        k2_group<512, 32, 16>(st.codes, st.scale, st.d2, 1, st.J, 0, item.a, min(16, st.J - item.a), smem);
-        break;
-      case 2048:
-        k2_group<1024, 64, 8>(st.codes, st.scale, st.d2, 1, st.J, 0, item.a, min(8, st.J - item.a), smem);
-        break;
-      case 4096:
-        k2_group<2048, 128, 4>(st.codes, st.scale, st.d2, 1, st.J, 0, item.a, min(4, st.J - item.a), smem);
-        break;
-      default:
-        break;
-    }
+    if (st.N == 2 * H)  // always true within the list
+      k2_group<H, TPF, F>(st.codes, st.scale, st.d2, 1, st.J, 0, item.a, FULL ? F : min(F, st.J - item.a), smem);
     __syncthreads();
   }
 }
