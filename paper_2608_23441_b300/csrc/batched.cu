@@ -19,16 +19,17 @@ using namespace ipfb;
 
 namespace {
 
-// kb3 variants the autotuner chooses between: cluster size, threads, max radix
+// kb3 variants the autotuner chooses between: cluster size, threads (0: S / 16), max
+// radix, and the run lengths S = M / C each serves
 struct Variant {
-  int C, T, MAXR;
+  int C, T, MAXR, smin, smax;
   const char* name;
 };
-// (T = 0: S / 16 threads, for S = 512 .. 2048 only)
-constexpr Variant kVariants[] = {{4, 256, 32, "c4_t256_r32"}, {4, 256, 16, "c4_t256_r16"}, {2, 256, 32, "c2_t256_r32"},
-                                 {8, 256, 32, "c8_t256_r32"}, {1, 512, 32, "c1_t512_r32"}, {2, 0, 32, "c2_ts16_r32"},
-                                 {4, 0, 32, "c4_ts16_r32"}};
-constexpr int kNumVariants = 7;
+constexpr Variant kVariants[] = {{4, 256, 32, 512, 8192, "c4_t256_r32"},  {4, 256, 16, 512, 8192, "c4_t256_r16"},
+                                 {2, 256, 32, 512, 8192, "c2_t256_r32"},  {8, 256, 32, 512, 8192, "c8_t256_r32"},
+                                 {1, 512, 32, 512, 16384, "c1_t512_r32"}, {2, 0, 32, 512, 2048, "c2_ts16_r32"},
+                                 {4, 0, 32, 512, 2048, "c4_ts16_r32"},    {2, 512, 32, 16384, 16384, "c2_t512_r32"}};
+constexpr int kNumVariants = 8;
 constexpr int kNumMClass = 5;   // power-of-two M = 2048 .. 32768, tuned among the variants
 constexpr int kNumOddClass = 2; // M = 5, 6 x 4096, one kernel each (kb3_odd.cu)
 constexpr int kNumClass = kNumMClass + kNumOddClass;
@@ -44,8 +45,7 @@ int mclass(int M) {
 // a CTA of a cluster holds up to 8192 elements (two buffers); a single CTA up to 16384 (one)
 bool variant_ok(int v, int M) {
   const int S = M / kVariants[v].C;
-  if (kVariants[v].T == 0) return S >= 512 && S <= 2048;
-  return S <= (kVariants[v].C == 1 ? 16384 : 8192) && S >= 512;
+  return S >= kVariants[v].smin && S <= kVariants[v].smax;
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -63,7 +63,7 @@ struct Plan {
   std::vector<float2*> chirp_ptr, bhat_ptr;  // device addresses of the tables, uploaded by prepare
   size_t total = 0;
   // defaults = the autotuner's choice on the 256-stream batch (M = 2048 .. 32768)
-  int variant[kNumMClass] = {0, 5, 2, 4, 0};
+  int variant[kNumMClass] = {0, 5, 2, 4, 7};
   const void* prepared_ws = nullptr;
   int normalize = 1;
 };
@@ -134,6 +134,7 @@ cudaError_t kb3_launch_v3(int, const BStream*, const BItem*, int, int*, cudaStre
 cudaError_t kb3_launch_v4(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb3_launch_v5(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb3_launch_v6(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb3_launch_v7(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb3_launch_odd(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb_bhat_odd_launch(const int*, const int*, const float2* const*, float2* const*, int, cudaStream_t);
 }  // namespace ipfb
@@ -161,6 +162,7 @@ int launch_kb3(const Plan& P, char* ws, int cls, int v, cudaStream_t stream) {
     case 4: e = kb3_launch_v4(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
     case 5: e = kb3_launch_v5(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
     case 6: e = kb3_launch_v6(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
+    case 7: e = kb3_launch_v7(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
   }
   if (e != cudaSuccess) return fail(e, "kb3_columns");
   return IPFB_OK;

@@ -323,7 +323,7 @@ kb2_unpack(const BStream* __restrict__ streams, const BItem* __restrict__ items,
 // the largest and spilled ~3.7 KB per thread), and limited to 128 registers so two
 // CTAs share an SM (measured faster than one CTA with 255 registers).
 template <int C, int S, int T, int MAXR>
-__global__ void __launch_bounds__(T, (C == 1 ? 1 : 2))
+__global__ void __launch_bounds__(T, (C == 1 || S > 8192 ? 1 : 2))
 kb3_columns(const BStream* __restrict__ streams, const BItem* __restrict__ items, int nitems, int* counter) {
   extern __shared__ float2 smem[];
   (void)counter;

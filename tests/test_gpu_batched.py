@@ -24,7 +24,7 @@ SHAPES = [(1024, 1031), (2048, 1500), (4096, 1024), (1024, 2310), (2048, 4099), 
 
 # column-kernel variants (cluster size, threads, largest radix) and their cluster sizes
 VARIANTS = {"c4_t256_r32": 4, "c4_t256_r16": 4, "c2_t256_r32": 2, "c8_t256_r32": 8, "c1_t512_r32": 1,
-            "c2_ts16_r32": 2, "c4_ts16_r32": 4}
+            "c2_ts16_r32": 2, "c4_ts16_r32": 4, "c2_t512_r32": 2}
 
 
 def _in_range(M, C, name=""):
@@ -32,6 +32,8 @@ def _in_range(M, C, name=""):
     # "ts16" variants (S / 16 threads) serve S = 512 .. 2048
     if "ts16" in name:
         return 512 <= M // C <= 2048
+    if name == "c2_t512_r32":
+        return M // C == 16384
     return 512 <= M // C <= (16384 if C == 1 else 8192)
 
 
