@@ -214,7 +214,7 @@ __device__ __forceinline__ uint8_t pack2(int lo, int hi) {
 
 // Pass B: recompute spectra, quantize, pack (and optionally write spectra).
 template <int H, int TPF, int F, int NT>
-__global__ void __launch_bounds__(TPF* F)
+__global__ void __launch_bounds__(TPF* F, 2)
 k1_pfb_quant(const float* __restrict__ x, const float* __restrict__ window, int ntap, int J,
              const float* __restrict__ scale, uint8_t* __restrict__ codes, float2* __restrict__ spectra) {
   extern __shared__ float2 smem[];
