@@ -115,7 +115,7 @@ __device__ __forceinline__ void rfft_post(const float2* sm, int H, int k, const 
 // Pass A: per-channel sums of Re^2 and Im^2 over all spectra (FP64 atomics at the
 // end of each CTA).  CTA processes frames blockIdx.x*F + f, stepping gridDim.x*F.
 template <int H, int TPF, int F, int NT>
-__global__ void __launch_bounds__(TPF* F)
+__global__ void __launch_bounds__(TPF* F, 2)
 k1_pfb_power(const float* __restrict__ x, const float* __restrict__ window, int ntap, int J,
              double* __restrict__ sums /* [2][H+1] */) {
   extern __shared__ float2 smem[];
