@@ -61,6 +61,30 @@ __global__ void kb_chirp(const int* __restrict__ Js, float2* const* __restrict__
 
 #endif  // IPFB_BATCHED_HOST_KERNELS
 
+// C-point DFT of the cluster cross stage: the radix-2 form of DFT<C> for a power of
+// two, otherwise (the 5- and 6-CTA clusters) the direct sum out[k] = sum_j v[j] W_C^{jk}
+// with j k reduced mod C at compile time.
+template <int R, bool INV, int K, int... Js>
+__device__ __forceinline__ float2 direct_dft_term(const float2* v, std::integer_sequence<int, Js...>) {
+  float2 acc = v[0];
+  ((acc = cadd(acc, rot_const<((Js + 1) * K) % R, R, INV>(v[Js + 1]))), ...);
+  return acc;
+}
+template <int R, bool INV, int... Ks>
+__device__ __forceinline__ void direct_dft(float2* v, std::integer_sequence<int, Ks...>) {
+  float2 out[R];
+  ((out[Ks] = direct_dft_term<R, INV, Ks>(v, std::make_integer_sequence<int, R - 1>{})), ...);
+#pragma unroll
+  for (int k = 0; k < R; ++k) v[k] = out[k];
+}
+template <int R, bool INV>
+__device__ __forceinline__ void cluster_dft(float2* v) {
+  if constexpr ((R & (R - 1)) == 0)
+    DFT<R, INV>::run(v);
+  else
+    direct_dft<R, INV>(v, std::make_integer_sequence<int, R>{});
+}
+
 // ---------------------------------------------------------------- cluster engine
 // In: this CTA's S values a[C m + r] at sm[pidx(m)].  Out (CONV): the unnormalised
 // circular convolution (a (*) b)[C m + r] * M at sm[pidx(m)], with bhat = FFT_M(b).
@@ -90,7 +114,7 @@ __device__ __forceinline__ void conv_engine(float2* sm, const float2* __restrict
     if constexpr (C > 1) {
 #pragma unroll
       for (int q = 1; q < C; ++q) z[q] = cmul(z[q], w0[q]);
-      DFT<C, false>::run(z);
+      cluster_dft<C, false>(z);
     }
     if constexpr (FWD_ONLY) {
 #pragma unroll
@@ -99,7 +123,7 @@ __device__ __forceinline__ void conv_engine(float2* sm, const float2* __restrict
 #pragma unroll
       for (int ka = 0; ka < C; ++ka) z[ka] = cmul(z[ka], __ldg(bhat + kb + S * ka));
       if constexpr (C > 1) {
-        DFT<C, true>::run(z);
+        cluster_dft<C, true>(z);
 #pragma unroll
         for (int q = 1; q < C; ++q) z[q] = cmul(z[q], cconj(w0[q]));
       }

@@ -196,31 +196,11 @@ __device__ __forceinline__ void dif_stages(float2* v) {
   }
 }
 
-// R not a power of two (the 3-, 5-, 6- and 7-CTA cluster stages): the direct sum
-//   out[k] = sum_j v[j] W_R^{j k},  j k reduced mod R at compile time.
-template <int R, bool INV, int K, int... Js>
-__device__ __forceinline__ float2 direct_dft_term(const float2* v, std::integer_sequence<int, Js...>) {
-  float2 acc = v[0];
-  ((acc = cadd(acc, rot_const<((Js + 1) * K) % R, R, INV>(v[Js + 1]))), ...);
-  return acc;
-}
-template <int R, bool INV, int... Ks>
-__device__ __forceinline__ void direct_dft(float2* v, std::integer_sequence<int, Ks...>) {
-  float2 out[R];
-  ((out[Ks] = direct_dft_term<R, INV, Ks>(v, std::make_integer_sequence<int, R - 1>{})), ...);
-#pragma unroll
-  for (int k = 0; k < R; ++k) v[k] = out[k];
-}
-
 template <int R, bool INV>
 struct DFT {
   __device__ __forceinline__ static void run(float2* v) {
-    if constexpr ((R & (R - 1)) == 0) {
-      dif_stages<R, INV, R / 2>(v);
-      bitrev_all<R>(v, std::make_integer_sequence<int, R>{});
-    } else {
-      direct_dft<R, INV>(v, std::make_integer_sequence<int, R>{});
-    }
+    dif_stages<R, INV, R / 2>(v);
+    bitrev_all<R>(v, std::make_integer_sequence<int, R>{});
   }
 };
 template <bool INV>
