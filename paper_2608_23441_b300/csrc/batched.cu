@@ -28,8 +28,11 @@ struct Variant {
 constexpr Variant kVariants[] = {{4, 256, 32, 512, 8192, "c4_t256_r32"},  {4, 256, 16, 512, 8192, "c4_t256_r16"},
                                  {2, 256, 32, 512, 8192, "c2_t256_r32"},  {8, 256, 32, 512, 8192, "c8_t256_r32"},
                                  {1, 512, 32, 512, 16384, "c1_t512_r32"}, {2, 0, 32, 512, 2048, "c2_ts16_r32"},
-                                 {4, 0, 32, 512, 2048, "c4_ts16_r32"},    {2, 512, 32, 16384, 16384, "c2_t512_r32"}};
-constexpr int kNumVariants = 8;
+                                 {4, 0, 32, 512, 2048, "c4_ts16_r32"},    {2, 512, 32, 16384, 16384, "c2_t512_r32"},
+                                 {1, 0, 32, 2048, 4096, "c1_ts16_r32"},   {1, 256, 32, 8192, 8192, "c1_t256_r32"},
+                                 {1, 1024, 32, 16384, 16384, "c1_t1024_r32"},
+                                 {2, 1024, 32, 16384, 16384, "c2_t1024_r32"}};
+constexpr int kNumVariants = 12;
 constexpr int kNumMClass = 5;   // power-of-two M = 2048 .. 32768, tuned among the variants
 constexpr int kNumOddClass = 2; // M = 5, 6 x 4096, one kernel each (kb3_odd.cu)
 constexpr int kNumClass = kNumMClass + kNumOddClass;
@@ -63,7 +66,7 @@ struct Plan {
   std::vector<float2*> chirp_ptr, bhat_ptr;  // device addresses of the tables, uploaded by prepare
   size_t total = 0;
   // defaults = the autotuner's choice on the 256-stream batch (M = 2048 .. 32768)
-  int variant[kNumMClass] = {0, 5, 2, 4, 7};
+  int variant[kNumMClass] = {8, 8, 9, 10, 11};
   const void* prepared_ws = nullptr;
   int normalize = 1;
 };
@@ -135,6 +138,10 @@ cudaError_t kb3_launch_v4(int, const BStream*, const BItem*, int, int*, cudaStre
 cudaError_t kb3_launch_v5(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb3_launch_v6(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb3_launch_v7(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb3_launch_v8(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb3_launch_v9(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb3_launch_v10(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
+cudaError_t kb3_launch_v11(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb3_launch_odd(int, const BStream*, const BItem*, int, int*, cudaStream_t, int*);
 cudaError_t kb_bhat_odd_launch(const int*, const int*, const float2* const*, float2* const*, int, cudaStream_t);
 }  // namespace ipfb
@@ -163,6 +170,10 @@ int launch_kb3(const Plan& P, char* ws, int cls, int v, cudaStream_t stream) {
     case 5: e = kb3_launch_v5(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
     case 6: e = kb3_launch_v6(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
     case 7: e = kb3_launch_v7(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
+    case 8: e = kb3_launch_v8(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
+    case 9: e = kb3_launch_v9(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
+    case 10: e = kb3_launch_v10(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
+    case 11: e = kb3_launch_v11(2048 << cls, s, it, (int)n, ctr, stream, &nclusters); break;
   }
   if (e != cudaSuccess) return fail(e, "kb3_columns");
   return IPFB_OK;

@@ -346,8 +346,10 @@ kb2_unpack(const BStream* __restrict__ streams, const BItem* __restrict__ items,
 // specialised to its S (one kernel switching over all S was register-allocated for
 // the largest and spilled ~3.7 KB per thread), and limited to 128 registers so two
 // CTAs share an SM (measured faster than one CTA with 255 registers).
+// Two CTAs per SM (at most 128 registers) except for the single-CTA 512-thread variant
+// and the 16384-element cluster runs, which hold one CTA per SM.
 template <int C, int S, int T, int MAXR>
-__global__ void __launch_bounds__(T, (C == 1 || S > 8192 ? 1 : 2))
+__global__ void __launch_bounds__(T, (C == 1 ? (T <= 256 && S <= 32 * T ? 2 : 1) : (S > 8192 ? 1 : 2)))
 kb3_columns(const BStream* __restrict__ streams, const BItem* __restrict__ items, int nitems, int* counter) {
   extern __shared__ float2 smem[];
   (void)counter;

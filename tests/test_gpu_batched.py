@@ -24,12 +24,19 @@ SHAPES = [(1024, 1031), (2048, 1500), (4096, 1024), (1024, 2310), (2048, 4099), 
 
 # column-kernel variants (cluster size, threads, largest radix) and their cluster sizes
 VARIANTS = {"c4_t256_r32": 4, "c4_t256_r16": 4, "c2_t256_r32": 2, "c8_t256_r32": 8, "c1_t512_r32": 1,
-            "c2_ts16_r32": 2, "c4_ts16_r32": 4, "c2_t512_r32": 2}
+            "c2_ts16_r32": 2, "c4_ts16_r32": 4, "c2_t512_r32": 2, "c1_ts16_r32": 1, "c1_t256_r32": 1,
+            "c1_t1024_r32": 1, "c2_t1024_r32": 2}
 
 
 def _in_range(M, C, name=""):
     # a CTA of a cluster holds up to 8192 elements, a single CTA up to 16384; the
     # "ts16" variants (S / 16 threads) serve S = 512 .. 2048
+    if name == "c1_ts16_r32":
+        return 2048 <= M <= 4096
+    if name == "c1_t256_r32":
+        return M == 8192
+    if name.endswith("t1024_r32"):
+        return M // C == 16384
     if "ts16" in name:
         return 512 <= M // C <= 2048
     if name == "c2_t512_r32":
