@@ -175,3 +175,37 @@ def test_binding_refuses_cpu_tensors():
     with pytest.raises(TypeError):
         ipfb.upchannelize(x, 1024)
 
+
+
+def test_batched_plan_lengths_and_default_variants():
+    """The batched plan is built on the host alone (descriptor pointers are checked, never
+    dereferenced): the Bluestein length classes report their kernels -- the tuned
+    defaults for the powers of two, the fixed 5- and 6-CTA kernels for 20480 and
+    24576 -- and a length that is neither is refused."""
+    L = ipfb.lib()
+    fake = 0x10000
+    shapes = [(1024, 1024), (2048, 1500), (4096, 3000), (1024, 5000), (1024, 9000), (2048, 11000), (1024, 16384)]
+    descs = (ipfb.StreamDesc * len(shapes))()
+    for i, (N, J) in enumerate(shapes):
+        descs[i] = ipfb.StreamDesc(N, 4, J, fake, fake, fake, 0.0141, fake)
+    plan = ctypes.c_void_p()
+    nbytes = ctypes.c_size_t(0)
+    assert L.ipfb_batched_plan(descs, len(shapes), 1, None, ctypes.byref(plan), ctypes.byref(nbytes)) == 0
+    assert nbytes.value > 0
+    buf = ctypes.create_string_buffer(64)
+
+    def variant(M):
+        rc = L.ipfb_batched_variant(plan, M, buf, 64)
+        return buf.value.decode() if rc == 0 else rc
+
+    assert variant(2048) == "c1_ts16_r32" and variant(4096) == "c1_ts16_r32"
+    assert variant(8192) == "c1_t256_r32"
+    assert variant(16384) == "c1_t1024_r32" and variant(32768) == "c2_t1024_r32"
+    assert variant(20480) == "c5_t256_r32" and variant(24576) == "c6_t256_r32"
+    assert variant(28672) == ipfb.ERR_INVALID and variant(65536) == ipfb.ERR_INVALID
+    assert L.ipfb_batched_free(plan) == 0
+    # frame counts outside 1024 .. 16384 and unaligned code arrays are refused
+    for N, J, codes in ((1024, 16385, fake), (1024, 1023, fake), (1024, 4000, fake + 8)):
+        one = (ipfb.StreamDesc * 1)(ipfb.StreamDesc(N, 4, J, codes, fake, fake, 0.0141, fake))
+        p = ctypes.c_void_p()
+        assert L.ipfb_batched_plan(one, 1, 1, None, ctypes.byref(p), ctypes.byref(nbytes)) != 0
