@@ -346,10 +346,18 @@ kb2_unpack(const BStream* __restrict__ streams, const BItem* __restrict__ items,
 // specialised to its S (one kernel switching over all S was register-allocated for
 // the largest and spilled ~3.7 KB per thread), and limited to 128 registers so two
 // CTAs share an SM (measured faster than one CTA with 255 registers).
-// Two CTAs per SM (at most 128 registers) except for the single-CTA 512-thread variant
-// and the 16384-element cluster runs, which hold one CTA per SM.
+// CTAs per SM the register budget is set for: two (at most 128 registers) in general,
+// three (at most 80) for the 5- and 6-CTA clusters and the single-CTA 4096-point run
+// (measured faster despite 88-160 bytes of spills per thread), one for the single-CTA
+// 512-thread variant and the 16384-element runs.
+template <int C, int S, int T>
+constexpr int kb3_min_blocks() {
+  if (C == 1) return (S == 4096 && T == 256) ? 3 : ((T <= 256 && S <= 32 * T) ? 2 : 1);
+  if (S > 8192) return 1;
+  return (C == 5 || C == 6) ? 3 : 2;
+}
 template <int C, int S, int T, int MAXR>
-__global__ void __launch_bounds__(T, (C == 1 ? (T <= 256 && S <= 32 * T ? 2 : 1) : (S > 8192 ? 1 : 2)))
+__global__ void __launch_bounds__(T, kb3_min_blocks<C, S, T>())
 kb3_columns(const BStream* __restrict__ streams, const BItem* __restrict__ items, int nitems, int* counter) {
   extern __shared__ float2 smem[];
   (void)counter;
